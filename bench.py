@@ -1,0 +1,324 @@
+"""Benchmark of the out-of-core star-join path on one GB300.
+
+Workload (default, "star"): 600,000,000-row fact table of 8 int32 columns
+(19.2 GB) held in pinned host memory, four dimensions of 2,556 / 200,000 /
+2,000,000 / 30,000 rows, device budget 4 GiB.  One step runs the six star
+templates with 3-4 chained probes at ~0.1 / 1 / 10 % combined selectivity
+(group-by over 175 or 875 groups, SUM(price - cost) with both payload columns
+late-materialized when the estimate is below TH).
+
+Reported (one JSON line): host GB/s consumed (referenced column bytes x rows /
+step time) with dimension tables resident, against the pinned host->device
+peak measured in the same run; the dominant kernel's HBM roofline; an
+end-to-end figure through the public call with dimension tables rebuilt from
+host memory every step; the oracle timed on the host cores on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--rows R] [--budget-gb G]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TEMPLATES = ["T2_0.1", "T2_1", "T2_10", "T3_0.1", "T3_1", "T3_10"]
+METRIC = "Host-data GB/s vs measured H2D peak (learned vs plain); p50/p99 query latency"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rows", type=int, default=600_000_000)
+    ap.add_argument("--budget-gb", type=float, default=4.0)
+    ap.add_argument("--cpu-sample-rows", type=int, default=0, help="oracle sample rows (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                mhz.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_per_row():
+    """dram bytes per fact row of the chunk kernel from the committed ncu
+    summary (None if absent or stale)."""
+    p = os.path.join(ROOT, "profiles", "star_chunk_kernel_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("dram_bytes_per_row:"):
+            try:
+                return float(line.split(":", 1)[1])
+            except ValueError:
+                return None
+    return None
+
+
+def make_data(rows):
+    import datagen as G
+    fact = G.star_fact(rows)
+    dims = G.star_dims(0)
+    return fact, dims
+
+
+def cpu_baseline(fact, dims, sample_rows):
+    """The oracle as it stands, on the host cores, over the first sample_rows
+    fact rows of every template of one step."""
+    import datagen as G
+    import oracle as O
+    nthreads = os.cpu_count() or 1
+    logical = 0
+    t0 = time.perf_counter()
+    for name in TEMPLATES:
+        T = G.star_templates()[name]
+        O.star(T, fact, dims, 0, sample_rows, nthreads=nthreads)
+        cols = {c for c, _, _ in T["fact_preds"]} | {d["fk"] for d in T["dims"]} | \
+            {c for c in T["agg"][1:] if c}
+        logical += 4 * len(cols) * sample_rows
+    dt = time.perf_counter() - t0
+    return logical / dt / 1e9, nthreads, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import datagen as G  # noqa: F401
+    sample = args.cpu_sample_rows or 20_000_000
+    fact, dims = make_data(sample)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state
+    vals, dts = [], []
+    for _ in range(args.steps):
+        v, cores, dt = cpu_baseline(fact, dims, sample)
+        vals.append(v)
+        dts.append(dt)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * statistics.median(dts), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"star join, {TEMPLATES} over the first {sample} rows of the 600M-row fact table",
+                   "rows": sample},
+        "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} fact rows, 6 templates"},
+        "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import datagen as G
+    import paper_2502_09541_gb300 as vx
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    vx.load()
+    t_gen = time.perf_counter()
+    fact, dims = make_data(args.rows)
+    t_gen = time.perf_counter() - t_gen
+
+    budget = int(args.budget_gb * (1 << 30))
+    arena = torch.empty(budget, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    ctx = vx.vx_open_ex(arena.data_ptr(), budget, stream.cuda_stream)
+    fid = {c: vx.vx_register_host_column(ctx, c, fact[c]) for c in fact}
+    did = {d: {a: vx.vx_register_host_column(ctx, f"{d}.{a}", arr) for a, arr in dims[d].items()} for d in dims}
+    tmpls = G.star_templates()
+    plans = [vx.make_plan(tmpls[n], fid, did, G.STAR_ATTR_CARD) for n in TEMPLATES]
+
+    # link peak measured in this run (pinned copies, 64 MiB chunks)
+    h2d_peak, d2h_peak, bid_peak = vx.vx_probe_link(ctx, 2 << 30, 64 << 20)
+
+    def step(collect):
+        for p in plans:
+            st, gid, s, c, stats = vx.vx_run_plan(ctx, p)
+            assert st == vx.VX_OK
+            collect.append(stats)
+
+    for _ in range(max(args.warmup, 3)):
+        step([])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    stats_all = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(stats_all)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    logical = sum(s["bytes_logical"] for s in stats_all) / args.steps
+    link = sum(s["bytes_h2d"] + s["bytes_zero_copy"] for s in stats_all) / args.steps
+    host_gbs = logical * world / (ms_step * 1e6)
+    link_gbs = link / (ms_step * 1e6)
+    launches = int(sum(s["kernel_launches"] for s in stats_all))
+    kern_ms = sum(s["ms_kernel"] for s in stats_all)
+    rows_step = sum(s["rows"] for s in stats_all) / args.steps
+    per_q_ms = {}
+    for i, n in enumerate(TEMPLATES):
+        per_q_ms[n] = round(statistics.median(s["ms_total"] for s in stats_all[i::len(TEMPLATES)]), 3)
+
+    # dominant kernel: the fused chunk kernel; algorithmic HBM bytes = staged
+    # column bytes it reads (rows x staged columns x 4)
+    staged_bytes = sum(s["bytes_h2d"] for s in stats_all)
+    hbm_peak, peak_kind = measured_peaks()
+    ach = staged_bytes / (kern_ms * 1e6) if kern_ms > 0 else None
+    tpr = traffic_per_row()
+    avg_launch_rows = sum(s["rows"] for s in stats_all) / max(1, launches)
+    roofline = {"bound": "hbm", "kernel": "star_chunk_kernel", "achieved": round(ach, 1) if ach else None,
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4) if ach else None,
+                "peak_kind": peak_kind,
+                "traffic": round(tpr * avg_launch_rows) if tpr else None,
+                "algorithmic_bytes_per_launch": round(staged_bytes / max(1, launches)),
+                "avg_launch_us": round(1000 * kern_ms / max(1, launches), 2)}
+
+    # end to end through the public call: dimension tables rebuilt from host
+    # columns every step, fact chunks copied from pinned host memory, results
+    # read back to host
+    e2e_stats = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vx.vx_drop_resident(ctx)
+        step(e2e_stats)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    dim_bytes = sum(4 * len(dims[d]) * len(dims[d]["key"]) for d in dims)
+    e2e_h2d = sum(s["bytes_h2d"] + s["bytes_zero_copy"] for s in e2e_stats) / args.steps + dim_bytes
+    e2e_d2h = sum(s["bytes_d2h"] for s in e2e_stats) / args.steps
+    e2e_gbs = logical * world / (e2e_s * 1e9)
+
+    line = {
+        "metric": METRIC, "value": round(host_gbs, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"star join: {args.rows}-row fact (8 int32 cols, host-resident), dims 2556/200000/"
+                               f"2000000/30000, templates {TEMPLATES}, budget {args.budget_gb} GiB",
+                   "rows": args.rows, "l2": "inputs larger than L2 (fact columns stream from host)",
+                   "chunk_bytes": int(vx.vx_get_config(ctx).chunk_bytes), "form": "plain"},
+        "link": {"h2d_peak_gbs": round(h2d_peak, 1), "d2h_peak_gbs": round(d2h_peak, 1),
+                 "bidir_peak_gbs": round(bid_peak, 1), "link_gbs": round(link_gbs, 1),
+                 "link_frac": round(link_gbs / h2d_peak, 4), "host_frac": round(host_gbs / world / h2d_peak, 4)},
+        "rows_per_s": round(rows_step * world / (ms_step / 1000)),
+        "query_ms": per_q_ms,
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": int(e2e_h2d),
+                "d2h_bytes_per_step": int(e2e_d2h)},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "setup_s": {"generate": round(t_gen, 1)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = args.cpu_sample_rows or min(args.rows, 20_000_000)
+        v, cores, dt = cpu_baseline(fact, dims, sample)
+        line["cpu_baseline"] = {"value": round(v, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                                "sample": f"first {sample} fact rows x 6 templates ({dt:.1f} s)"}
+    vx.vx_close(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

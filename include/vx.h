@@ -1,0 +1,235 @@
+/*
+ * vx.h — C ABI of the GB300 out-of-core query library.
+ *
+ * The library runs relational operators over columns that live in host memory
+ * and are larger than the device budget (Vortex, arXiv 2502.09541).  As in the
+ * paper's IO-decoupled programming model (Section 5), every operator is split
+ * into (a) a data mapping — which host extents form chunk `it` — and (b) an
+ * IO-agnostic kernel that sees only device buffers; a pipelined executor
+ * (Section 5.3) streams chunks from pinned host memory into staging slots on
+ * a copy-engine stream while the kernel of the previous chunk runs and the
+ * output of the chunk before it is saved.  Columns whose estimated selectivity
+ * is below the zero-copy threshold are not staged: the kernel reads them from
+ * mapped host memory for qualifying rows only (Section 6.3).
+ *
+ * Conventions
+ *   - Every call returns vx_status: VX_OK (0) or a negative VX_E_* code.
+ *     vx_last_error() returns a thread-local message for the last failure.
+ *   - Handles are opaque.  One context may be used by one thread at a time
+ *     (calls take an internal lock; concurrent calls serialise).
+ *   - Host memory: the caller owns every host buffer.  Registered columns must
+ *     stay alive and unchanged until they are unregistered or the context is
+ *     closed.  The library page-locks (cudaHostRegister, mapped) columns that
+ *     are not already pinned and unlocks them again on unregister/close.
+ *     Output buffers are plain host memory sized by the caller; a call whose
+ *     output does not fit returns VX_E_CAPACITY and reports the size needed.
+ *   - Device memory: all device memory the library uses comes from one arena
+ *     of exactly the budget given to vx_open (or the arena handed to
+ *     vx_open_ex).  A request that does not fit returns VX_E_NOMEM.
+ *   - Results are exact: integer keys, two's-complement wrapping 64-bit sums,
+ *     row ids in ascending order, stable sort order.
+ */
+#ifndef VX_H
+#define VX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vx_status;
+
+enum {
+  VX_OK = 0,
+  VX_E_INVAL = -1,       /* bad argument */
+  VX_E_NOMEM = -2,       /* device arena or host allocation exhausted */
+  VX_E_CUDA = -3,        /* CUDA runtime error (message in vx_last_error) */
+  VX_E_CAPACITY = -4,    /* caller output buffer too small; required size reported */
+  VX_E_TIMEOUT = -5,     /* a bounded wait expired */
+  VX_E_BUSY = -6,        /* serving queue full */
+  VX_E_UNSUPPORTED = -7, /* valid request outside what this build implements */
+  VX_E_DUPKEY = -8,      /* duplicate key on the build side of a join */
+  VX_E_RANGE = -9        /* a group-key code outside [0, card) */
+};
+
+typedef enum { VX_I32 = 0, VX_U32 = 1, VX_I64 = 2, VX_U64 = 3 } vx_dtype;
+
+typedef struct vx_ctx vx_ctx;
+
+/* ---------------------------------------------------------------- config */
+enum { VX_SCHED_IMMEDIATE = 0, VX_SCHED_DAG = 1 };
+enum { VX_LATE_AUTO = 0, VX_LATE_FORCE_EARLY = 1, VX_LATE_FORCE_LATE = 2 };
+
+typedef struct {
+  uint64_t chunk_bytes;     /* staged host bytes per chunk, all staged columns (default 64 MiB) */
+  int32_t n_slots;          /* staging slots in the ring, >= 2 (default 3) */
+  int32_t sched;            /* VX_SCHED_IMMEDIATE: the host issues a copy only when it can run at
+                               once (Section 4.3, principle 1); VX_SCHED_DAG: every copy and kernel
+                               is enqueued up front with stream/event dependencies (Section 4.2) */
+  int32_t late_mat;         /* default late-materialization policy of vx_run_plan */
+  double zc_threshold;      /* selectivity threshold TH of Section 6.3; 0 = default */
+  int32_t use_graphs;       /* vx_run_plan: capture the chunk pipeline in a CUDA graph and replay it */
+  int32_t block_threads;    /* threads per block of the chunk kernels (default 256) */
+  int32_t blocks_per_sm;    /* resident blocks per SM of the chunk kernels (default 4) */
+  uint32_t wait_timeout_ms; /* limit of every host-side wait (default 60000) */
+} vx_config;
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Opens a context on the current CUDA device with a device arena of exactly
+ * device_budget_bytes (one cudaMalloc).  The budget caps every operator so that
+ * data larger than it must stream (Section 5.3: the executor divides device
+ * memory into staging buffers and temporary space).  Creates three streams:
+ * compute, host-to-device and device-to-host. */
+vx_status vx_open(uint64_t device_budget_bytes, vx_ctx **out);
+
+/* As vx_open, but uses a caller-owned device arena [dev_arena, dev_arena+bytes)
+ * (e.g. allocated by PyTorch) and, if cuda_stream is non-NULL, that stream as
+ * the compute stream.  The arena must stay allocated until vx_close. */
+vx_status vx_open_ex(void *dev_arena, uint64_t bytes, void *cuda_stream, vx_ctx **out);
+
+/* Unregisters all columns, frees what the context allocated, destroys its
+ * streams.  NULL is accepted. */
+vx_status vx_close(vx_ctx *ctx);
+
+/* Thread-local text of the last error ("" if none). */
+const char *vx_last_error(void);
+
+vx_status vx_get_config(vx_ctx *ctx, vx_config *out);
+vx_status vx_set_config(vx_ctx *ctx, const vx_config *cfg);
+
+/* ---------------------------------------------------------------- columns */
+
+/* Registers a host column of n_rows elements of dtype (the paper's stationary
+ * DRAM data, Section 5.2: only a mapping table refers to it).  flags: 0.
+ * Returns its id in *col_id. */
+vx_status vx_register_host_column(vx_ctx *ctx, const char *name, int32_t dtype, const void *host,
+                                  uint64_t n_rows, uint32_t flags, int32_t *col_id);
+vx_status vx_unregister_host_column(vx_ctx *ctx, int32_t col_id);
+
+/* ---------------------------------------------------------------- predicates */
+enum { VX_BETWEEN = 0, VX_EQ = 1, VX_NE = 2, VX_LT = 3, VX_LE = 4, VX_GT = 5, VX_GE = 6 };
+
+/* Row predicate on an int32 column: BETWEEN is lo <= v <= hi; the others
+ * compare v with lo. */
+typedef struct {
+  int32_t col;
+  int32_t op;
+  int32_t lo, hi;
+} vx_pred;
+
+/* Filter with stream compaction (Section 6.3, selection sigma): writes the
+ * ascending global row ids r in [row_begin, row_end) for which every predicate
+ * holds into out_rows[0 .. min(count, cap)), and the full count into
+ * *out_count.  row_end = 0 means the column length.  out_rows may be NULL (count
+ * only).  All predicate columns must be int32 and of equal length.
+ * Returns VX_E_CAPACITY if count > cap (the first cap ids are written). */
+vx_status vx_filter(vx_ctx *ctx, const vx_pred *preds, int32_t n_preds, uint64_t row_begin,
+                    uint64_t row_end, uint64_t *out_rows, uint64_t cap, uint64_t *out_count);
+
+/* ---------------------------------------------------------------- plans */
+enum { VX_AGG_COUNT = 0, VX_AGG_SUM = 1, VX_AGG_MUL = 2, VX_AGG_SUB = 3 };
+#define VX_MAX_DIMS 8
+#define VX_MAX_PREDS 8
+#define VX_MAX_GKEYS 4
+
+/* One dimension of a star plan: the fact column fact_fk_col is joined to
+ * key_col (unique int32 keys, an inner join), and the dimension predicates
+ * are applied to its attribute columns (Section 7.1: dimensions are filtered
+ * and hashed on the device and kept there while fact chunks stream). */
+typedef struct {
+  int32_t key_col;
+  int32_t fact_fk_col;
+  int32_t n_attr;
+  int32_t attr_col[4];
+  int32_t n_preds;
+  int32_t pred_attr[4]; /* index into attr_col */
+  int32_t pred_op[4], pred_lo[4], pred_hi[4];
+} vx_plan_dim;
+
+/* Group key: dim >= 0 -> attribute attr of dimension dim; dim == -1 -> the
+ * int32 fact column fact_col.  Codes must lie in [0, card). */
+typedef struct {
+  int32_t dim;
+  int32_t attr;
+  int32_t card;
+  int32_t fact_col;
+} vx_plan_gkey;
+
+/* A star query: filter fact rows, probe the dimensions in the given order,
+ * group by the mixed-radix number of the group-key codes (first key most
+ * significant) and aggregate agg(a, b) as wrapping int64 sums plus counts. */
+typedef struct {
+  int32_t n_dims;
+  vx_plan_dim dims[VX_MAX_DIMS];
+  int32_t n_fact_preds;
+  vx_pred fact_preds[VX_MAX_PREDS];
+  int32_t n_group_keys;
+  vx_plan_gkey group_keys[VX_MAX_GKEYS];
+  int32_t agg_op;        /* VX_AGG_* */
+  int32_t agg_a, agg_b;  /* int32 fact columns (-1 if unused) */
+  int32_t late_mat;      /* VX_LATE_* for the aggregate columns */
+  uint64_t row_begin, row_end; /* fact row range; row_end = 0 means all rows */
+} vx_plan;
+
+/* Per-call statistics (host-visible). */
+typedef struct {
+  uint64_t rows;           /* fact rows scanned */
+  uint64_t survivors;      /* rows aggregated / emitted */
+  uint64_t chunks;
+  uint64_t bytes_h2d;      /* bytes moved by the copy engine host->device */
+  uint64_t bytes_d2h;      /* bytes moved by the copy engine device->host */
+  uint64_t bytes_zero_copy;/* estimated bytes crossing the link for zero-copy reads (64 B granules) */
+  uint64_t bytes_logical;  /* referenced column bytes x rows (the host data the query consumes) */
+  uint32_t late_mask;      /* bit i set: aggregate column i was read by zero-copy */
+  uint32_t overflow_retries;
+  double est_selectivity;  /* planner estimate used for the late/early decision */
+  double ms_total;         /* wall time of the call */
+  double ms_kernel;        /* summed device time of the chunk kernels (CUDA events) */
+  uint64_t kernel_launches;/* kernels launched by the call */
+} vx_query_stats;
+
+/* Result of vx_run_plan / vx_groupby: groups with count > 0 in ascending group
+ * id.  The caller provides arrays of capacity cap; *n_out receives the number
+ * of non-empty groups (VX_E_CAPACITY if it exceeds cap). */
+typedef struct {
+  uint64_t cap;
+  uint64_t *gid;
+  int64_t *sum;
+  uint64_t *cnt;
+  uint64_t n_out;
+  vx_query_stats stats;
+} vx_result;
+
+/* Runs a star plan over the registered columns (Sections 5-7: chunked fact
+ * stream, resident dimension hash tables, zero-copy late materialization). */
+vx_status vx_run_plan(vx_ctx *ctx, const vx_plan *plan, vx_result *out);
+
+/* Group-by aggregation over fact columns only (a star plan without
+ * dimensions): keys are int32 fact columns with codes in [0, card). */
+vx_status vx_groupby(vx_ctx *ctx, const vx_plan_gkey *keys, int32_t n_keys, int32_t agg_op, int32_t agg_a,
+                     int32_t agg_b, const vx_pred *preds, int32_t n_preds, vx_result *out);
+
+/* Frees the dimension hash tables that vx_run_plan keeps resident on the
+ * device between calls (Section 7.1 keeps filtered dimension tables on the
+ * GPU); the next plan rebuilds them from the host columns. */
+vx_status vx_drop_resident(vx_ctx *ctx);
+
+/* Statistics of the last completed call on this context. */
+vx_status vx_last_stats(vx_ctx *ctx, vx_query_stats *out);
+
+/* ---------------------------------------------------------------- link probe */
+
+/* Pinned-copy microbenchmark of the host link (Section 8.1 measures Exchange
+ * bandwidth against transfer and packet size): copies `bytes` in chunks of
+ * `chunk` bytes host->device, device->host and both at once, using the
+ * context's copy streams and arena, and reports GB/s (1e9 B/s). */
+vx_status vx_probe_link(vx_ctx *ctx, uint64_t bytes, uint64_t chunk, double *h2d_gbs, double *d2h_gbs,
+                        double *bidir_gbs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VX_H */

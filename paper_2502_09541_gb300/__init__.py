@@ -1,0 +1,271 @@
+"""Python binding of libvx (include/vx.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls; all work runs
+in the CUDA library.  Loading fails loudly if the library is missing or no
+CUDA device is present — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvx.so")
+_lib = None
+_lock = threading.Lock()
+
+# ---- constants (vx.h)
+VX_OK, VX_E_INVAL, VX_E_NOMEM, VX_E_CUDA, VX_E_CAPACITY, VX_E_TIMEOUT, VX_E_BUSY, VX_E_UNSUPPORTED, \
+    VX_E_DUPKEY, VX_E_RANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+VX_I32, VX_U32, VX_I64, VX_U64 = 0, 1, 2, 3
+VX_SCHED_IMMEDIATE, VX_SCHED_DAG = 0, 1
+VX_LATE_AUTO, VX_LATE_FORCE_EARLY, VX_LATE_FORCE_LATE = 0, 1, 2
+VX_BETWEEN, VX_EQ, VX_NE, VX_LT, VX_LE, VX_GT, VX_GE = range(7)
+VX_AGG_COUNT, VX_AGG_SUM, VX_AGG_MUL, VX_AGG_SUB = range(4)
+VX_MAX_DIMS, VX_MAX_PREDS, VX_MAX_GKEYS = 8, 8, 4
+I32MIN = -2**31
+
+_NP_DTYPE = {np.dtype(np.int32): VX_I32, np.dtype(np.uint32): VX_U32, np.dtype(np.int64): VX_I64,
+             np.dtype(np.uint64): VX_U64}
+
+
+class VxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"vx status {status}: {msg}")
+        self.status = status
+
+
+# ---- structs (vx.h)
+class vx_config(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_uint64), ("n_slots", ctypes.c_int32), ("sched", ctypes.c_int32),
+                ("late_mat", ctypes.c_int32), ("zc_threshold", ctypes.c_double), ("use_graphs", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("wait_timeout_ms", ctypes.c_uint32)]
+
+
+class vx_pred(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int32), ("op", ctypes.c_int32), ("lo", ctypes.c_int32), ("hi", ctypes.c_int32)]
+
+
+class vx_plan_dim(ctypes.Structure):
+    _fields_ = [("key_col", ctypes.c_int32), ("fact_fk_col", ctypes.c_int32), ("n_attr", ctypes.c_int32),
+                ("attr_col", ctypes.c_int32 * 4), ("n_preds", ctypes.c_int32), ("pred_attr", ctypes.c_int32 * 4),
+                ("pred_op", ctypes.c_int32 * 4), ("pred_lo", ctypes.c_int32 * 4), ("pred_hi", ctypes.c_int32 * 4)]
+
+
+class vx_plan_gkey(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("attr", ctypes.c_int32), ("card", ctypes.c_int32),
+                ("fact_col", ctypes.c_int32)]
+
+
+class vx_plan(ctypes.Structure):
+    _fields_ = [("n_dims", ctypes.c_int32), ("dims", vx_plan_dim * VX_MAX_DIMS), ("n_fact_preds", ctypes.c_int32),
+                ("fact_preds", vx_pred * VX_MAX_PREDS), ("n_group_keys", ctypes.c_int32),
+                ("group_keys", vx_plan_gkey * VX_MAX_GKEYS), ("agg_op", ctypes.c_int32), ("agg_a", ctypes.c_int32),
+                ("agg_b", ctypes.c_int32), ("late_mat", ctypes.c_int32), ("row_begin", ctypes.c_uint64),
+                ("row_end", ctypes.c_uint64)]
+
+
+class vx_query_stats(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint64), ("survivors", ctypes.c_uint64), ("chunks", ctypes.c_uint64),
+                ("bytes_h2d", ctypes.c_uint64), ("bytes_d2h", ctypes.c_uint64), ("bytes_zero_copy", ctypes.c_uint64),
+                ("bytes_logical", ctypes.c_uint64), ("late_mask", ctypes.c_uint32),
+                ("overflow_retries", ctypes.c_uint32), ("est_selectivity", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class vx_result(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_uint64), ("gid", ctypes.c_void_p), ("sum", ctypes.c_void_p),
+                ("cnt", ctypes.c_void_p), ("n_out", ctypes.c_uint64), ("stats", vx_query_stats)]
+
+
+_P = ctypes.POINTER
+_vp, _u64, _i32, _u32, _dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
+SIGNATURES = {
+    "vx_open": ([_u64, _P(_vp)], _i32),
+    "vx_open_ex": ([_vp, _u64, _vp, _P(_vp)], _i32),
+    "vx_close": ([_vp], _i32),
+    "vx_last_error": ([], ctypes.c_char_p),
+    "vx_get_config": ([_vp, _P(vx_config)], _i32),
+    "vx_set_config": ([_vp, _P(vx_config)], _i32),
+    "vx_register_host_column": ([_vp, ctypes.c_char_p, _i32, _vp, _u64, _u32, _P(_i32)], _i32),
+    "vx_unregister_host_column": ([_vp, _i32], _i32),
+    "vx_filter": ([_vp, _P(vx_pred), _i32, _u64, _u64, _vp, _u64, _P(_u64)], _i32),
+    "vx_run_plan": ([_vp, _P(vx_plan), _P(vx_result)], _i32),
+    "vx_groupby": ([_vp, _P(vx_plan_gkey), _i32, _i32, _i32, _i32, _P(vx_pred), _i32, _P(vx_result)], _i32),
+    "vx_last_stats": ([_vp, _P(vx_query_stats)], _i32),
+    "vx_drop_resident": ([_vp], _i32),
+    "vx_probe_link": ([_vp, _u64, _u64, _P(_dbl), _P(_dbl), _P(_dbl)], _i32),
+}
+
+
+def load(build_if_missing: bool = True):
+    """Loads libvx.so (building it in-tree first if asked).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                from . import build as _b
+                _b.build()
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libvx.so not built at {LIB_PATH}")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != VX_OK:
+        raise VxError(st, load().vx_last_error().decode(errors="replace"))
+    return st
+
+
+def vx_last_error() -> str:
+    return load().vx_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------ thin wrappers
+def vx_open(device_budget_bytes: int):
+    h = ctypes.c_void_p()
+    _check(load().vx_open(device_budget_bytes, ctypes.byref(h)))
+    return h
+
+
+def vx_open_ex(dev_ptr: int, nbytes: int, stream: int | None = None):
+    h = ctypes.c_void_p()
+    _check(load().vx_open_ex(dev_ptr, nbytes, stream, ctypes.byref(h)))
+    return h
+
+
+def vx_close(ctx):
+    _check(load().vx_close(ctx))
+
+
+def vx_get_config(ctx) -> vx_config:
+    c = vx_config()
+    _check(load().vx_get_config(ctx, ctypes.byref(c)))
+    return c
+
+
+def vx_set_config(ctx, cfg: vx_config):
+    _check(load().vx_set_config(ctx, ctypes.byref(cfg)))
+
+
+def vx_register_host_column(ctx, name: str, array: np.ndarray) -> int:
+    assert array.flags["C_CONTIGUOUS"]
+    cid = ctypes.c_int32()
+    _check(load().vx_register_host_column(ctx, name.encode(), _NP_DTYPE[array.dtype], array.ctypes.data,
+                                          len(array), 0, ctypes.byref(cid)))
+    return cid.value
+
+
+def vx_unregister_host_column(ctx, col_id: int):
+    _check(load().vx_unregister_host_column(ctx, col_id))
+
+
+def vx_filter(ctx, preds, row_begin=0, row_end=0, out: np.ndarray | None = None):
+    """preds: list of (col_id, op, lo, hi).  Returns (status, count); writes out."""
+    arr = (vx_pred * len(preds))(*[vx_pred(*p) for p in preds])
+    cnt = ctypes.c_uint64()
+    st = load().vx_filter(ctx, arr, len(preds), row_begin, row_end, None if out is None else out.ctypes.data,
+                          0 if out is None else len(out), ctypes.byref(cnt))
+    if st not in (VX_OK, VX_E_CAPACITY):
+        _check(st)
+    return st, cnt.value
+
+
+def vx_run_plan(ctx, plan: vx_plan, cap: int = 1 << 16):
+    """Returns (status, gid, sum, cnt, stats) with arrays trimmed to n_out."""
+    gid = np.zeros(cap, np.uint64)
+    s = np.zeros(cap, np.int64)
+    c = np.zeros(cap, np.uint64)
+    res = vx_result(cap, gid.ctypes.data, s.ctypes.data, c.ctypes.data, 0, vx_query_stats())
+    st = load().vx_run_plan(ctx, ctypes.byref(plan), ctypes.byref(res))
+    if st not in (VX_OK, VX_E_CAPACITY):
+        _check(st)
+    n = min(res.n_out, cap)
+    return st, gid[:n], s[:n], c[:n], res.stats.as_dict()
+
+
+def vx_groupby(ctx, keys, agg_op, agg_a, agg_b, preds, cap: int = 1 << 16):
+    """keys: list of (col_id, card)."""
+    karr = (vx_plan_gkey * max(1, len(keys)))(*[vx_plan_gkey(-1, 0, card, col) for col, card in keys])
+    parr = (vx_pred * max(1, len(preds)))(*[vx_pred(*p) for p in preds])
+    gid = np.zeros(cap, np.uint64)
+    s = np.zeros(cap, np.int64)
+    c = np.zeros(cap, np.uint64)
+    res = vx_result(cap, gid.ctypes.data, s.ctypes.data, c.ctypes.data, 0, vx_query_stats())
+    st = load().vx_groupby(ctx, karr, len(keys), agg_op, agg_a, agg_b, parr, len(preds), ctypes.byref(res))
+    if st not in (VX_OK, VX_E_CAPACITY):
+        _check(st)
+    n = min(res.n_out, cap)
+    return st, gid[:n], s[:n], c[:n], res.stats.as_dict()
+
+
+def vx_drop_resident(ctx):
+    _check(load().vx_drop_resident(ctx))
+
+
+def vx_last_stats(ctx) -> dict:
+    s = vx_query_stats()
+    _check(load().vx_last_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def vx_probe_link(ctx, nbytes: int, chunk: int):
+    a, b, c = _dbl(), _dbl(), _dbl()
+    _check(load().vx_probe_link(ctx, nbytes, chunk, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+# ------------------------------------------------------------------ plan marshalling
+def make_plan(tmpl: dict, fact_ids: dict, dim_ids: dict, attr_cards: dict, late_mat=VX_LATE_AUTO,
+              row_begin=0, row_end=0) -> vx_plan:
+    """Marshals a template dict (dims / fact_preds / group / agg, predicates as
+    inclusive int32 ranges) into a vx_plan.  fact_ids: fact column -> id;
+    dim_ids: dim -> {"key": id, attr: id}; attr_cards: dim -> {attr: card} in
+    attribute order."""
+    attr_names = {d: list(v.keys()) for d, v in attr_cards.items()}
+    p = vx_plan()
+    p.n_dims = len(tmpl["dims"])
+    dindex = {}
+    for d, spec in enumerate(tmpl["dims"]):
+        attrs = attr_names[spec["dim"]]
+        pd = p.dims[d]
+        pd.key_col = dim_ids[spec["dim"]]["key"]
+        pd.fact_fk_col = fact_ids[spec["fk"]]
+        pd.n_attr = len(attrs)
+        for k, a in enumerate(attrs):
+            pd.attr_col[k] = dim_ids[spec["dim"]][a]
+        pd.n_preds = len(spec["preds"])
+        for k, (a, lo, hi) in enumerate(spec["preds"]):
+            pd.pred_attr[k] = attrs.index(a)
+            pd.pred_op[k] = VX_BETWEEN
+            pd.pred_lo[k] = lo
+            pd.pred_hi[k] = hi
+        dindex[spec["dim"]] = d
+    p.n_fact_preds = len(tmpl["fact_preds"])
+    for k, (c, lo, hi) in enumerate(tmpl["fact_preds"]):
+        p.fact_preds[k] = vx_pred(fact_ids[c], VX_BETWEEN, lo, hi)
+    p.n_group_keys = len(tmpl["group"])
+    for k, g in enumerate(tmpl["group"]):
+        dname, a = g
+        p.group_keys[k] = vx_plan_gkey(dindex[dname], attr_names[dname].index(a), attr_cards[dname][a], -1)
+    op, a, b = tmpl["agg"]
+    p.agg_op = {"sum": VX_AGG_SUM, "mul": VX_AGG_MUL, "sub": VX_AGG_SUB, "count": VX_AGG_COUNT}[op]
+    p.agg_a = fact_ids[a] if a else -1
+    p.agg_b = fact_ids[b] if b else -1
+    p.late_mat = late_mat
+    p.row_begin = row_begin
+    p.row_end = row_end
+    return p

@@ -1,0 +1,374 @@
+// Context lifetime, device arena, host column registry, errors, link probe.
+#include <cstdarg>
+#include <cstdio>
+
+#include "vx_internal.h"
+
+namespace vx {
+
+static thread_local char g_err[1024];
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------ arena
+static constexpr uint64_t kAlign = 256;
+
+void Arena::init(char *base, uint64_t bytes) {
+  base_ = base;
+  uint64_t b = bytes & ~(kAlign - 1);
+  bytes_ = b;
+  used_ = 0;
+  free_.clear();
+  live_.clear();
+  if (b) free_[0] = b;
+}
+
+void *Arena::alloc(uint64_t bytes) {
+  uint64_t need = (bytes + kAlign - 1) & ~(kAlign - 1);
+  if (need == 0) need = kAlign;
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second >= need) {
+      uint64_t off = it->first, sz = it->second;
+      free_.erase(it);
+      if (sz > need) free_[off + need] = sz - need;
+      live_[off] = need;
+      used_ += need;
+      return base_ + off;
+    }
+  }
+  return nullptr;
+}
+
+void Arena::free(void *p) {
+  if (!p) return;
+  uint64_t off = (uint64_t)((char *)p - base_);
+  auto it = live_.find(off);
+  if (it == live_.end()) return;
+  uint64_t sz = it->second;
+  live_.erase(it);
+  used_ -= sz;
+  auto nx = free_.lower_bound(off);
+  if (nx != free_.end() && nx->first == off + sz) {  // merge with next
+    sz += nx->second;
+    free_.erase(nx);
+  }
+  auto pv = free_.lower_bound(off);
+  if (pv != free_.begin()) {
+    --pv;
+    if (pv->first + pv->second == off) {  // merge with previous
+      pv->second += sz;
+      return;
+    }
+  }
+  free_[off] = sz;
+}
+
+uint64_t Arena::largest_free() const {
+  uint64_t m = 0;
+  for (auto &kv : free_) m = kv.second > m ? kv.second : m;
+  return m;
+}
+
+vx_status check_ctx(vx_ctx *ctx) {
+  if (!ctx) {
+    set_error("null context");
+    return VX_E_INVAL;
+  }
+  VX_CUDA_TRY(cudaSetDevice(ctx->device));
+  return VX_OK;
+}
+
+const Column *get_col(vx_ctx *ctx, int32_t id, int32_t want) {
+  if (id < 0 || id >= (int32_t)ctx->cols.size() || !ctx->cols[id].live) {
+    set_error("invalid column id %d", id);
+    return nullptr;
+  }
+  const Column &c = ctx->cols[id];
+  if (want >= 0 && c.dtype != want) {
+    set_error("column %d (%s) has dtype %d, expected %d", id, c.name.c_str(), c.dtype, want);
+    return nullptr;
+  }
+  return &c;
+}
+
+static void default_config(vx_config *c) {
+  memset(c, 0, sizeof *c);
+  c->chunk_bytes = 64ull << 20;
+  c->n_slots = 3;
+  c->sched = VX_SCHED_IMMEDIATE;
+  c->late_mat = VX_LATE_AUTO;
+  c->zc_threshold = 0.0;
+  c->use_graphs = 0;
+  c->block_threads = 256;
+  c->blocks_per_sm = 4;
+  c->wait_timeout_ms = 60000;
+}
+
+static vx_status init_common(vx_ctx *ctx) {
+  VX_CUDA_TRY(cudaGetDevice(&ctx->device));
+  VX_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  if (!ctx->s_compute) {
+    VX_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->s_compute, cudaStreamNonBlocking));
+    ctx->own_compute = true;
+  }
+  VX_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->s_h2d, cudaStreamNonBlocking));
+  VX_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking));
+  VX_CUDA_TRY(cudaHostAlloc((void **)&ctx->h_scalars, sizeof(uint64_t) * vx_ctx::kScalars,
+                            cudaHostAllocMapped));
+  memset(ctx->h_scalars, 0, sizeof(uint64_t) * vx_ctx::kScalars);
+  VX_CUDA_TRY(cudaHostGetDevicePointer((void **)&ctx->d_scalars, ctx->h_scalars, 0));
+  ctx->arena.init(ctx->arena_base, ctx->arena_bytes);
+  default_config(&ctx->cfg);
+  return VX_OK;
+}
+
+}  // namespace vx
+
+using namespace vx;
+
+VX_API const char *vx_last_error(void) { return g_err; }
+
+VX_API vx_status vx_open(uint64_t budget, vx_ctx **out) {
+  clear_error();
+  if (!out || budget < (1u << 20)) {
+    set_error("vx_open: budget must be >= 1 MiB");
+    return VX_E_INVAL;
+  }
+  std::unique_ptr<vx_ctx> ctx(new vx_ctx());
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, budget);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("vx_open: cudaMalloc(%llu) failed: %s", (unsigned long long)budget, cudaGetErrorString(e));
+    return VX_E_NOMEM;
+  }
+  ctx->arena_base = (char *)p;
+  ctx->arena_bytes = budget;
+  ctx->own_arena = true;
+  vx_status st = init_common(ctx.get());
+  if (st != VX_OK) {
+    vx_close(ctx.release());
+    return st;
+  }
+  *out = ctx.release();
+  return VX_OK;
+}
+
+VX_API vx_status vx_open_ex(void *dev_arena, uint64_t bytes, void *stream, vx_ctx **out) {
+  clear_error();
+  if (!out || !dev_arena || bytes < (1u << 20)) {
+    set_error("vx_open_ex: need a device arena of >= 1 MiB");
+    return VX_E_INVAL;
+  }
+  std::unique_ptr<vx_ctx> ctx(new vx_ctx());
+  ctx->arena_base = (char *)dev_arena;
+  ctx->arena_bytes = bytes;
+  ctx->own_arena = false;
+  ctx->s_compute = (cudaStream_t)stream;
+  vx_status st = init_common(ctx.get());
+  if (st != VX_OK) {
+    vx_close(ctx.release());
+    return st;
+  }
+  *out = ctx.release();
+  return VX_OK;
+}
+
+VX_API vx_status vx_close(vx_ctx *ctx) {
+  if (!ctx) return VX_OK;
+  cudaSetDevice(ctx->device);
+  {
+    std::lock_guard<std::recursive_mutex> g(ctx->mu);
+    if (ctx->s_compute) cudaStreamSynchronize(ctx->s_compute);
+    if (ctx->s_h2d) cudaStreamSynchronize(ctx->s_h2d);
+    if (ctx->s_d2h) cudaStreamSynchronize(ctx->s_d2h);
+    ctx->resident.clear();
+    for (auto &c : ctx->cols)
+      if (c.live && c.we_registered) cudaHostUnregister((void *)c.host);
+    ctx->cols.clear();
+    if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
+    if (ctx->own_compute && ctx->s_compute) cudaStreamDestroy(ctx->s_compute);
+    if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
+    if (ctx->s_d2h) cudaStreamDestroy(ctx->s_d2h);
+    if (ctx->own_arena && ctx->arena_base) cudaFree(ctx->arena_base);
+  }
+  delete ctx;
+  return VX_OK;
+}
+
+VX_API vx_status vx_get_config(vx_ctx *ctx, vx_config *out) {
+  if (!ctx || !out) return VX_E_INVAL;
+  *out = ctx->cfg;
+  return VX_OK;
+}
+
+VX_API vx_status vx_set_config(vx_ctx *ctx, const vx_config *cfg) {
+  clear_error();
+  if (!ctx || !cfg) return VX_E_INVAL;
+  if (cfg->n_slots < 2 || cfg->n_slots > 16 || cfg->chunk_bytes < 4096 || cfg->block_threads < 64 ||
+      cfg->block_threads > 1024 || (cfg->block_threads & 31) || cfg->blocks_per_sm < 1 ||
+      cfg->blocks_per_sm > 32 || (cfg->sched != VX_SCHED_IMMEDIATE && cfg->sched != VX_SCHED_DAG) ||
+      cfg->wait_timeout_ms == 0 || cfg->zc_threshold < 0 || cfg->zc_threshold > 1) {
+    set_error("vx_set_config: value out of range");
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  ctx->cfg = *cfg;
+  return VX_OK;
+}
+
+VX_API vx_status vx_register_host_column(vx_ctx *ctx, const char *name, int32_t dtype, const void *host,
+                                         uint64_t n_rows, uint32_t flags, int32_t *col_id) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (!col_id || (dtype < VX_I32 || dtype > VX_U64) || (!host && n_rows) || flags != 0) {
+    set_error("vx_register_host_column: bad argument");
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  Column c;
+  c.name = name ? name : "";
+  c.dtype = dtype;
+  c.elem = dtype_size(dtype);
+  c.host = host;
+  c.n_rows = n_rows;
+  c.live = true;
+  uint64_t bytes = n_rows * c.elem;
+  if (bytes) {
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, host);
+    bool pinned = (e == cudaSuccess && at.type == cudaMemoryTypeHost);
+    cudaGetLastError();
+    if (!pinned) {
+      e = cudaHostRegister((void *)host, bytes, cudaHostRegisterMapped);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaHostRegister(%llu bytes) failed: %s", (unsigned long long)bytes, cudaGetErrorString(e));
+        return VX_E_CUDA;
+      }
+      c.we_registered = true;
+    }
+    void *dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, (void *)host, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (c.we_registered) cudaHostUnregister((void *)host);
+      set_error("cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+      return VX_E_CUDA;
+    }
+    c.dev = dp;
+  }
+  ctx->cols.push_back(c);
+  *col_id = (int32_t)ctx->cols.size() - 1;
+  return VX_OK;
+}
+
+VX_API vx_status vx_unregister_host_column(vx_ctx *ctx, int32_t col_id) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  if (!get_col(ctx, col_id, -1)) return VX_E_INVAL;
+  Column &c = ctx->cols[col_id];
+  cudaStreamSynchronize(ctx->s_compute);
+  cudaStreamSynchronize(ctx->s_h2d);
+  ctx->resident.clear();  // cached tables may refer to the column
+  if (c.we_registered) cudaHostUnregister((void *)c.host);
+  c.live = false;
+  return VX_OK;
+}
+
+VX_API vx_status vx_drop_resident(vx_ctx *ctx) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  ctx->resident.clear();
+  return VX_OK;
+}
+
+VX_API vx_status vx_last_stats(vx_ctx *ctx, vx_query_stats *out) {
+  if (!ctx || !out) return VX_E_INVAL;
+  *out = ctx->last;
+  return VX_OK;
+}
+
+// ------------------------------------------------------------------ link probe
+VX_API vx_status vx_probe_link(vx_ctx *ctx, uint64_t bytes, uint64_t chunk, double *h2d, double *d2h,
+                               double *bidir) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (!bytes || !chunk || chunk > bytes) {
+    set_error("vx_probe_link: need 0 < chunk <= bytes");
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  bytes = bytes / chunk * chunk;
+  DevBuf a, b;
+  a.arena = b.arena = &ctx->arena;
+  a.p = ctx->arena.alloc(bytes);
+  b.p = ctx->arena.alloc(bytes);
+  if (!a.p || !b.p) {
+    set_error("vx_probe_link: %llu bytes x2 do not fit the arena", (unsigned long long)bytes);
+    return VX_E_NOMEM;
+  }
+  char *hs = nullptr, *hd = nullptr;
+  VX_CUDA_TRY(cudaHostAlloc((void **)&hs, bytes, cudaHostAllocDefault));
+  cudaError_t e = cudaHostAlloc((void **)&hd, bytes, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    cudaFreeHost(hs);
+    VX_CUDA_TRY(e);
+  }
+  memset(hs, 1, bytes);
+  memset(hd, 2, bytes);
+  cudaEvent_t e0, e1, eh, ed;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventCreate(&eh);
+  cudaEventCreate(&ed);
+  double res[3] = {0, 0, 0};
+  for (int warm = 0; warm < 2; ++warm) {
+    for (int dir = 0; dir < 3; ++dir) {
+      cudaStreamSynchronize(ctx->s_h2d);
+      cudaStreamSynchronize(ctx->s_d2h);
+      cudaEventRecord(e0, ctx->s_h2d);
+      cudaStreamWaitEvent(ctx->s_d2h, e0, 0);
+      for (uint64_t off = 0; off < bytes; off += chunk) {
+        if (dir != 1) cudaMemcpyAsync((char *)a.p + off, hs + off, chunk, cudaMemcpyHostToDevice, ctx->s_h2d);
+        if (dir != 0) cudaMemcpyAsync(hd + off, (char *)b.p + off, chunk, cudaMemcpyDeviceToHost, ctx->s_d2h);
+      }
+      cudaEventRecord(ed, ctx->s_d2h);
+      cudaStreamWaitEvent(ctx->s_h2d, ed, 0);
+      cudaEventRecord(e1, ctx->s_h2d);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      res[dir] = (double)bytes * (dir == 2 ? 2 : 1) / (ms * 1e6);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(eh);
+  cudaEventDestroy(ed);
+  cudaFreeHost(hs);
+  cudaFreeHost(hd);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) {
+    set_error("vx_probe_link: %s", cudaGetErrorString(le));
+    return VX_E_CUDA;
+  }
+  if (h2d) *h2d = res[0];
+  if (d2h) *d2h = res[1];
+  if (bidir) *bidir = res[2];
+  return VX_OK;
+}

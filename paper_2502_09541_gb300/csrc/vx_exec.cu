@@ -1,0 +1,179 @@
+// Pipelined executor (Section 5.3) over a ring of staging slots.
+//
+// In cycle n the kernel of chunk n-1 runs on the compute stream while the
+// copy engine loads chunk n into a free slot and saves the output of chunk n-2
+// on the device-to-host stream.  Two schedules:
+//   VX_SCHED_IMMEDIATE — a host loop issues a copy only when it can start at
+//     once (its slot is free and the previous user of the slot has finished),
+//     following the first design principle of Section 4.3, and keeps the
+//     device-to-host queue from running ahead of the host-to-device queue
+//     (the flow-control policy of Section 4.3); it waits with a 10 us back-off
+//     and a wall-clock limit.
+//   VX_SCHED_DAG — every copy and kernel is enqueued up front with stream and
+//     event dependencies (the baseline of Section 4.2).  Only operators whose
+//     outputs stay on the device use it.
+#include <thread>
+
+#include "vx_internal.h"
+
+namespace vx {
+
+namespace {
+
+struct SlotState {
+  int64_t chunk = -1;
+  int phase = 0;  // 0 free, 1 kernel issued, 2 storing
+  cudaEvent_t ev_in = nullptr, ev_k0 = nullptr, ev_k = nullptr, ev_out = nullptr;
+};
+
+struct EventSet {
+  std::vector<SlotState> s;
+  ~EventSet() {
+    for (auto &x : s) {
+      if (x.ev_in) cudaEventDestroy(x.ev_in);
+      if (x.ev_k0) cudaEventDestroy(x.ev_k0);
+      if (x.ev_k) cudaEventDestroy(x.ev_k);
+      if (x.ev_out) cudaEventDestroy(x.ev_out);
+    }
+  }
+};
+
+vx_status issue_copies(const std::vector<CopyOp> &ops, cudaMemcpyKind kind, cudaStream_t s, uint64_t *bytes) {
+  for (const CopyOp &c : ops) {
+    if (!c.bytes) continue;
+    VX_CUDA_TRY(cudaMemcpyAsync(c.dst, c.src, c.bytes, kind, s));
+    *bytes += c.bytes;
+  }
+  return VX_OK;
+}
+
+}  // namespace
+
+vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
+  const uint64_t N = k.size();
+  if (N == 0) return VX_OK;
+  const int S = ctx->cfg.n_slots < 2 ? 2 : ctx->cfg.n_slots;
+  const uint64_t slot_bytes = (k.slot_bytes() + 255) & ~255ull;
+  DevBuf ring;
+  ring.arena = &ctx->arena;
+  ring.p = ctx->arena.alloc(slot_bytes * (uint64_t)S);
+  if (!ring.p) {
+    set_error("executor: %d slots of %llu bytes do not fit the arena (%llu of %llu bytes free)", S,
+              (unsigned long long)slot_bytes, (unsigned long long)ctx->arena.largest_free(),
+              (unsigned long long)ctx->arena.capacity());
+    return VX_E_NOMEM;
+  }
+  char *base = ring.as<char>();
+  EventSet es;
+  es.s.resize(S);
+  for (auto &x : es.s) {
+    VX_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_in, cudaEventDisableTiming));
+    VX_CUDA_TRY(cudaEventCreate(&x.ev_k0));
+    VX_CUDA_TRY(cudaEventCreate(&x.ev_k));
+    VX_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_out, cudaEventDisableTiming));
+  }
+  std::vector<CopyOp> ops;
+  const bool dag = ctx->cfg.sched == VX_SCHED_DAG && !k.has_outputs();
+
+  if (dag) {
+    for (uint64_t it = 0; it < N; ++it) {
+      SlotState &sl = es.s[it % S];
+      char *slot = base + (it % S) * slot_bytes;
+      if (it >= (uint64_t)S) VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_h2d, sl.ev_k, 0));
+      ops.clear();
+      k.inputs(it, slot, ops);
+      VX_TRY(issue_copies(ops, cudaMemcpyHostToDevice, ctx->s_h2d, &st->bytes_h2d));
+      VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
+      VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
+      VX_TRY(k.kernel(slot, it, ctx->s_compute));
+      st->kernel_launches += 1;
+      VX_CUDA_TRY(cudaEventRecord(sl.ev_k, ctx->s_compute));
+    }
+    st->chunks += N;
+    // the caller synchronises the compute stream; the h2d stream must not run
+    // ahead of the next operator's use of the arena either
+    VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_h2d, es.s[(N - 1) % S].ev_k, 0));
+    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_h2d));
+    return VX_OK;
+  }
+
+  const double deadline = now_ms() + ctx->cfg.wait_timeout_ms;
+  uint64_t next_load = 0, next_retire = 0, loads_issued = 0, stores_issued = 0;
+  const int max_loading = 2;  // chunks whose loads may be queued on the copy engine at once
+  while (next_retire < N) {
+    bool progress = false;
+    // retire in chunk order
+    while (next_retire < next_load) {
+      SlotState &sl = es.s[next_retire % S];
+      if (sl.phase == 1) {
+        cudaError_t q = cudaEventQuery(sl.ev_k);
+        if (q == cudaErrorNotReady) break;
+        VX_CUDA_TRY(q);
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k) == cudaSuccess) st->ms_kernel += ms;
+        cudaGetLastError();
+        if (k.has_outputs()) {
+          ops.clear();
+          VX_TRY(k.outputs(next_retire, base + (next_retire % S) * slot_bytes, ops));
+          VX_TRY(issue_copies(ops, cudaMemcpyDeviceToHost, ctx->s_d2h, &st->bytes_d2h));
+          VX_CUDA_TRY(cudaEventRecord(sl.ev_out, ctx->s_d2h));
+          ++stores_issued;
+          sl.phase = 2;
+        } else {
+          sl.phase = 0;
+          ++next_retire;
+        }
+        progress = true;
+      } else if (sl.phase == 2) {
+        cudaError_t q = cudaEventQuery(sl.ev_out);
+        if (q == cudaErrorNotReady) break;
+        VX_CUDA_TRY(q);
+        sl.phase = 0;
+        ++next_retire;
+        progress = true;
+      } else {
+        break;
+      }
+    }
+    // load the next chunk when its slot is free and the copy engine queue is short;
+    // stores may not run ahead of loads (flow control)
+    if (next_load < N && next_load - next_retire < (uint64_t)S && stores_issued <= loads_issued) {
+      SlotState &sl = es.s[next_load % S];
+      uint64_t loading = next_load - next_retire;
+      if (sl.phase == 0 && loading < (uint64_t)max_loading + 1) {
+        char *slot = base + (next_load % S) * slot_bytes;
+        ops.clear();
+        k.inputs(next_load, slot, ops);
+        VX_TRY(issue_copies(ops, cudaMemcpyHostToDevice, ctx->s_h2d, &st->bytes_h2d));
+        VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
+        VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
+        VX_CUDA_TRY(cudaEventRecord(sl.ev_k0, ctx->s_compute));
+        VX_TRY(k.kernel(slot, next_load, ctx->s_compute));
+        st->kernel_launches += 1;
+        VX_CUDA_TRY(cudaEventRecord(sl.ev_k, ctx->s_compute));
+        sl.chunk = (int64_t)next_load;
+        sl.phase = 1;
+        ++next_load;
+        ++loads_issued;
+        progress = true;
+      }
+    }
+    if (!progress) {
+      if (now_ms() > deadline) {
+        set_error("executor: wait limit of %u ms expired at chunk %llu of %llu", ctx->cfg.wait_timeout_ms,
+                  (unsigned long long)next_retire, (unsigned long long)N);
+        cudaStreamSynchronize(ctx->s_compute);
+        cudaStreamSynchronize(ctx->s_h2d);
+        cudaStreamSynchronize(ctx->s_d2h);
+        return VX_E_TIMEOUT;
+      }
+      std::this_thread::sleep_for(std::chrono::microseconds(10));
+    }
+  }
+  st->chunks += N;
+  VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_d2h));
+  return VX_OK;
+}
+
+}  // namespace vx

@@ -1,0 +1,874 @@
+// Star-join pipeline: dimension hash tables (build), fused chunk kernel (filter
+// -> chained probes -> group-by aggregate with zero-copy late
+// materialization), filter with ordered stream compaction, and the
+// vx_run_plan / vx_groupby / vx_filter entry points.
+//
+// Section 7.1: dimension tables are filtered and hashed on the device and kept
+// there; fact chunks stream through one fused kernel per chunk.  Section 6.3:
+// aggregate columns whose estimated selectivity is below TH are not staged;
+// the kernel reads them from mapped host memory for qualifying rows only.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "vx_internal.h"
+#include "vx_star.cuh"
+
+namespace vx {
+
+// ================================================================== device code
+
+__device__ __forceinline__ bool pred_ok(int32_t v, int32_t op, int32_t lo, int32_t hi) {
+  switch (op) {
+    case VX_BETWEEN: return lo <= v && v <= hi;
+    case VX_EQ: return v == lo;
+    case VX_NE: return v != lo;
+    case VX_LT: return v < lo;
+    case VX_LE: return v <= lo;
+    case VX_GT: return v > lo;
+    case VX_GE: return v >= lo;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t ht_hash32(int32_t k, uint32_t log2cap) {
+  return ((uint32_t)k * 0x9E3779B1u) >> (32u - log2cap);
+}
+
+// Inserts every dimension row: value = group-code contribution of the row if
+// it passes the dimension predicates, HT_FILTERED otherwise (so duplicate keys
+// are detected over the whole dimension, not only its qualifying rows).
+__global__ void ht_build_kernel(const DimBuildParams p) {
+  const uint32_t mask = (1u << p.log2cap) - 1u;
+  unsigned long long passed = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < p.rows;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int32_t key = p.key[i];
+    bool ok = true;
+    for (int q = 0; q < p.n_preds && ok; ++q) ok = pred_ok(p.attr[p.pred_attr[q]][i], p.pred_op[q], p.pred_lo[q], p.pred_hi[q]);
+    uint32_t val = HT_FILTERED;
+    if (ok) {
+      uint64_t g = 0;
+      for (int a = 0; a < p.n_attr; ++a) {
+        if (p.stride[a] == 0) continue;
+        int32_t code = p.attr[a][i];
+        if (code < 0 || code >= p.card[a]) {
+          atomicOr(p.err, ERR_RANGE);
+          code = 0;
+        }
+        g += (uint64_t)code * p.stride[a];
+      }
+      val = (uint32_t)g;
+      ++passed;
+    }
+    const unsigned long long packed = ((unsigned long long)val << 32) | (uint32_t)key;
+    uint32_t h = ht_hash32(key, p.log2cap);
+    bool done = false;
+    for (uint32_t n = 0; n <= mask; ++n) {
+      unsigned long long old = atomicCAS((unsigned long long *)&p.slots[h], HT_EMPTY, packed);
+      if (old == HT_EMPTY) { done = true; break; }
+      if ((int32_t)(uint32_t)old == key) { atomicOr(p.err, ERR_DUPKEY); done = true; break; }
+      h = (h + 1u) & mask;
+    }
+    if (!done) atomicOr(p.err, ERR_HT_FULL);
+  }
+  // passed-row count (planner's dimension selectivity)
+  for (int off = 16; off > 0; off >>= 1) passed += __shfl_down_sync(0xffffffffu, passed, off);
+  if ((threadIdx.x & 31) == 0 && passed) atomicAdd(p.passed, passed);
+}
+
+__global__ void fill_u64_kernel(uint64_t *p, uint64_t n, uint64_t v) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+__device__ __forceinline__ bool ht_lookup(const uint64_t *__restrict__ slots, uint32_t log2cap, int32_t key,
+                                          uint32_t &val) {
+  const uint32_t mask = (1u << log2cap) - 1u;
+  uint32_t h = ht_hash32(key, log2cap);
+  for (uint32_t n = 0; n <= mask; ++n) {
+    const uint64_t s = __ldg(&slots[h]);
+    const uint32_t v = (uint32_t)(s >> 32);
+    if (v == HT_EMPTY_VAL) return false;
+    if ((int32_t)(uint32_t)s == key) {
+      val = v;
+      return v != HT_FILTERED;
+    }
+    h = (h + 1u) & mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int32_t load_role(const ChunkParams &p, int r, uint64_t i) {
+  const int32_t *s = p.staged[r];
+  return s ? __ldg(&s[i]) : p.zc[r][p.row0 + i];
+}
+
+// Fused chunk kernel: per row (kRows rows per thread, strided by blockDim for
+// coalescing) — fact predicates, chained probes into the dimension tables,
+// mixed-radix group id, aggregate.  Accumulators live in shared memory when
+// the groups fit (kSmem), else in global memory.
+template <bool kSmem, int kRows>
+__global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
+  extern __shared__ unsigned long long sacc[];  // [2 * n_groups]
+  unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
+  if (kSmem) {
+    for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
+    __syncthreads();
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kRows;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x * kRows + threadIdx.x; base < p.n; base += stride) {
+    uint64_t row[kRows];
+    bool alive[kRows];
+    uint32_t g[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      row[j] = base + (uint64_t)j * blockDim.x;
+      alive[j] = row[j] < p.n;
+      g[j] = 0;
+    }
+    for (int q = 0; q < p.n_fact_preds; ++q) {
+      int32_t v[kRows];
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) v[j] = alive[j] ? load_role(p, p.fp_role[q], row[j]) : 0;
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) alive[j] = alive[j] && pred_ok(v[j], p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+    }
+    for (int d = 0; d < p.n_dims; ++d) {
+      int32_t key[kRows];
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) key[j] = alive[j] ? load_role(p, p.dim_role[d], row[j]) : 0;
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        uint32_t val = 0;
+        if (alive[j]) {
+          alive[j] = ht_lookup(p.ht[d], p.ht_log2[d], key[j], val);
+          g[j] += val;
+        }
+      }
+    }
+    for (int k = 0; k < p.n_fgk; ++k) {
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        if (!alive[j]) continue;
+        int32_t code = load_role(p, p.fgk_role[k], row[j]);
+        if (code < 0 || code >= p.fgk_card[k]) {
+          atomicOr(p.err, ERR_RANGE);
+          alive[j] = false;
+          continue;
+        }
+        g[j] += (uint32_t)code * p.fgk_stride[k];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      if (!alive[j]) continue;
+      int64_t a = p.agg_a_role >= 0 ? load_role(p, p.agg_a_role, row[j]) : 0;
+      int64_t b = p.agg_b_role >= 0 ? load_role(p, p.agg_b_role, row[j]) : 0;
+      int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
+      if (kSmem) {
+        atomicAdd(&ssum[g[j]], (unsigned long long)v);
+        atomicAdd(&scnt[g[j]], 1ull);
+      } else {
+        atomicAdd(&p.g_sum[g[j]], (unsigned long long)v);
+        atomicAdd(&p.g_cnt[g[j]], 1ull);
+      }
+    }
+  }
+  if (kSmem) {
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < p.n_groups; q += blockDim.x) {
+      if (scnt[q]) {
+        atomicAdd(&p.g_sum[q], ssum[q]);
+        atomicAdd(&p.g_cnt[q], scnt[q]);
+      }
+    }
+  }
+}
+
+// Fraction of sampled rows passing the fact predicates (planner estimate);
+// reads the sampled rows through mapped host memory.
+__global__ void sample_preds_kernel(const SampleParams p) {
+  unsigned long long c = 0;
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < p.n_samples; s += gridDim.x * blockDim.x) {
+    const uint64_t i = p.row_begin + (uint64_t)s * p.n / p.n_samples;
+    bool ok = true;
+    for (int q = 0; q < p.n_preds && ok; ++q) ok = pred_ok(p.col[q][i], p.op[q], p.lo[q], p.hi[q]);
+    c += ok;
+  }
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(p.out, c);
+}
+
+// ---- filter with ordered compaction: count per tile, scan, write ----------
+__device__ __forceinline__ bool filter_row(const FilterParams &p, uint64_t i) {
+  for (int q = 0; q < p.n_preds; ++q)
+    if (!pred_ok(__ldg(&p.col[q][i]), p.op[q], p.lo[q], p.hi[q])) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(kFilterThreads) filter_count_kernel(const FilterParams p, uint32_t *tile_cnt) {
+  const uint64_t t0 = (uint64_t)blockIdx.x * kFilterTile;
+  uint32_t c = 0;
+  for (uint32_t k = 0; k < kFilterItems; ++k) {
+    uint64_t i = t0 + (uint64_t)k * kFilterThreads + threadIdx.x;
+    if (i < p.n) c += filter_row(p, i);
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ uint32_t ws[kFilterThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int w = 0; w < kFilterThreads / 32; ++w) s += ws[w];
+    tile_cnt[blockIdx.x] = s;
+  }
+}
+
+// one block: exclusive scan of tile counts; total -> *count_out (mapped host)
+__global__ void __launch_bounds__(1024) filter_scan_kernel(const uint32_t *tile_cnt, uint32_t n_tiles,
+                                                           uint32_t *tile_off, uint64_t *count_out) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < n_tiles; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t v = i < n_tiles ? tile_cnt[i] : 0;
+    uint32_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if ((threadIdx.x & 31) >= (unsigned)off) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t w = threadIdx.x < (blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
+      for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+        if (threadIdx.x >= (unsigned)off) w += y;
+      }
+      wsum[threadIdx.x] = w;  // inclusive
+    }
+    __syncthreads();
+    uint32_t wpre = (threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0;
+    if (i < n_tiles) tile_off[i] = carry + wpre + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += wsum[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count_out = carry;
+}
+
+__global__ void __launch_bounds__(kFilterThreads) filter_write_kernel(const FilterParams p, const uint32_t *tile_off,
+                                                                      uint64_t *out) {
+  __shared__ uint32_t wcnt[kFilterThreads / 32];
+  const uint64_t t0 = (uint64_t)blockIdx.x * kFilterTile;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t running = tile_off[blockIdx.x];
+  for (uint32_t k = 0; k < kFilterItems; ++k) {
+    uint64_t i = t0 + (uint64_t)k * kFilterThreads + threadIdx.x;
+    bool keep = i < p.n && filter_row(p, i);
+    uint32_t bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (uint32_t w = 0; w < kFilterThreads / 32; ++w) {
+      uint32_t c = wcnt[w];
+      before += w < warp ? c : 0;
+      total += c;
+    }
+    if (keep) out[running + before + __popc(bal & ((1u << lane) - 1u))] = p.row0 + i;
+    running += total;
+    __syncthreads();
+  }
+}
+
+// ================================================================== host code
+
+static uint32_t ceil_log2(uint64_t v) {
+  uint32_t l = 0;
+  while ((1ull << l) < v) ++l;
+  return l;
+}
+
+static int grid_for(vx_ctx *ctx, uint64_t work_items, int threads) {
+  uint64_t want = (work_items + threads - 1) / threads;
+  uint64_t cap = (uint64_t)ctx->num_sms * (uint64_t)ctx->cfg.blocks_per_sm;
+  if (want > cap) want = cap;
+  return want < 1 ? 1 : (int)want;
+}
+
+vx_status build_dim_table(vx_ctx *ctx, const DimSpec &d, BuiltDim *out, uint32_t *d_err, uint64_t *d_passed) {
+  const uint64_t rows = d.rows;
+  uint32_t log2cap = ceil_log2(std::max<uint64_t>(2 * rows, 16));
+  if (log2cap > 31) {
+    set_error("dimension of %llu rows is too large for a 32-bit-indexed table", (unsigned long long)rows);
+    return VX_E_UNSUPPORTED;
+  }
+  out->log2cap = log2cap;
+  out->rows = rows;
+  out->buf.arena = &ctx->arena;
+  out->buf.p = ctx->arena.alloc((1ull << log2cap) * sizeof(uint64_t));
+  if (!out->buf.p) {
+    set_error("dimension hash table of %llu bytes does not fit the arena", (unsigned long long)(8ull << log2cap));
+    return VX_E_NOMEM;
+  }
+  cudaStream_t s = ctx->s_compute;
+  uint64_t cap = 1ull << log2cap;
+  fill_u64_kernel<<<grid_for(ctx, cap, 256), 256, 0, s>>>(out->buf.as<uint64_t>(), cap, HT_EMPTY);
+  VX_CUDA_TRY(cudaGetLastError());
+  DimBuildParams bp{};
+  bp.key = d.key;
+  bp.rows = rows;
+  bp.n_attr = d.n_attr;
+  for (int a = 0; a < d.n_attr; ++a) {
+    bp.attr[a] = d.attr[a];
+    bp.stride[a] = d.stride[a];
+    bp.card[a] = d.card[a];
+  }
+  bp.n_preds = d.n_preds;
+  for (int q = 0; q < d.n_preds; ++q) {
+    bp.pred_attr[q] = d.pred_attr[q];
+    bp.pred_op[q] = d.pred_op[q];
+    bp.pred_lo[q] = d.pred_lo[q];
+    bp.pred_hi[q] = d.pred_hi[q];
+  }
+  bp.slots = out->buf.as<uint64_t>();
+  bp.log2cap = log2cap;
+  bp.err = d_err;
+  bp.passed = (unsigned long long *)d_passed;
+  if (rows) {
+    ht_build_kernel<<<grid_for(ctx, rows, 256), 256, 0, s>>>(bp);
+    VX_CUDA_TRY(cudaGetLastError());
+  }
+  return VX_OK;
+}
+
+vx_status check_err_word(vx_ctx *ctx, const uint32_t *d_err) {
+  uint32_t e = 0;
+  VX_CUDA_TRY(cudaMemcpyAsync(&e, d_err, 4, cudaMemcpyDeviceToHost, ctx->s_compute));
+  VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  if (e & ERR_DUPKEY) {
+    set_error("duplicate key on the build side");
+    return VX_E_DUPKEY;
+  }
+  if (e & ERR_RANGE) {
+    set_error("group-key code outside [0, card)");
+    return VX_E_RANGE;
+  }
+  if (e & ERR_HT_FULL) {
+    set_error("hash table full");
+    return VX_E_NOMEM;
+  }
+  return VX_OK;
+}
+
+// ------------------------------------------------------------------ star ExKernel
+struct StarExKernel : ExKernel {
+  vx_ctx *ctx;
+  ChunkParams proto{};
+  std::vector<const Column *> staged_cols;  // staged role r -> column
+  std::vector<int> staged_role;             // index of role in proto.staged
+  uint64_t row_begin = 0, n_rows = 0, chunk_rows = 0;
+  bool smem = true;
+  size_t smem_bytes = 0;
+  int grid = 1;
+
+  uint64_t size() override { return (n_rows + chunk_rows - 1) / chunk_rows; }
+  uint64_t slot_bytes() override { return (uint64_t)staged_cols.size() * chunk_rows * 4 + 256 * staged_cols.size(); }
+  uint64_t col_off(size_t k) const { return k * ((chunk_rows * 4 + 255) & ~255ull); }
+  uint64_t rows_of(uint64_t it) const { return std::min(chunk_rows, n_rows - it * chunk_rows); }
+
+  void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) override {
+    const uint64_t r0 = row_begin + it * chunk_rows, n = rows_of(it);
+    for (size_t k = 0; k < staged_cols.size(); ++k)
+      h2d.push_back({(const char *)staged_cols[k]->host + r0 * 4, slot + col_off(k), n * 4});
+  }
+  vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
+    ChunkParams p = proto;
+    p.row0 = row_begin + it * chunk_rows;
+    p.n = rows_of(it);
+    for (size_t k = 0; k < staged_cols.size(); ++k) p.staged[staged_role[k]] = (const int32_t *)(slot + col_off(k));
+    int threads = ctx->cfg.block_threads > 256 ? 256 : ctx->cfg.block_threads;
+    int g = grid_for(ctx, (p.n + 3) / 4, threads);
+    if (smem) {
+      static bool attr_set = false;
+      if (!attr_set) {
+        VX_CUDA_TRY(cudaFuncSetAttribute(star_chunk_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(16 * kSmemGroups)));
+        attr_set = true;
+      }
+      star_chunk_kernel<true, 4><<<g, threads, smem_bytes, s>>>(p);
+    }
+    else
+      star_chunk_kernel<false, 4><<<g, threads, 0, s>>>(p);
+    VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+  }
+};
+
+// planner: resolves a plan into dimension specs and chunk-kernel parameters
+vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_resident) {
+  const double t_start = now_ms();
+  vx_query_stats qs{};
+  if (!plan || !out) {
+    set_error("vx_run_plan: null argument");
+    return VX_E_INVAL;
+  }
+  if (plan->n_dims < 0 || plan->n_dims > VX_MAX_DIMS || plan->n_fact_preds < 0 ||
+      plan->n_fact_preds > VX_MAX_PREDS || plan->n_group_keys < 0 || plan->n_group_keys > VX_MAX_GKEYS ||
+      plan->agg_op < VX_AGG_COUNT || plan->agg_op > VX_AGG_SUB) {
+    set_error("vx_run_plan: counts out of range");
+    return VX_E_INVAL;
+  }
+  // ---- fact columns and roles
+  std::vector<int32_t> role_col;  // role -> column id
+  auto role_of = [&](int32_t col) -> int {
+    for (size_t r = 0; r < role_col.size(); ++r)
+      if (role_col[r] == col) return (int)r;
+    role_col.push_back(col);
+    return (int)role_col.size() - 1;
+  };
+  uint64_t n_fact = UINT64_MAX;
+  auto fact_col = [&](int32_t id) -> const Column * {
+    const Column *c = get_col(ctx, id, VX_I32);
+    if (c) {
+      if (n_fact == UINT64_MAX) n_fact = c->n_rows;
+      if (c->n_rows != n_fact) {
+        set_error("fact columns differ in length");
+        return nullptr;
+      }
+    }
+    return c;
+  };
+  ChunkParams P{};
+  for (int r = 0; r < kMaxRoles; ++r) {
+    P.staged[r] = nullptr;
+    P.zc[r] = nullptr;
+  }
+  P.n_fact_preds = plan->n_fact_preds;
+  for (int q = 0; q < plan->n_fact_preds; ++q) {
+    const vx_pred &fp = plan->fact_preds[q];
+    if (!fact_col(fp.col)) return VX_E_INVAL;
+    if (fp.op < VX_BETWEEN || fp.op > VX_GE) {
+      set_error("bad predicate op %d", fp.op);
+      return VX_E_INVAL;
+    }
+    P.fp_role[q] = role_of(fp.col);
+    P.fp_op[q] = fp.op;
+    P.fp_lo[q] = fp.lo;
+    P.fp_hi[q] = fp.hi;
+  }
+  // group strides: first key most significant
+  uint64_t G = 1;
+  uint64_t stride_of[VX_MAX_GKEYS];
+  for (int k = plan->n_group_keys - 1; k >= 0; --k) {
+    const vx_plan_gkey &gk = plan->group_keys[k];
+    if (gk.card < 1) {
+      set_error("group key cardinality must be >= 1");
+      return VX_E_INVAL;
+    }
+    stride_of[k] = G;
+    G *= (uint64_t)gk.card;
+    if (G > (1ull << 26)) {
+      set_error("too many groups (%llu)", (unsigned long long)G);
+      return VX_E_UNSUPPORTED;
+    }
+  }
+  P.n_groups = (uint32_t)G;
+  // dimensions
+  std::vector<DimSpec> dspec(plan->n_dims);
+  P.n_dims = plan->n_dims;
+  for (int d = 0; d < plan->n_dims; ++d) {
+    const vx_plan_dim &pd = plan->dims[d];
+    const Column *kc = get_col(ctx, pd.key_col, VX_I32);
+    if (!kc || !fact_col(pd.fact_fk_col)) return VX_E_INVAL;
+    if (pd.n_attr < 0 || pd.n_attr > 4 || pd.n_preds < 0 || pd.n_preds > 4) {
+      set_error("dimension %d: attribute/predicate count out of range", d);
+      return VX_E_INVAL;
+    }
+    DimSpec &ds = dspec[d];
+    ds.key = (const int32_t *)kc->dev;
+    ds.key_col = pd.key_col;
+    ds.rows = kc->n_rows;
+    ds.n_attr = pd.n_attr;
+    for (int a = 0; a < pd.n_attr; ++a) {
+      const Column *ac = get_col(ctx, pd.attr_col[a], VX_I32);
+      if (!ac || ac->n_rows != kc->n_rows) {
+        set_error("dimension %d attribute %d: bad column", d, a);
+        return VX_E_INVAL;
+      }
+      ds.attr[a] = (const int32_t *)ac->dev;
+      ds.attr_col[a] = pd.attr_col[a];
+      ds.stride[a] = 0;
+      ds.card[a] = 0;
+    }
+    ds.n_preds = pd.n_preds;
+    for (int q = 0; q < pd.n_preds; ++q) {
+      if (pd.pred_attr[q] < 0 || pd.pred_attr[q] >= pd.n_attr || pd.pred_op[q] < 0 || pd.pred_op[q] > VX_GE) {
+        set_error("dimension %d predicate %d: bad attribute or op", d, q);
+        return VX_E_INVAL;
+      }
+      ds.pred_attr[q] = pd.pred_attr[q];
+      ds.pred_op[q] = pd.pred_op[q];
+      ds.pred_lo[q] = pd.pred_lo[q];
+      ds.pred_hi[q] = pd.pred_hi[q];
+    }
+    P.dim_role[d] = role_of(pd.fact_fk_col);
+  }
+  P.n_fgk = 0;
+  for (int k = 0; k < plan->n_group_keys; ++k) {
+    const vx_plan_gkey &gk = plan->group_keys[k];
+    if (gk.dim >= 0) {
+      if (gk.dim >= plan->n_dims || gk.attr < 0 || gk.attr >= dspec[gk.dim].n_attr) {
+        set_error("group key %d: bad dimension attribute", k);
+        return VX_E_INVAL;
+      }
+      if (dspec[gk.dim].stride[gk.attr]) {
+        set_error("group key %d repeats an attribute", k);
+        return VX_E_INVAL;
+      }
+      dspec[gk.dim].stride[gk.attr] = (uint32_t)stride_of[k];
+      dspec[gk.dim].card[gk.attr] = gk.card;
+    } else {
+      if (!fact_col(gk.fact_col)) return VX_E_INVAL;
+      P.fgk_role[P.n_fgk] = role_of(gk.fact_col);
+      P.fgk_card[P.n_fgk] = gk.card;
+      P.fgk_stride[P.n_fgk] = (uint32_t)stride_of[k];
+      ++P.n_fgk;
+    }
+  }
+  if (n_fact == UINT64_MAX) {
+    set_error("plan references no fact column");
+    return VX_E_INVAL;
+  }
+  const uint64_t row_begin = std::min(plan->row_begin, n_fact);
+  const uint64_t row_end = plan->row_end == 0 ? n_fact : std::min(plan->row_end, n_fact);
+  const uint64_t n_rows = row_end > row_begin ? row_end - row_begin : 0;
+  const size_t n_row_roles = role_col.size();  // roles needed for every row
+  // aggregate columns
+  P.agg_op = plan->agg_op;
+  P.agg_a_role = P.agg_b_role = -1;
+  int agg_cols[2] = {plan->agg_op == VX_AGG_COUNT ? -1 : plan->agg_a,
+                     (plan->agg_op == VX_AGG_MUL || plan->agg_op == VX_AGG_SUB) ? plan->agg_b : -1};
+  for (int j = 0; j < 2; ++j)
+    if (agg_cols[j] >= 0 && !fact_col(agg_cols[j])) return VX_E_INVAL;
+
+  // ---- device scratch: error word + counters
+  DevBuf scratch;
+  scratch.arena = &ctx->arena;
+  scratch.p = ctx->arena.alloc(256 + 16 * 8);
+  if (!scratch.p) {
+    set_error("arena exhausted");
+    return VX_E_NOMEM;
+  }
+  uint32_t *d_err = scratch.as<uint32_t>();
+  uint64_t *d_cnt = (uint64_t *)(scratch.as<char>() + 256);
+  VX_CUDA_TRY(cudaMemsetAsync(scratch.p, 0, 256 + 16 * 8, ctx->s_compute));
+
+  // ---- dimension tables (Section 7.1: filtered, hashed, kept on the device)
+  std::vector<std::shared_ptr<ResidentHT>> tables(plan->n_dims);
+  for (int d = 0; d < plan->n_dims; ++d) {
+    std::string sig = dim_signature(dspec[d]);
+    auto it = use_resident ? ctx->resident.find(sig) : ctx->resident.end();
+    if (it != ctx->resident.end()) {
+      tables[d] = it->second;
+      continue;
+    }
+    auto t = std::make_shared<ResidentHT>();
+    VX_TRY(build_dim_table(ctx, dspec[d], &t->dim, d_err, d_cnt + d));
+    tables[d] = t;
+  }
+  {
+    uint64_t passed[VX_MAX_DIMS] = {0};
+    VX_CUDA_TRY(cudaMemcpyAsync(passed, d_cnt, 8 * VX_MAX_DIMS, cudaMemcpyDeviceToHost, ctx->s_compute));
+    VX_TRY(check_err_word(ctx, d_err));
+    for (int d = 0; d < plan->n_dims; ++d) {
+      if (!tables[d]->built) {
+        tables[d]->dim.passed = passed[d];
+        tables[d]->built = true;
+        if (use_resident) ctx->resident[dim_signature(dspec[d])] = tables[d];
+      }
+      P.ht[d] = tables[d]->dim.buf.as<uint64_t>();
+      P.ht_log2[d] = tables[d]->dim.log2cap;
+    }
+  }
+  // ---- selectivity estimate: dimension pass fractions x sampled fact predicates
+  double est = 1.0;
+  for (int d = 0; d < plan->n_dims; ++d)
+    est *= tables[d]->dim.rows ? (double)tables[d]->dim.passed / (double)tables[d]->dim.rows : 0.0;
+  if (plan->n_fact_preds > 0 && n_rows > 0) {
+    SampleParams sp{};
+    sp.n_preds = plan->n_fact_preds;
+    for (int q = 0; q < plan->n_fact_preds; ++q) {
+      sp.col[q] = (const int32_t *)ctx->cols[plan->fact_preds[q].col].dev;
+      sp.op[q] = plan->fact_preds[q].op;
+      sp.lo[q] = plan->fact_preds[q].lo;
+      sp.hi[q] = plan->fact_preds[q].hi;
+    }
+    sp.row_begin = row_begin;
+    sp.n = n_rows;
+    sp.n_samples = (uint32_t)std::min<uint64_t>(n_rows, 8192);
+    sp.out = (unsigned long long *)(d_cnt + 15);
+    sample_preds_kernel<<<16, 256, 0, ctx->s_compute>>>(sp);
+    VX_CUDA_TRY(cudaGetLastError());
+    uint64_t hit = 0;
+    VX_CUDA_TRY(cudaMemcpyAsync(&hit, d_cnt + 15, 8, cudaMemcpyDeviceToHost, ctx->s_compute));
+    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+    est *= (double)hit / (double)sp.n_samples;
+  }
+  qs.est_selectivity = est;
+  const double TH = ctx->cfg.zc_threshold > 0 ? ctx->cfg.zc_threshold : kDefaultZeroCopyTH;
+  bool late = plan->late_mat == VX_LATE_FORCE_LATE || (plan->late_mat == VX_LATE_AUTO && est < TH);
+  // aggregate roles: a column already staged for the row logic stays staged
+  uint32_t late_mask = 0;
+  for (int j = 0; j < 2; ++j) {
+    if (agg_cols[j] < 0) continue;
+    size_t before = role_col.size();
+    int r = role_of(agg_cols[j]);
+    bool is_new = role_col.size() > before;
+    if (j == 0) P.agg_a_role = r; else P.agg_b_role = r;
+    if (is_new && late) late_mask |= 1u << j;
+  }
+  if (role_col.size() > (size_t)kMaxRoles) {
+    set_error("plan references %zu fact columns; at most %d", role_col.size(), kMaxRoles);
+    return VX_E_UNSUPPORTED;
+  }
+  // ---- accumulators
+  DevBuf acc;
+  acc.arena = &ctx->arena;
+  acc.p = ctx->arena.alloc(16 * G);
+  if (!acc.p) {
+    set_error("group accumulators do not fit the arena");
+    return VX_E_NOMEM;
+  }
+  P.g_sum = acc.as<unsigned long long>();
+  P.g_cnt = P.g_sum + G;
+  P.err = d_err;
+  VX_CUDA_TRY(cudaMemsetAsync(acc.p, 0, 16 * G, ctx->s_compute));
+
+  StarExKernel ek;
+  ek.ctx = ctx;
+  ek.row_begin = row_begin;
+  ek.n_rows = n_rows;
+  for (size_t r = 0; r < role_col.size(); ++r) {
+    const Column *c = &ctx->cols[role_col[r]];
+    bool is_late = false;
+    if ((int)r == P.agg_a_role && (late_mask & 1u)) is_late = true;
+    if ((int)r == P.agg_b_role && (late_mask & 2u)) is_late = true;
+    if (is_late) {
+      P.zc[r] = (const int32_t *)c->dev;
+    } else {
+      ek.staged_cols.push_back(c);
+      ek.staged_role.push_back((int)r);
+    }
+  }
+  (void)n_row_roles;
+  // rows per chunk follow from all referenced columns, so the chunking does not
+  // depend on the late/early decision
+  const uint64_t per_row = 4 * std::max<size_t>(1, role_col.size());
+  uint64_t cr = ctx->cfg.chunk_bytes / per_row;
+  cr = cr / 1024 * 1024;
+  if (cr < 1024) cr = 1024;
+  if (cr > n_rows) cr = std::max<uint64_t>(n_rows, 1);
+  ek.chunk_rows = cr;
+  ek.smem = G <= kSmemGroups;
+  ek.smem_bytes = ek.smem ? 16 * G : 0;
+  ek.proto = P;
+
+  ExecStats es;
+  if (n_rows) VX_TRY(run_pipeline(ctx, ek, &es));
+  VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  VX_TRY(check_err_word(ctx, d_err));
+
+  // ---- results: non-empty groups in ascending id
+  std::vector<uint64_t> h(2 * G);
+  VX_CUDA_TRY(cudaMemcpy(h.data(), acc.p, 16 * G, cudaMemcpyDeviceToHost));
+  uint64_t n_out = 0, surv = 0;
+  vx_status st = VX_OK;
+  for (uint64_t g = 0; g < G; ++g) {
+    uint64_t c = h[G + g];
+    if (!c) continue;
+    surv += c;
+    if (n_out < out->cap) {
+      if (out->gid) out->gid[n_out] = g;
+      if (out->sum) out->sum[n_out] = (int64_t)h[g];
+      if (out->cnt) out->cnt[n_out] = c;
+    }
+    ++n_out;
+  }
+  out->n_out = n_out;
+  if (n_out > out->cap) {
+    set_error("result has %llu groups; capacity %llu", (unsigned long long)n_out, (unsigned long long)out->cap);
+    st = VX_E_CAPACITY;
+  }
+  qs.rows = n_rows;
+  qs.survivors = surv;
+  qs.chunks = es.chunks;
+  qs.bytes_h2d = es.bytes_h2d;
+  qs.bytes_d2h = es.bytes_d2h + 16 * G;
+  qs.late_mask = late_mask;
+  qs.bytes_zero_copy = surv * 64ull * (uint64_t)__builtin_popcount(late_mask);
+  qs.bytes_logical = n_rows * 4ull * role_col.size();
+  qs.ms_kernel = es.ms_kernel;
+  qs.kernel_launches = es.kernel_launches;
+  qs.ms_total = now_ms() - t_start;
+  out->stats = qs;
+  ctx->last = qs;
+  return st;
+}
+
+// ------------------------------------------------------------------ filter ExKernel
+struct FilterExKernel : ExKernel {
+  vx_ctx *ctx;
+  FilterParams proto{};
+  std::vector<const Column *> cols;
+  uint64_t row_begin = 0, n_rows = 0, chunk_rows = 0;
+  uint64_t *out_rows = nullptr, cap = 0, written = 0, total = 0;
+  int S = 2;
+
+  uint64_t size() override { return (n_rows + chunk_rows - 1) / chunk_rows; }
+  uint64_t in_bytes() const { return cols.size() * ((chunk_rows * 4 + 255) & ~255ull); }
+  uint64_t n_tiles() const { return (chunk_rows + kFilterTile - 1) / kFilterTile; }
+  uint64_t tile_bytes() const { return ((n_tiles() * 4 + 255) & ~255ull); }
+  uint64_t slot_bytes() override { return in_bytes() + 2 * tile_bytes() + chunk_rows * 8; }
+  uint64_t rows_of(uint64_t it) const { return std::min(chunk_rows, n_rows - it * chunk_rows); }
+  void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) override {
+    const uint64_t r0 = row_begin + it * chunk_rows, n = rows_of(it);
+    for (size_t k = 0; k < cols.size(); ++k)
+      h2d.push_back({(const char *)cols[k]->host + r0 * 4, slot + k * ((chunk_rows * 4 + 255) & ~255ull), n * 4});
+  }
+  vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
+    FilterParams p = proto;
+    p.row0 = row_begin + it * chunk_rows;
+    p.n = rows_of(it);
+    for (int q = 0; q < p.n_preds; ++q)
+      p.col[q] = (const int32_t *)(slot + (uint64_t)p.colidx[q] * ((chunk_rows * 4 + 255) & ~255ull));
+    uint32_t *tcnt = (uint32_t *)(slot + in_bytes());
+    uint32_t *toff = (uint32_t *)(slot + in_bytes() + tile_bytes());
+    uint64_t *outb = (uint64_t *)(slot + in_bytes() + 2 * tile_bytes());
+    uint32_t nt = (uint32_t)((p.n + kFilterTile - 1) / kFilterTile);
+    filter_count_kernel<<<nt, kFilterThreads, 0, s>>>(p, tcnt);
+    filter_scan_kernel<<<1, 1024, 0, s>>>(tcnt, nt, toff, ctx->d_scalars + 8 + (it % S));
+    filter_write_kernel<<<nt, kFilterThreads, 0, s>>>(p, toff, outb);
+    VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+  }
+  bool has_outputs() override { return true; }
+  vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
+    uint64_t c = ((volatile uint64_t *)ctx->h_scalars)[8 + (it % S)];
+    uint64_t *outb = (uint64_t *)(slot + in_bytes() + 2 * tile_bytes());
+    uint64_t fit = written < cap ? std::min(c, cap - written) : 0;
+    if (fit && out_rows) d2h.push_back({outb, out_rows + written, fit * 8});
+    written += fit;
+    total += c;
+    return VX_OK;
+  }
+};
+
+}  // namespace vx
+
+using namespace vx;
+
+VX_API vx_status vx_run_plan(vx_ctx *ctx, const vx_plan *plan, vx_result *out) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  return run_star(ctx, plan, out, true);
+}
+
+VX_API vx_status vx_groupby(vx_ctx *ctx, const vx_plan_gkey *keys, int32_t n_keys, int32_t agg_op, int32_t agg_a,
+                            int32_t agg_b, const vx_pred *preds, int32_t n_preds, vx_result *out) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (n_keys < 0 || n_keys > VX_MAX_GKEYS || n_preds < 0 || n_preds > VX_MAX_PREDS || (n_keys && !keys) ||
+      (n_preds && !preds)) {
+    set_error("vx_groupby: bad argument");
+    return VX_E_INVAL;
+  }
+  vx_plan p{};
+  p.n_dims = 0;
+  p.n_fact_preds = n_preds;
+  for (int i = 0; i < n_preds; ++i) p.fact_preds[i] = preds[i];
+  p.n_group_keys = n_keys;
+  for (int i = 0; i < n_keys; ++i) {
+    p.group_keys[i] = keys[i];
+    if (keys[i].dim != -1) {
+      set_error("vx_groupby: keys must be fact columns (dim = -1)");
+      return VX_E_INVAL;
+    }
+  }
+  p.agg_op = agg_op;
+  p.agg_a = agg_a;
+  p.agg_b = agg_b;
+  p.late_mat = VX_LATE_FORCE_EARLY;
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  return run_star(ctx, &p, out, false);
+}
+
+VX_API vx_status vx_filter(vx_ctx *ctx, const vx_pred *preds, int32_t n_preds, uint64_t row_begin, uint64_t row_end,
+                           uint64_t *out_rows, uint64_t cap, uint64_t *out_count) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (n_preds < 1 || n_preds > VX_MAX_PREDS || !preds || !out_count) {
+    set_error("vx_filter: need 1..%d predicates and out_count", VX_MAX_PREDS);
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const double t0 = now_ms();
+  FilterExKernel fk;
+  fk.ctx = ctx;
+  uint64_t n = UINT64_MAX;
+  for (int q = 0; q < n_preds; ++q) {
+    const Column *c = get_col(ctx, preds[q].col, VX_I32);
+    if (!c) return VX_E_INVAL;
+    if (n == UINT64_MAX) n = c->n_rows;
+    if (c->n_rows != n || preds[q].op < VX_BETWEEN || preds[q].op > VX_GE) {
+      set_error("vx_filter: columns differ in length or bad op");
+      return VX_E_INVAL;
+    }
+    int k = -1;
+    for (size_t j = 0; j < fk.cols.size(); ++j)
+      if (fk.cols[j] == c) k = (int)j;
+    if (k < 0) {
+      fk.cols.push_back(c);
+      k = (int)fk.cols.size() - 1;
+    }
+    fk.proto.op[q] = preds[q].op;
+    fk.proto.lo[q] = preds[q].lo;
+    fk.proto.hi[q] = preds[q].hi;
+    fk.proto.colidx[q] = k;
+  }
+  fk.proto.n_preds = n_preds;
+  const uint64_t rb = std::min(row_begin, n);
+  const uint64_t re = row_end == 0 ? n : std::min(row_end, n);
+  fk.row_begin = rb;
+  fk.n_rows = re > rb ? re - rb : 0;
+  uint64_t cr = ctx->cfg.chunk_bytes / (4 * fk.cols.size());
+  cr = std::max<uint64_t>(cr / kFilterTile * kFilterTile, kFilterTile);
+  cr = std::min<uint64_t>(cr, (uint64_t)kFilterTile * 65535);
+  fk.chunk_rows = cr;
+  fk.out_rows = out_rows;
+  fk.cap = out_rows ? cap : 0;
+  fk.S = ctx->cfg.n_slots;
+  ExecStats es;
+  if (fk.n_rows) VX_TRY(run_pipeline(ctx, fk, &es));
+  *out_count = fk.total;
+  vx_query_stats qs{};
+  qs.rows = fk.n_rows;
+  qs.survivors = fk.total;
+  qs.chunks = es.chunks;
+  qs.bytes_h2d = es.bytes_h2d;
+  qs.bytes_d2h = es.bytes_d2h;
+  qs.bytes_logical = fk.n_rows * 4 * fk.cols.size();
+  qs.ms_kernel = es.ms_kernel;
+  qs.kernel_launches = es.kernel_launches * 3;
+  qs.ms_total = now_ms() - t0;
+  ctx->last = qs;
+  if (out_rows && fk.total > cap) {
+    set_error("vx_filter: %llu rows qualify; capacity %llu", (unsigned long long)fk.total, (unsigned long long)cap);
+    return VX_E_CAPACITY;
+  }
+  return VX_OK;
+}

@@ -1,0 +1,120 @@
+// Parameter blocks and constants of the star-join / filter kernels.
+#pragma once
+#include <cstdint>
+#include <memory>
+#include <string>
+
+#include "vx_internal.h"
+
+namespace vx {
+
+// open-addressing slot: (value << 32) | uint32(key); value 0xFFFFFFFF = empty,
+// 0xFFFFFFFE = key present but the row fails the dimension predicates
+constexpr uint32_t HT_EMPTY_VAL = 0xFFFFFFFFu;
+constexpr uint32_t HT_FILTERED = 0xFFFFFFFEu;
+constexpr unsigned long long HT_EMPTY = 0xFFFFFFFF00000000ull;
+
+constexpr int kMaxRoles = 12;        // distinct fact columns a plan may reference
+constexpr uint32_t kSmemGroups = 4096;  // groups accumulated in shared memory
+// Zero-copy threshold for 4-byte columns on one host link: TH = (E / G) *
+// (B_zc / B_ce) (Section 6.3, generalised) with a 64-byte link granule and
+// equal zero-copy and copy-engine bandwidth.
+constexpr double kDefaultZeroCopyTH = 4.0 / 64.0;
+
+constexpr int kFilterThreads = 256;
+constexpr int kFilterItems = 8;
+constexpr int kFilterTile = kFilterThreads * kFilterItems;
+
+struct DimSpec {
+  const int32_t *key = nullptr;
+  int32_t key_col = -1;
+  uint64_t rows = 0;
+  int n_attr = 0;
+  const int32_t *attr[4] = {};
+  int32_t attr_col[4] = {-1, -1, -1, -1};
+  uint32_t stride[4] = {};
+  int32_t card[4] = {};
+  int n_preds = 0;
+  int32_t pred_attr[4] = {}, pred_op[4] = {}, pred_lo[4] = {}, pred_hi[4] = {};
+};
+
+struct BuiltDim {
+  DevBuf buf;
+  uint32_t log2cap = 0;
+  uint64_t rows = 0, passed = 0;
+};
+
+struct ResidentHT {
+  BuiltDim dim;
+  bool built = false;
+};
+
+inline std::string dim_signature(const DimSpec &d) {
+  std::string s = "k" + std::to_string(d.key_col) + ":" + std::to_string(d.rows);
+  for (int a = 0; a < d.n_attr; ++a)
+    s += "|a" + std::to_string(d.attr_col[a]) + "s" + std::to_string(d.stride[a]) + "c" + std::to_string(d.card[a]);
+  for (int q = 0; q < d.n_preds; ++q)
+    s += "|p" + std::to_string(d.pred_attr[q]) + "o" + std::to_string(d.pred_op[q]) + "l" +
+         std::to_string(d.pred_lo[q]) + "h" + std::to_string(d.pred_hi[q]);
+  return s;
+}
+
+struct DimBuildParams {
+  const int32_t *key;
+  uint64_t rows;
+  int n_attr;
+  const int32_t *attr[4];
+  uint32_t stride[4];
+  int32_t card[4];
+  int n_preds;
+  int32_t pred_attr[4], pred_op[4], pred_lo[4], pred_hi[4];
+  uint64_t *slots;
+  uint32_t log2cap;
+  uint32_t *err;
+  unsigned long long *passed;
+};
+
+struct ChunkParams {
+  const int32_t *staged[kMaxRoles];  // role -> column slice in the staging slot (chunk-local rows)
+  const int32_t *zc[kMaxRoles];      // role -> mapped host column (global rows), for late roles
+  int n_fact_preds;
+  int8_t fp_role[VX_MAX_PREDS];
+  int32_t fp_op[VX_MAX_PREDS], fp_lo[VX_MAX_PREDS], fp_hi[VX_MAX_PREDS];
+  int n_dims;
+  int8_t dim_role[VX_MAX_DIMS];
+  const uint64_t *ht[VX_MAX_DIMS];
+  uint32_t ht_log2[VX_MAX_DIMS];
+  int n_fgk;
+  int8_t fgk_role[VX_MAX_GKEYS];
+  int32_t fgk_card[VX_MAX_GKEYS];
+  uint32_t fgk_stride[VX_MAX_GKEYS];
+  int agg_op;
+  int8_t agg_a_role, agg_b_role;
+  uint32_t n_groups;
+  unsigned long long *g_sum, *g_cnt;
+  uint32_t *err;
+  uint64_t row0, n;
+};
+
+struct SampleParams {
+  int n_preds;
+  const int32_t *col[VX_MAX_PREDS];
+  int32_t op[VX_MAX_PREDS], lo[VX_MAX_PREDS], hi[VX_MAX_PREDS];
+  uint64_t row_begin, n;
+  uint32_t n_samples;
+  unsigned long long *out;
+};
+
+struct FilterParams {
+  int n_preds;
+  const int32_t *col[VX_MAX_PREDS];
+  int32_t colidx[VX_MAX_PREDS];
+  int32_t op[VX_MAX_PREDS], lo[VX_MAX_PREDS], hi[VX_MAX_PREDS];
+  uint64_t row0, n;
+};
+
+vx_status build_dim_table(vx_ctx *ctx, const DimSpec &d, BuiltDim *out, uint32_t *d_err, uint64_t *d_passed);
+vx_status check_err_word(vx_ctx *ctx, const uint32_t *d_err);
+vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_resident);
+
+}  // namespace vx
