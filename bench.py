@@ -134,9 +134,16 @@ def traffic_per_row():
     return None
 
 
-def make_data(rows):
+def make_data(rows, pinned=False):
+    """Fact columns (optionally in page-locked host memory allocated by
+    PyTorch, the 'pinned host memory' the workload holds its table in) and
+    the four dimensions."""
     import datagen as G
-    fact = G.star_fact(rows)
+    out = None
+    if pinned:
+        import torch
+        out = {c: torch.empty(rows, dtype=torch.int32, pin_memory=True).numpy() for c in G.STAR_FACT_COLS}
+    fact = G.star_fact(rows, out=out)
     dims = G.star_dims(0)
     return fact, dims
 
@@ -200,7 +207,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     vx.load()
     t_gen = time.perf_counter()
-    fact, dims = make_data(args.rows)
+    fact, dims = make_data(args.rows, pinned=True)
     t_gen = time.perf_counter() - t_gen
 
     budget = int(args.budget_gb * (1 << 30))

@@ -220,6 +220,86 @@ vx_status vx_drop_resident(vx_ctx *ctx);
 /* Statistics of the last completed call on this context. */
 vx_status vx_last_stats(vx_ctx *ctx, vx_query_stats *out);
 
+/* ---------------------------------------------------------------- sort */
+enum { VX_PART_SAMPLE = 0, VX_PART_LEARNED_PL = 1, VX_PART_LEARNED_MLP = 2 };
+
+typedef struct {
+  int32_t partitioner;        /* VX_PART_*: how the range partition's splitters are chosen */
+  int32_t n_partitions;       /* 0 = smallest count whose expected partition fits a slot; <= 256 */
+  uint64_t seed;              /* sample positions */
+  uint64_t sample_size;       /* keys sampled for the splitters (0 = 1 Mi) */
+  uint32_t mlp_steps;         /* Adam steps of the CDF MLP (0 = 300) */
+  uint32_t reserved;
+  void *host_scratch;         /* optional host memory of >= 12 * n bytes for the partitioned
+                                 intermediate (else allocated for the call) */
+  uint64_t host_scratch_bytes;
+  uint64_t max_slot_pairs;    /* optional cap on the pairs per staging slot (0 = from the arena) */
+  uint64_t *splitters_out;    /* optional: receives the P-1 top-level splitters */
+} vx_sort_opts;
+
+typedef struct {
+  uint32_t n_partitions;
+  uint32_t passthrough_partitions; /* single-key partitions copied through unsorted */
+  uint32_t overflow_retries;       /* multi-key partitions above the slot, sorted recursively */
+  uint32_t reserved;
+  uint64_t max_partition, min_partition, slot_pairs;
+  double imbalance;                /* largest partition / mean partition */
+  double ms_sample, ms_train, ms_partition, ms_sort, ms_total;
+  uint64_t bytes_h2d, bytes_d2h, kernel_launches;
+} vx_sort_stats;
+
+/* Out-of-core sort of (uint64 key, uint32 row id) pairs held in two registered
+ * host columns (Section 6.1 sorts 64-bit integers larger than device memory).
+ * The output is the stable sort by key (equal keys keep input order) written
+ * to out_keys/out_rowids (n elements each, caller-owned host memory).
+ * Pass 1 range-partitions the input chunk by chunk into a host intermediate
+ * with per-chunk boundary arrays (Section 6.2.1); pass 2 gathers each
+ * partition's extents, radix-sorts it in HBM and stores it at its final
+ * offset (Section 5.3 pipeline for both).  Splitters come from a sorted key
+ * sample (VX_PART_SAMPLE) or from a learned monotone CDF model: a
+ * 1,024-segment piecewise-linear model (VX_PART_LEARNED_PL) or a 1-32-1 MLP
+ * trained on the device (VX_PART_LEARNED_MLP).  Any splitters give the same
+ * output; they decide only where to cut. */
+vx_status vx_sort(vx_ctx *ctx, int32_t key_col, int32_t rowid_col, uint64_t *out_keys, uint32_t *out_rowids,
+                  const vx_sort_opts *opts, vx_sort_stats *stats);
+
+/* In-HBM stable LSD radix sort of n pairs given in host buffers (the
+ * per-partition sort of vx_sort, Section 6.1); n must fit the arena. */
+vx_status vx_radix_sort_pairs(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                              uint64_t *out_keys, uint32_t *out_vals);
+
+/* In-HBM stable range partition of n pairs (Section 6.2.1 clustering with a
+ * range function): partition id = number of splitters <= key; writes the
+ * pairs grouped by partition in input order and the P+1 boundary array
+ * (boundary[p] = first position of partition p, boundary[P] = n; empty
+ * partitions repeat the next start, as find_boundary back-fills them). */
+vx_status vx_range_partition(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                             const uint64_t *splitters, uint32_t n_partitions, uint64_t *out_keys,
+                             uint32_t *out_vals, uint64_t *boundary);
+
+/* Splitters for n_partitions of a registered uint64 column: sample_size keys
+ * at counter-based positions (seed), sorted on the device, then the chosen
+ * partitioner; repeated splitters are separated so that a heavy key forms its
+ * own partition. */
+vx_status vx_sort_splitters(vx_ctx *ctx, int32_t key_col, int32_t partitioner, uint32_t n_partitions,
+                            uint64_t sample_size, uint64_t seed, uint64_t *splitters_out);
+
+/* ---------------------------------------------------------------- learned CDF model */
+
+/* Monotone CDF MLP with H hidden units (fp32):
+ *   y(x) = gamma + sum_j softplus(alpha_j) * sigmoid(softplus(omega_j) * x + beta_j),
+ * theta = [omega(H), beta(H), alpha(H), gamma].  Loss L = mean_i (y(x_i) - t_i)^2.
+ * Evaluates L and dL/dtheta over m host points with the device forward and
+ * backward kernels. */
+vx_status vx_mlp_loss_grad(vx_ctx *ctx, const float *theta, int32_t H, const float *x, const float *t, uint64_t m,
+                           float *grad_out, float *loss_out);
+
+/* Trains theta in place with `steps` full-batch Adam steps (lr, beta1 0.9,
+ * beta2 0.999, eps 1e-8; moments start at zero) on the device; writes the
+ * final loss. */
+vx_status vx_mlp_train(vx_ctx *ctx, float *theta, int32_t H, const float *x, const float *t, uint64_t m,
+                       uint32_t steps, float lr, float *loss_out);
+
 /* ---------------------------------------------------------------- link probe */
 
 /* Pinned-copy microbenchmark of the host link (Section 8.1 measures Exchange

@@ -106,6 +106,7 @@ def lib():
                 "or_mlp_loss_grad": ([vp, ci, vp, vp, u64, vp], dbl),
                 "or_adam_step": ([vp, vp, vp, vp, ci, ci, dbl, dbl, dbl, dbl], None),
                 "or_zero_copy_threshold": ([dbl, dbl, dbl, dbl], dbl),
+                "or_isolate_splitters": ([vp, u32], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -313,6 +314,13 @@ def pl_splitters(knots, P):
     out = np.empty(max(P - 1, 0), np.uint64)
     lib().or_pl_splitters(_p(k), len(k) - 1, P, _p(out))
     return out
+
+
+def isolate_splitters(splitters):
+    s = np.array(splitters, dtype=np.uint64, copy=True)
+    if len(s):
+        lib().or_isolate_splitters(_p(s), len(s))
+    return s
 
 
 # ---------------------------------------------------------------- MLP CDF model

@@ -459,3 +459,12 @@ OR_EXPORT void or_adam_step(double *theta, const double *grad, double *m1, doubl
 OR_EXPORT double or_zero_copy_threshold(double elem_bytes, double gather_bytes, double bw_zero_copy, double bw_copy) {
   return (elem_bytes / gather_bytes) * (bw_zero_copy / bw_copy);
 }
+
+/* Heavy-key isolation of splitters: walking left to right, a splitter that is
+ * not above its predecessor v becomes v + 1 (v = UINT64_MAX stays), so that a
+ * key value repeated among the sample quantiles gets a partition [v, v + 1)
+ * of its own and no partition is empty by construction. */
+OR_EXPORT void or_isolate_splitters(uint64_t *spl, uint32_t n_spl) {
+  for (uint32_t i = 1; i < n_spl; ++i)
+    if (spl[i] <= spl[i - 1]) spl[i] = spl[i - 1] == UINT64_MAX ? UINT64_MAX : spl[i - 1] + 1;
+}

@@ -85,8 +85,32 @@ class vx_result(ctypes.Structure):
                 ("cnt", ctypes.c_void_p), ("n_out", ctypes.c_uint64), ("stats", vx_query_stats)]
 
 
+VX_PART_SAMPLE, VX_PART_LEARNED_PL, VX_PART_LEARNED_MLP = 0, 1, 2
+
+
+class vx_sort_opts(ctypes.Structure):
+    _fields_ = [("partitioner", ctypes.c_int32), ("n_partitions", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("sample_size", ctypes.c_uint64), ("mlp_steps", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("host_scratch", ctypes.c_void_p), ("host_scratch_bytes", ctypes.c_uint64),
+                ("max_slot_pairs", ctypes.c_uint64), ("splitters_out", ctypes.c_void_p)]
+
+
+class vx_sort_stats(ctypes.Structure):
+    _fields_ = [("n_partitions", ctypes.c_uint32), ("passthrough_partitions", ctypes.c_uint32),
+                ("overflow_retries", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("max_partition", ctypes.c_uint64), ("min_partition", ctypes.c_uint64),
+                ("slot_pairs", ctypes.c_uint64), ("imbalance", ctypes.c_double), ("ms_sample", ctypes.c_double),
+                ("ms_train", ctypes.c_double), ("ms_partition", ctypes.c_double), ("ms_sort", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("bytes_h2d", ctypes.c_uint64), ("bytes_d2h", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _P = ctypes.POINTER
 _vp, _u64, _i32, _u32, _dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
+_f32 = ctypes.c_float
 SIGNATURES = {
     "vx_open": ([_u64, _P(_vp)], _i32),
     "vx_open_ex": ([_vp, _u64, _vp, _P(_vp)], _i32),
@@ -102,6 +126,12 @@ SIGNATURES = {
     "vx_last_stats": ([_vp, _P(vx_query_stats)], _i32),
     "vx_drop_resident": ([_vp], _i32),
     "vx_probe_link": ([_vp, _u64, _u64, _P(_dbl), _P(_dbl), _P(_dbl)], _i32),
+    "vx_sort": ([_vp, _i32, _i32, _vp, _vp, _P(vx_sort_opts), _P(vx_sort_stats)], _i32),
+    "vx_radix_sort_pairs": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
+    "vx_range_partition": ([_vp, _vp, _vp, _u64, _vp, _u32, _vp, _vp, _vp], _i32),
+    "vx_sort_splitters": ([_vp, _i32, _i32, _u32, _u64, _u64, _vp], _i32),
+    "vx_mlp_loss_grad": ([_vp, _vp, _i32, _vp, _vp, _u64, _vp, _vp], _i32),
+    "vx_mlp_train": ([_vp, _vp, _i32, _vp, _vp, _u64, _u32, _f32, _vp], _i32),
 }
 
 
@@ -226,6 +256,65 @@ def vx_probe_link(ctx, nbytes: int, chunk: int):
     a, b, c = _dbl(), _dbl(), _dbl()
     _check(load().vx_probe_link(ctx, nbytes, chunk, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+# ------------------------------------------------------------------ sort / partition / learned
+def _np(a, dt):
+    a = np.ascontiguousarray(a, dtype=dt)
+    return a
+
+
+def vx_sort(ctx, key_col: int, rowid_col: int, out_keys: np.ndarray, out_rowids: np.ndarray,
+            opts: vx_sort_opts | None = None):
+    """Returns the stats dict; fills out_keys/out_rowids."""
+    st = vx_sort_stats()
+    _check(load().vx_sort(ctx, key_col, rowid_col, out_keys.ctypes.data, out_rowids.ctypes.data,
+                          None if opts is None else ctypes.byref(opts), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def vx_radix_sort_pairs(ctx, keys, vals):
+    keys, vals = _np(keys, np.uint64), _np(vals, np.uint32)
+    ok, ov = np.empty_like(keys), np.empty_like(vals)
+    _check(load().vx_radix_sort_pairs(ctx, keys.ctypes.data, vals.ctypes.data, len(keys), ok.ctypes.data,
+                                      ov.ctypes.data))
+    return ok, ov
+
+
+def vx_range_partition(ctx, keys, vals, splitters):
+    keys, vals = _np(keys, np.uint64), _np(vals, np.uint32)
+    spl = _np(splitters, np.uint64)
+    P = len(spl) + 1
+    ok, ov = np.empty_like(keys), np.empty_like(vals)
+    b = np.zeros(P + 1, np.uint64)
+    _check(load().vx_range_partition(ctx, keys.ctypes.data, vals.ctypes.data, len(keys),
+                                     spl.ctypes.data if len(spl) else None, P, ok.ctypes.data, ov.ctypes.data,
+                                     b.ctypes.data))
+    return ok, ov, b
+
+
+def vx_sort_splitters(ctx, key_col: int, partitioner: int, n_partitions: int, sample_size=0, seed=0):
+    out = np.zeros(n_partitions - 1, np.uint64)
+    _check(load().vx_sort_splitters(ctx, key_col, partitioner, n_partitions, sample_size, seed, out.ctypes.data))
+    return out
+
+
+def vx_mlp_loss_grad(ctx, theta, H, x, t):
+    th, x, t = _np(theta, np.float32), _np(x, np.float32), _np(t, np.float32)
+    g = np.zeros(3 * H + 1, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(load().vx_mlp_loss_grad(ctx, th.ctypes.data, H, x.ctypes.data, t.ctypes.data, len(x), g.ctypes.data,
+                                   loss.ctypes.data))
+    return float(loss[0]), g
+
+
+def vx_mlp_train(ctx, theta, H, x, t, steps, lr):
+    th = np.array(theta, dtype=np.float32, copy=True)
+    x, t = _np(x, np.float32), _np(t, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(load().vx_mlp_train(ctx, th.ctypes.data, H, x.ctypes.data, t.ctypes.data, len(x), steps, lr,
+                               loss.ctypes.data))
+    return th, float(loss[0])
 
 
 # ------------------------------------------------------------------ plan marshalling

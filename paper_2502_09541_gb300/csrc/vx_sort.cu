@@ -1,0 +1,920 @@
+// Out-of-core sort: range partition + per-partition LSD radix sort.
+//
+// Section 6.1 sorts chunks and merges them; here the partition step comes
+// first (the two-phase layout of Section 6.2.1: per-chunk clustering with a
+// boundary array, then per-group processing of the multi-extent partitions),
+// with a monotone range function so that sorted partitions concatenate into
+// the sorted output:
+//   pass 1 (ExKernel over input chunks): stable scatter of each chunk by
+//           partition id into a host intermediate at the chunk's own offset,
+//           plus the chunk's P+1 boundary array;
+//   pass 2 (ExKernel over partitions): gather partition p's extents (one per
+//           chunk), LSD radix sort in HBM, store at the partition's final
+//           offset.
+// Both passes run on the pipelined executor, so host->device loads and
+// device->host stores overlap with the kernels.  Partitions of one key value
+// are already in input order and are copied through; a multi-key partition
+// above the slot capacity is sorted recursively.
+#include <algorithm>
+#include <cmath>
+#include <thread>
+
+#include "vx_internal.h"
+#include "vx_radix.cuh"
+#include "vx_sort.cuh"
+
+namespace vx {
+
+// ================================================================== kernels
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// digit of a key: an LSD byte (kRange = false) or the number of splitters <= key
+template <bool kRange>
+__device__ __forceinline__ uint32_t key_digit(uint64_t k, int shift, const uint64_t *s_spl, int n_spl) {
+  if (!kRange) return (uint32_t)(k >> shift) & 0xFFu;
+  int lo = 0, hi = n_spl;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (s_spl[mid] <= k) lo = mid + 1;
+    else hi = mid;
+  }
+  return (uint32_t)lo;
+}
+
+template <bool kRange>
+__global__ void __launch_bounds__(kRxThreads) rx_upsweep(RadixBufs b, const RadixState *st, int pass, uint64_t n,
+                                                         int shift, const uint64_t *spl, int n_spl, uint32_t *hist,
+                                                         uint32_t ntiles) {
+  if (!kRange && st->skip[pass]) return;
+  __shared__ uint32_t wcnt[kRxWarps][kRxDigits];
+  __shared__ uint64_t s_spl[kRxDigits];
+  const int c = kRange ? 0 : st->cur[pass];
+  const uint64_t *keys = b.keys[c];
+  for (int i = threadIdx.x; i < kRxWarps * kRxDigits; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  if (kRange)
+    for (int i = threadIdx.x; i < n_spl; i += blockDim.x) s_spl[i] = spl[i];
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t wbase = (uint64_t)blockIdx.x * kRxTile + (uint64_t)w * (32 * kRxItems);
+#pragma unroll 4
+  for (int r = 0; r < kRxItems; ++r) {
+    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+    const uint32_t d = i < n ? key_digit<kRange>(keys[i], shift, s_spl, n_spl) : kRxInvalid;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d != kRxInvalid && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRxDigits; d += blockDim.x) {
+    uint32_t s = 0;
+    for (int q = 0; q < kRxWarps; ++q) s += wcnt[q][d];
+    hist[(uint64_t)d * ntiles + blockIdx.x] = s;
+  }
+}
+
+// block d: exclusive scan of hist[d][0..ntiles) in place; row total -> totals[d]
+__global__ void __launch_bounds__(1024) rx_scan_rows(uint32_t *hist, uint32_t ntiles, RadixState *st,
+                                                     const int pass, const bool check_skip) {
+  if (check_skip && st->skip[pass]) return;
+  __shared__ uint32_t wsum[32];
+  __shared__ uint64_t carry;
+  uint32_t *row = hist + (uint64_t)blockIdx.x * ntiles;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < ntiles ? row[i] : 0;
+    uint32_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if ((threadIdx.x & 31) >= (unsigned)off) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t wv = threadIdx.x < (blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
+      for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, wv, off);
+        if (threadIdx.x >= (unsigned)off) wv += y;
+      }
+      wsum[threadIdx.x] = wv;
+    }
+    __syncthreads();
+    const uint32_t wpre = (threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0;
+    if (i < ntiles) row[i] = (uint32_t)carry + wpre + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += wsum[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->totals[blockIdx.x] = carry;
+}
+
+// one block of 256 threads: digit bases (exclusive scan of totals, base[256] =
+// n); for LSD passes, a digit holding all n pairs marks the pass skipped and
+// the double-buffer marker advances only for executed passes
+__global__ void __launch_bounds__(kRxDigits) rx_scan_totals(RadixState *st, int pass, uint64_t n, bool lsd) {
+  __shared__ uint64_t s[kRxDigits];
+  __shared__ int any_full;
+  const int d = threadIdx.x;
+  if (lsd && st->skip[pass]) {  // decided by the digit-histogram prepass
+    if (d == 0) st->cur[pass + 1] = st->cur[pass];
+    return;
+  }
+  if (d == 0) any_full = 0;
+  __syncthreads();
+  const uint64_t t = st->totals[d];
+  s[d] = t;
+  if (t == n) any_full = 1;
+  __syncthreads();
+  for (int off = 1; off < kRxDigits; off <<= 1) {
+    uint64_t y = d >= off ? s[d - off] : 0;
+    __syncthreads();
+    s[d] += y;
+    __syncthreads();
+  }
+  st->base[d] = s[d] - t;
+  if (d == 0) st->base[kRxDigits] = n;
+  if (lsd && d == 0) {
+    st->skip[pass] = any_full;
+    st->cur[pass + 1] = any_full ? st->cur[pass] : 1 - st->cur[pass];
+  }
+}
+
+// full-range histogram of all eight key bytes in one read: marks constant
+// digits so that their passes are skipped (upsweep, scan and scatter)
+__global__ void __launch_bounds__(kRxThreads) rx_byte_hist(const RadixBufs b, uint64_t n, unsigned long long *bh) {
+  __shared__ uint32_t h[8][kRxDigits];
+  for (int i = threadIdx.x; i < 8 * kRxDigits; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = b.keys[0][i];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 8 * kRxDigits; i += blockDim.x)
+    if ((&h[0][0])[i]) atomicAdd(&bh[i], (unsigned long long)(&h[0][0])[i]);
+}
+
+__global__ void rx_init_state(RadixState *st, const unsigned long long *bh, uint64_t n) {
+  const int p = threadIdx.x;  // 8 threads
+  if (p == 0) st->cur[0] = 0;
+  if (p < 8) {
+    int full = 0;
+    for (int d = 0; d < kRxDigits; ++d) full |= bh[p * kRxDigits + d] == n;
+    st->skip[p] = full;
+  }
+}
+
+template <bool kRange>
+__global__ void __launch_bounds__(kRxThreads) rx_downsweep(RadixBufs b, const RadixState *st, int pass, uint64_t n,
+                                                           int shift, const uint64_t *spl, int n_spl,
+                                                           const uint32_t *hist, uint32_t ntiles) {
+  if (!kRange && st->skip[pass]) return;
+  __shared__ uint32_t wcnt[kRxWarps][kRxDigits];
+  __shared__ uint64_t s_off[kRxDigits];
+  __shared__ uint64_t s_spl[kRxDigits];
+  const int c = kRange ? 0 : st->cur[pass];
+  const uint64_t *kin = b.keys[c];
+  const uint32_t *vin = b.vals[c];
+  uint64_t *kout = b.keys[1 - c];
+  uint32_t *vout = b.vals[1 - c];
+  for (int i = threadIdx.x; i < kRxWarps * kRxDigits; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  if (kRange)
+    for (int i = threadIdx.x; i < n_spl; i += blockDim.x) s_spl[i] = spl[i];
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t wbase = (uint64_t)blockIdx.x * kRxTile + (uint64_t)w * (32 * kRxItems);
+  uint64_t k[kRxItems];
+  uint32_t v[kRxItems], dg[kRxItems], rk[kRxItems];
+#pragma unroll
+  for (int r = 0; r < kRxItems; ++r) {
+    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+    if (i < n) {
+      k[r] = kin[i];
+      v[r] = vin[i];
+    } else {
+      k[r] = 0;
+      v[r] = 0;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRxItems; ++r) {
+    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+    dg[r] = i < n ? key_digit<kRange>(k[r], shift, s_spl, n_spl) : kRxInvalid;
+  }
+#pragma unroll
+  for (int r = 0; r < kRxItems; ++r) {
+    const uint32_t d = dg[r];
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0;
+    if (d != kRxInvalid) before = wcnt[w][d];
+    __syncwarp();
+    rk[r] = before + __popc(peers & lanemask_lt());
+    if (d != kRxInvalid && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRxDigits; d += blockDim.x) {
+    uint32_t run = 0;
+    for (int q = 0; q < kRxWarps; ++q) {
+      const uint32_t cq = wcnt[q][d];
+      wcnt[q][d] = run;
+      run += cq;
+    }
+    s_off[d] = st->base[d] + hist[(uint64_t)d * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRxItems; ++r) {
+    const uint32_t d = dg[r];
+    if (d == kRxInvalid) continue;
+    const uint64_t pos = s_off[d] + wcnt[w][d] + rk[r];
+    kout[pos] = k[r];
+    vout[pos] = v[r];
+  }
+}
+
+__global__ void rx_publish(const RadixState *st, int pass, uint64_t *host_word) { *host_word = (uint64_t)st->cur[pass]; }
+
+// ---- sampling and splitters -----------------------------------------------
+
+// key of sample i at position mix64(base + i) mod n (the library's own
+// counter-based positions), read through mapped host memory
+__device__ __forceinline__ uint64_t mix64_dev(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void sample_keys_kernel(const uint64_t *keys, uint64_t n, uint64_t m, uint64_t seed, uint64_t *out,
+                                   uint32_t *out_vals) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t pos = mix64_dev(seed * 0x9E3779B97F4A7C15ull + i) % n;
+    out[i] = keys[pos];
+    out_vals[i] = (uint32_t)i;
+  }
+}
+
+// splitters from the sorted sample: s_p = sample[p*m/P]
+__global__ void sample_splitters_kernel(const uint64_t *sorted, uint64_t m, uint32_t P, uint64_t *spl) {
+  for (uint32_t p = 1 + blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+    spl[p - 1] = sorted[(uint64_t)p * m / P];
+}
+
+// piecewise-linear CDF model: knot j = sorted[j*(m-1)/S], CDF(knot j) = j/S;
+// splitter p = model inverse at p/P, exact integer interpolation
+__global__ void pl_knots_kernel(const uint64_t *sorted, uint64_t m, uint32_t S, uint64_t *knots) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= S; j += gridDim.x * blockDim.x)
+    knots[j] = sorted[(uint64_t)j * (m - 1) / S];
+}
+
+__global__ void pl_splitters_kernel(const uint64_t *knots, uint32_t S, uint32_t P, uint64_t *spl) {
+  for (uint32_t p = 1 + blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const uint64_t num = (uint64_t)p * S;
+    const uint64_t j = num / P, rem = num % P;
+    if (j >= S) {
+      spl[p - 1] = knots[S];
+      continue;
+    }
+    const uint64_t gap = knots[j + 1] - knots[j];
+    // floor(gap * rem / P) without 128-bit arithmetic: gap = q*P + r
+    spl[p - 1] = knots[j] + (gap / P) * rem + ((gap % P) * rem) / P;
+  }
+}
+
+// Heavy keys: a value repeated among consecutive splitters would leave empty
+// partitions and one partition [v, next) holding all copies of v plus other
+// keys; the repeat is replaced by v + 1 (if that keeps the order), so that
+// [v, v+1) isolates v as a single-key partition.
+__global__ void isolate_splitters_kernel(uint64_t *spl, uint32_t n_spl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (uint32_t i = 1; i < n_spl; ++i) {
+    if (spl[i] <= spl[i - 1]) {
+      const uint64_t v = spl[i - 1];
+      spl[i] = v == UINT64_MAX ? v : v + 1;
+    }
+  }
+}
+
+// ================================================================== host helpers
+
+static uint32_t ntiles_of(uint64_t n) { return (uint32_t)((n + kRxTile - 1) / kRxTile); }
+
+// temp layout: [RadixState | 8 byte histograms (u64) | per-tile histograms]
+constexpr uint64_t kStateBytes = (sizeof(RadixState) + 255) & ~255ull;
+constexpr uint64_t kByteHistBytes = 8ull * kRxDigits * 8;
+
+uint64_t radix_temp_bytes(uint64_t cap) {
+  return kStateBytes + kByteHistBytes + (uint64_t)kRxDigits * std::max<uint32_t>(ntiles_of(cap), 1) * 4 + 256;
+}
+
+RadixState *radix_state_of(char *temp) { return (RadixState *)temp; }
+
+// Enqueues a stable LSD radix sort of b.keys[0]/b.vals[0] (n pairs) on s.
+// The sorted pairs end in buffer st->cur[8] (0 or 1).
+vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms) {
+  uint32_t nt = ntiles_of(n);
+  RadixState *st = radix_state_of(temp);
+  unsigned long long *bh = (unsigned long long *)(temp + kStateBytes);
+  uint32_t *hist = (uint32_t *)(temp + kStateBytes + kByteHistBytes);
+  VX_CUDA_TRY(cudaMemsetAsync(bh, 0, kByteHistBytes, s));
+  if (n == 0) {
+    VX_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(RadixState), s));
+    return VX_OK;
+  }
+  int g = (int)std::min<uint64_t>((n + kRxThreads - 1) / kRxThreads, (uint64_t)num_sms * 4);
+  rx_byte_hist<<<g, kRxThreads, 0, s>>>(b, n, bh);
+  rx_init_state<<<1, 32, 0, s>>>(st, bh, n);
+  for (int pass = 0; pass < 8; ++pass) {
+    // skipped passes return at once in every kernel
+    rx_upsweep<false><<<nt, kRxThreads, 0, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, hist, nt);
+    rx_scan_rows<<<kRxDigits, 1024, 0, s>>>(hist, nt, st, pass, true);
+    rx_scan_totals<<<1, kRxDigits, 0, s>>>(st, pass, n, true);
+    rx_downsweep<false><<<nt, kRxThreads, 0, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, hist, nt);
+  }
+  VX_CUDA_TRY(cudaGetLastError());
+  return VX_OK;
+}
+
+// Enqueues a stable scatter of b.keys[0]/b.vals[0] into b.keys[1]/b.vals[1] by
+// partition id (splitters spl[0..P-2] on the device); the P+1 boundary array
+// is left in st->base[0..P] with base[P] = n.
+vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, uint32_t P, char *temp,
+                                  cudaStream_t s) {
+  uint32_t nt = std::max<uint32_t>(ntiles_of(n), 1);
+  RadixState *st = radix_state_of(temp);
+  uint32_t *hist = (uint32_t *)(temp + kStateBytes + kByteHistBytes);
+  VX_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(RadixState), s));
+  if (n) {
+    rx_upsweep<true><<<nt, kRxThreads, 0, s>>>(b, st, 0, n, 0, spl, (int)P - 1, hist, nt);
+    rx_scan_rows<<<kRxDigits, 1024, 0, s>>>(hist, nt, st, 0, false);
+  }
+  rx_scan_totals<<<1, kRxDigits, 0, s>>>(st, 0, n, false);
+  if (n) rx_downsweep<true><<<nt, kRxThreads, 0, s>>>(b, st, 0, n, 0, spl, (int)P - 1, hist, nt);
+  VX_CUDA_TRY(cudaGetLastError());
+  return VX_OK;
+}
+
+
+// splitters for P partitions from the sorted sample (device), then heavy-key isolation
+vx_status splitters_from_sample(vx_ctx *ctx, int32_t kind, const uint64_t *sorted, uint64_t m, uint32_t P,
+                                uint64_t *d_spl, uint64_t *d_knots, uint32_t mlp_steps, double *ms_train) {
+  cudaStream_t s = ctx->s_compute;
+  if (P < 2) return VX_OK;
+  if (kind == VX_PART_SAMPLE) {
+    sample_splitters_kernel<<<1, 256, 0, s>>>(sorted, m, P, d_spl);
+  } else if (kind == VX_PART_LEARNED_PL) {
+    pl_knots_kernel<<<(kPLSegments + 256) / 256, 256, 0, s>>>(sorted, m, kPLSegments, d_knots);
+    pl_splitters_kernel<<<1, 256, 0, s>>>(d_knots, kPLSegments, P, d_spl);
+  } else if (kind == VX_PART_LEARNED_MLP) {
+    VX_TRY(mlp_splitters(ctx, sorted, m, P, mlp_steps, d_spl, ms_train));
+  } else {
+    set_error("unknown partitioner %d", kind);
+    return VX_E_INVAL;
+  }
+  isolate_splitters_kernel<<<1, 32, 0, s>>>(d_spl, P - 1);
+  VX_CUDA_TRY(cudaGetLastError());
+  return VX_OK;
+}
+
+// samples m keys of a mapped column and sorts them on the device
+vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t m, uint64_t seed,
+                          DevBuf &sorted_out, uint64_t **sorted_ptr) {
+  cudaStream_t s = ctx->s_compute;
+  uint64_t bytes = 2 * m * 12 + radix_temp_bytes(m) + 1024;
+  sorted_out.arena = &ctx->arena;
+  sorted_out.p = ctx->arena.alloc(bytes);
+  if (!sorted_out.p) {
+    set_error("sample of %llu keys does not fit the arena", (unsigned long long)m);
+    return VX_E_NOMEM;
+  }
+  char *p = sorted_out.as<char>();
+  RadixBufs b;
+  b.keys[0] = (uint64_t *)p;
+  b.keys[1] = (uint64_t *)(p + ((8 * m + 255) & ~255ull));
+  char *q = p + 2 * ((8 * m + 255) & ~255ull);
+  b.vals[0] = (uint32_t *)q;
+  b.vals[1] = (uint32_t *)(q + ((4 * m + 255) & ~255ull));
+  char *temp = q + 2 * ((4 * m + 255) & ~255ull);
+  sample_keys_kernel<<<ctx->num_sms * 2, 256, 0, s>>>(dev_keys, n, m, seed, b.keys[0], b.vals[0]);
+  VX_CUDA_TRY(cudaGetLastError());
+  VX_TRY(radix_sort_enqueue(b, m, temp, s, ctx->num_sms));
+  int cur = 0;
+  RadixState *st = radix_state_of(temp);
+  VX_CUDA_TRY(cudaMemcpyAsync(&cur, &st->cur[8], 4, cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  *sorted_ptr = b.keys[cur];
+  return VX_OK;
+}
+
+// ================================================================== out-of-core sort
+
+namespace {
+
+struct HostReg {  // registers host memory for the duration of a call if not pinned
+  void *p = nullptr;
+  bool reg = false;
+  vx_status add(void *ptr, uint64_t bytes) {
+    if (!ptr || !bytes) return VX_OK;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    cudaGetLastError();
+    if (e == cudaSuccess && at.type == cudaMemoryTypeHost) return VX_OK;
+    e = cudaHostRegister(ptr, bytes, cudaHostRegisterMapped);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaHostRegister(%llu) failed: %s", (unsigned long long)bytes, cudaGetErrorString(e));
+      return VX_E_CUDA;
+    }
+    p = ptr;
+    reg = true;
+    return VX_OK;
+  }
+  ~HostReg() {
+    if (reg) cudaHostUnregister(p);
+  }
+};
+
+void parallel_copy(void *dst, const void *src, uint64_t bytes) {
+  const uint64_t kMin = 64ull << 20;
+  unsigned nt = std::max(1u, std::min(16u, (unsigned)(bytes / kMin)));
+  if (nt == 1) {
+    memcpy(dst, src, bytes);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) {
+    uint64_t b = bytes * t / nt, e = bytes * (t + 1) / nt;
+    th.emplace_back([=] { memcpy((char *)dst + b, (const char *)src + b, e - b); });
+  }
+  for (auto &x : th) x.join();
+}
+
+// pass 1: per-chunk stable partition into the intermediate + boundary arrays
+struct PartitionPass : ExKernel {
+  vx_ctx *ctx;
+  const uint64_t *keys;
+  const uint32_t *vals;
+  uint64_t n, R;
+  uint32_t P;
+  const uint64_t *d_spl;
+  uint64_t *mid_keys;
+  uint32_t *mid_vals;
+  std::vector<uint64_t> *bnd;  // chunks x (P+1)
+  int S;
+
+  uint64_t size() override { return (n + R - 1) / R; }
+  uint64_t rows(uint64_t it) const { return std::min(R, n - it * R); }
+  uint64_t kb() const { return (8 * R + 255) & ~255ull; }
+  uint64_t vb() const { return (4 * R + 255) & ~255ull; }
+  uint64_t slot_bytes() override { return 2 * kb() + 2 * vb() + radix_temp_bytes(R); }
+  RadixBufs bufs(char *slot) const {
+    RadixBufs b;
+    b.keys[0] = (uint64_t *)slot;
+    b.keys[1] = (uint64_t *)(slot + kb());
+    b.vals[0] = (uint32_t *)(slot + 2 * kb());
+    b.vals[1] = (uint32_t *)(slot + 2 * kb() + vb());
+    return b;
+  }
+  char *temp(char *slot) const { return slot + 2 * kb() + 2 * vb(); }
+  void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) override {
+    RadixBufs b = bufs(slot);
+    uint64_t r0 = it * R, m = rows(it);
+    h2d.push_back({keys + r0, b.keys[0], 8 * m});
+    h2d.push_back({vals + r0, b.vals[0], 4 * m});
+  }
+  vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
+    return range_partition_enqueue(bufs(slot), rows(it), d_spl, P, temp(slot), s);
+  }
+  bool has_outputs() override { return true; }
+  vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
+    RadixBufs b = bufs(slot);
+    uint64_t r0 = it * R, m = rows(it);
+    d2h.push_back({b.keys[1], mid_keys + r0, 8 * m});
+    d2h.push_back({b.vals[1], mid_vals + r0, 4 * m});
+    RadixState *st = radix_state_of(temp(slot));
+    d2h.push_back({st->base, bnd->data() + it * (P + 1), 8ull * (P + 1)});
+    return VX_OK;
+  }
+};
+
+struct Extent {
+  uint64_t off, len;
+};
+
+// pass 2: per-partition gather + radix sort + store
+struct SortPass : ExKernel {
+  vx_ctx *ctx;
+  const uint64_t *mid_keys;
+  const uint32_t *mid_vals;
+  uint64_t cap;
+  std::vector<std::vector<Extent>> ext;  // per job
+  std::vector<uint64_t> job_n, job_off;
+  uint64_t *out_keys;
+  uint32_t *out_vals;
+  int S;
+
+  uint64_t size() override { return job_n.size(); }
+  uint64_t kb() const { return (8 * cap + 255) & ~255ull; }
+  uint64_t vb() const { return (4 * cap + 255) & ~255ull; }
+  uint64_t slot_bytes() override { return 2 * kb() + 2 * vb() + radix_temp_bytes(cap); }
+  RadixBufs bufs(char *slot) const {
+    RadixBufs b;
+    b.keys[0] = (uint64_t *)slot;
+    b.keys[1] = (uint64_t *)(slot + kb());
+    b.vals[0] = (uint32_t *)(slot + 2 * kb());
+    b.vals[1] = (uint32_t *)(slot + 2 * kb() + vb());
+    return b;
+  }
+  char *temp(char *slot) const { return slot + 2 * kb() + 2 * vb(); }
+  void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) override {
+    RadixBufs b = bufs(slot);
+    uint64_t at = 0;
+    for (const Extent &e : ext[it]) {
+      if (!e.len) continue;
+      h2d.push_back({mid_keys + e.off, b.keys[0] + at, 8 * e.len});
+      h2d.push_back({mid_vals + e.off, b.vals[0] + at, 4 * e.len});
+      at += e.len;
+    }
+  }
+  vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
+    VX_TRY(radix_sort_enqueue(bufs(slot), job_n[it], temp(slot), s, ctx->num_sms));
+    rx_publish<<<1, 1, 0, s>>>(radix_state_of(temp(slot)), 8, ctx->d_scalars + 64 + (it % S));
+    VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+  }
+  bool has_outputs() override { return true; }
+  vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
+    RadixBufs b = bufs(slot);
+    int c = (int)((volatile uint64_t *)ctx->h_scalars)[64 + (it % S)];
+    if (job_n[it] == 0) return VX_OK;
+    d2h.push_back({b.keys[c], out_keys + job_off[it], 8 * job_n[it]});
+    d2h.push_back({b.vals[c], out_vals + job_off[it], 4 * job_n[it]});
+    return VX_OK;
+  }
+};
+
+}  // namespace
+
+// sorts contiguous host pairs (keys/vals mapped or pinned) into out
+vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, const uint64_t *dev_keys, uint64_t n,
+                          uint64_t *out_keys, uint32_t *out_vals, const vx_sort_opts &o, vx_sort_stats &ss, int depth) {
+  const int S = std::max(2, ctx->cfg.n_slots);
+  const uint64_t avail = ctx->arena.largest_free();
+  // pairs per slot: (2 x 12 B + histograms) per pair, S slots
+  uint64_t cap = (uint64_t)((double)avail / (S * (24.0 + 256.0 * 4 / kRxTile)) * 0.97);
+  cap = cap / kRxTile * kRxTile;
+  if (o.max_slot_pairs) cap = std::min<uint64_t>(cap, o.max_slot_pairs / kRxTile * kRxTile);
+  if (cap < kRxTile) {
+    set_error("vx_sort: arena of %llu bytes too small", (unsigned long long)ctx->arena.capacity());
+    return VX_E_NOMEM;
+  }
+  ss.slot_pairs = cap;
+  if (n == 0) return VX_OK;
+  double t0 = now_ms();
+  // ---- P = 1: the input fits one slot
+  if (n <= cap && o.n_partitions <= 1) {
+    SortPass sp;
+    sp.ctx = ctx;
+    sp.mid_keys = keys;
+    sp.mid_vals = vals;
+    sp.cap = cap;
+    sp.ext.push_back({{0, n}});
+    sp.job_n.push_back(n);
+    sp.job_off.push_back(0);
+    sp.out_keys = out_keys;
+    sp.out_vals = out_vals;
+    sp.S = S;
+    ExecStats es;
+    VX_TRY(run_pipeline(ctx, sp, &es));
+    ss.bytes_h2d += es.bytes_h2d;
+    ss.bytes_d2h += es.bytes_d2h;
+    ss.kernel_launches += es.kernel_launches;
+    ss.n_partitions = std::max<uint32_t>(ss.n_partitions, 1);
+    ss.max_partition = std::max(ss.max_partition, n);
+    ss.ms_sort += now_ms() - t0;
+    return VX_OK;
+  }
+  // ---- splitters from a sample
+  uint32_t P = o.n_partitions > 1 ? (uint32_t)o.n_partitions
+                                  : (uint32_t)std::min<uint64_t>(256, (uint64_t)std::ceil(1.3 * (double)n / cap));
+  if (P < 2) P = 2;
+  if (P > 256) {
+    set_error("vx_sort: at most 256 partitions per pass");
+    return VX_E_UNSUPPORTED;
+  }
+  const uint64_t m = std::min<uint64_t>(o.sample_size ? o.sample_size : (1ull << 20), n);
+  DevBuf sbuf, splbuf;
+  uint64_t *sorted = nullptr;
+  double ts = now_ms();
+  VX_TRY(sample_and_sort(ctx, dev_keys, n, m, o.seed + (uint64_t)depth * 7919, sbuf, &sorted));
+  splbuf.arena = &ctx->arena;
+  splbuf.p = ctx->arena.alloc(8 * 256 + 8 * (kPLSegments + 1));
+  if (!splbuf.p) return VX_E_NOMEM;
+  uint64_t *d_spl = splbuf.as<uint64_t>();
+  uint64_t *d_knots = d_spl + 256;
+  double ms_train = 0;
+  VX_TRY(splitters_from_sample(ctx, o.partitioner, sorted, m, P, d_spl, d_knots, o.mlp_steps, &ms_train));
+  std::vector<uint64_t> spl(P - 1);
+  VX_CUDA_TRY(cudaMemcpyAsync(spl.data(), d_spl, 8 * (P - 1), cudaMemcpyDeviceToHost, ctx->s_compute));
+  VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  sbuf.release();
+  ss.ms_sample += now_ms() - ts - ms_train;
+  ss.ms_train += ms_train;
+  if (depth == 0 && o.splitters_out) memcpy(o.splitters_out, spl.data(), 8 * (P - 1));
+
+  // ---- host intermediate
+  uint64_t *mid_keys = nullptr;
+  uint32_t *mid_vals = nullptr;
+  std::vector<char> own;
+  HostReg reg_mid;
+  const uint64_t mid_bytes = n * 12;
+  if (depth == 0 && o.host_scratch && o.host_scratch_bytes >= mid_bytes) {
+    mid_keys = (uint64_t *)o.host_scratch;
+    mid_vals = (uint32_t *)((char *)o.host_scratch + 8 * n);
+    VX_TRY(reg_mid.add(o.host_scratch, mid_bytes));
+  } else {
+    own.resize(mid_bytes);
+    mid_keys = (uint64_t *)own.data();
+    mid_vals = (uint32_t *)(own.data() + 8 * n);
+    VX_TRY(reg_mid.add(own.data(), mid_bytes));
+  }
+
+  // ---- pass 1: partition
+  double tp = now_ms();
+  const uint64_t R = std::min<uint64_t>(cap, (uint64_t)UINT32_MAX / 2 / kRxTile * kRxTile);
+  const uint64_t n_chunks = (n + R - 1) / R;
+  std::vector<uint64_t> bnd(n_chunks * (P + 1));
+  {
+    PartitionPass pp;
+    pp.ctx = ctx;
+    pp.keys = keys;
+    pp.vals = vals;
+    pp.n = n;
+    pp.R = R;
+    pp.P = P;
+    pp.d_spl = d_spl;
+    pp.mid_keys = mid_keys;
+    pp.mid_vals = mid_vals;
+    pp.bnd = &bnd;
+    pp.S = S;
+    ExecStats es;
+    VX_TRY(run_pipeline(ctx, pp, &es));
+    ss.bytes_h2d += es.bytes_h2d;
+    ss.bytes_d2h += es.bytes_d2h;
+    ss.kernel_launches += es.kernel_launches * 4;  // upsweep, row scan, totals, downsweep
+  }
+  ss.ms_partition += now_ms() - tp;
+
+  // ---- partition sizes, offsets, extents
+  std::vector<uint64_t> psize(P, 0), poff(P, 0);
+  for (uint64_t c = 0; c < n_chunks; ++c)
+    for (uint32_t p = 0; p < P; ++p) psize[p] += bnd[c * (P + 1) + p + 1] - bnd[c * (P + 1) + p];
+  for (uint32_t p = 1; p < P; ++p) poff[p] = poff[p - 1] + psize[p - 1];
+  auto extents = [&](uint32_t p) {
+    std::vector<Extent> e;
+    for (uint64_t c = 0; c < n_chunks; ++c) {
+      uint64_t b0 = bnd[c * (P + 1) + p], b1 = bnd[c * (P + 1) + p + 1];
+      if (b1 > b0) e.push_back({c * R + b0, b1 - b0});
+    }
+    return e;
+  };
+  uint64_t mx = 0, mn = UINT64_MAX;
+  for (uint32_t p = 0; p < P; ++p) {
+    mx = std::max(mx, psize[p]);
+    mn = std::min(mn, psize[p]);
+  }
+  if (depth == 0) {
+    ss.n_partitions = P;
+    ss.max_partition = mx;
+    ss.min_partition = mn;
+    ss.imbalance = (double)mx / ((double)n / P);
+  }
+
+  // ---- pass 2: sort the partitions that fit; copy through single-key ones;
+  // recurse on the others
+  double tq = now_ms();
+  SortPass sp;
+  sp.ctx = ctx;
+  sp.mid_keys = mid_keys;
+  sp.mid_vals = mid_vals;
+  sp.cap = cap;
+  sp.out_keys = out_keys;
+  sp.out_vals = out_vals;
+  sp.S = S;
+  std::vector<uint32_t> big;
+  for (uint32_t p = 0; p < P; ++p) {
+    if (psize[p] == 0) continue;
+    if (psize[p] <= cap) {
+      sp.ext.push_back(extents(p));
+      sp.job_n.push_back(psize[p]);
+      sp.job_off.push_back(poff[p]);
+    } else {
+      big.push_back(p);
+    }
+  }
+  {
+    ExecStats es;
+    VX_TRY(run_pipeline(ctx, sp, &es));
+    ss.bytes_h2d += es.bytes_h2d;
+    ss.bytes_d2h += es.bytes_d2h;
+    ss.kernel_launches += es.kernel_launches * 35;  // byte histogram, state, 8 x 4 passes, publish
+  }
+  for (uint32_t p : big) {
+    const uint64_t lo = p == 0 ? 0 : spl[p - 1];
+    const bool single_key = p + 1 < P ? (spl[p] > lo && spl[p] - lo == 1) : lo == UINT64_MAX;
+    std::vector<Extent> ex = extents(p);
+    if (single_key) {  // already in input order: copy through
+      uint64_t at = poff[p];
+      for (const Extent &e : ex) {
+        parallel_copy(out_keys + at, mid_keys + e.off, 8 * e.len);
+        parallel_copy(out_vals + at, mid_vals + e.off, 4 * e.len);
+        at += e.len;
+      }
+      ss.passthrough_partitions += 1;
+      continue;
+    }
+    if (depth >= 3) {
+      set_error("vx_sort: partition of %llu pairs still exceeds the slot after 3 levels",
+                (unsigned long long)psize[p]);
+      return VX_E_CAPACITY;
+    }
+    ss.overflow_retries += 1;
+    // gather the partition contiguously (in input order) and sort it recursively
+    std::vector<char> tmp(psize[p] * 12);
+    uint64_t *tk = (uint64_t *)tmp.data();
+    uint32_t *tv = (uint32_t *)(tmp.data() + 8 * psize[p]);
+    uint64_t at = 0;
+    for (const Extent &e : ex) {
+      parallel_copy(tk + at, mid_keys + e.off, 8 * e.len);
+      parallel_copy(tv + at, mid_vals + e.off, 4 * e.len);
+      at += e.len;
+    }
+    HostReg rt;
+    VX_TRY(rt.add(tmp.data(), tmp.size()));
+    void *dk = nullptr;
+    VX_CUDA_TRY(cudaHostGetDevicePointer(&dk, tk, 0));
+    vx_sort_opts o2 = o;
+    o2.n_partitions = 0;
+    VX_TRY(sort_contiguous(ctx, tk, tv, (const uint64_t *)dk, psize[p], out_keys + poff[p], out_vals + poff[p], o2,
+                           ss, depth + 1));
+  }
+  ss.ms_sort += now_ms() - tq;
+  return VX_OK;
+}
+
+}  // namespace vx
+
+using namespace vx;
+
+VX_API vx_status vx_sort(vx_ctx *ctx, int32_t key_col, int32_t rowid_col, uint64_t *out_keys, uint32_t *out_rowids,
+                         const vx_sort_opts *opts, vx_sort_stats *stats) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const Column *kc = get_col(ctx, key_col, VX_U64);
+  const Column *vc = get_col(ctx, rowid_col, VX_U32);
+  if (!kc || !vc) return VX_E_INVAL;
+  if (kc->n_rows != vc->n_rows || ((!out_keys || !out_rowids) && kc->n_rows)) {
+    set_error("vx_sort: columns differ in length or null output");
+    return VX_E_INVAL;
+  }
+  vx_sort_opts o{};
+  if (opts) o = *opts;
+  if (o.partitioner < VX_PART_SAMPLE || o.partitioner > VX_PART_LEARNED_MLP || o.n_partitions < 0 ||
+      o.n_partitions > 256) {
+    set_error("vx_sort: bad options");
+    return VX_E_INVAL;
+  }
+  const uint64_t n = kc->n_rows;
+  HostReg r1, r2;
+  VX_TRY(r1.add(out_keys, 8 * n));
+  VX_TRY(r2.add(out_rowids, 4 * n));
+  vx_sort_stats ss{};
+  double t0 = now_ms();
+  vx_status st = sort_contiguous(ctx, (const uint64_t *)kc->host, (const uint32_t *)vc->host,
+                                 (const uint64_t *)kc->dev, n, out_keys, out_rowids, o, ss, 0);
+  ss.ms_total = now_ms() - t0;
+  if (stats) *stats = ss;
+  return st;
+}
+
+VX_API vx_status vx_radix_sort_pairs(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                                     uint64_t *out_keys, uint32_t *out_vals) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (n && (!keys || !vals || !out_keys || !out_vals)) {
+    set_error("vx_radix_sort_pairs: null buffer");
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  if (n == 0) return VX_OK;
+  DevBuf buf;
+  buf.arena = &ctx->arena;
+  const uint64_t kb = (8 * n + 255) & ~255ull, vb = (4 * n + 255) & ~255ull;
+  buf.p = ctx->arena.alloc(2 * kb + 2 * vb + radix_temp_bytes(n));
+  if (!buf.p) {
+    set_error("vx_radix_sort_pairs: %llu pairs do not fit the arena", (unsigned long long)n);
+    return VX_E_NOMEM;
+  }
+  char *p = buf.as<char>();
+  RadixBufs b;
+  b.keys[0] = (uint64_t *)p;
+  b.keys[1] = (uint64_t *)(p + kb);
+  b.vals[0] = (uint32_t *)(p + 2 * kb);
+  b.vals[1] = (uint32_t *)(p + 2 * kb + vb);
+  char *temp = p + 2 * kb + 2 * vb;
+  cudaStream_t s = ctx->s_compute;
+  VX_CUDA_TRY(cudaMemcpyAsync(b.keys[0], keys, 8 * n, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(b.vals[0], vals, 4 * n, cudaMemcpyHostToDevice, s));
+  VX_TRY(radix_sort_enqueue(b, n, temp, s, ctx->num_sms));
+  int cur = 0;
+  VX_CUDA_TRY(cudaMemcpyAsync(&cur, &radix_state_of(temp)->cur[8], 4, cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  VX_CUDA_TRY(cudaMemcpyAsync(out_keys, b.keys[cur], 8 * n, cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(out_vals, b.vals[cur], 4 * n, cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  return VX_OK;
+}
+
+VX_API vx_status vx_range_partition(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                                    const uint64_t *splitters, uint32_t n_partitions, uint64_t *out_keys,
+                                    uint32_t *out_vals, uint64_t *boundary) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (n_partitions < 1 || n_partitions > 256 || (n_partitions > 1 && !splitters) || !boundary ||
+      (n && (!keys || !vals || !out_keys || !out_vals))) {
+    set_error("vx_range_partition: bad argument");
+    return VX_E_INVAL;
+  }
+  for (uint32_t i = 1; i + 1 < n_partitions; ++i)
+    if (splitters[i] < splitters[i - 1]) {
+      set_error("vx_range_partition: splitters must be non-decreasing");
+      return VX_E_INVAL;
+    }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  DevBuf buf;
+  buf.arena = &ctx->arena;
+  const uint64_t kb = (8 * std::max<uint64_t>(n, 1) + 255) & ~255ull, vb = (4 * std::max<uint64_t>(n, 1) + 255) & ~255ull;
+  buf.p = ctx->arena.alloc(2 * kb + 2 * vb + radix_temp_bytes(std::max<uint64_t>(n, 1)) + 8 * 256);
+  if (!buf.p) {
+    set_error("vx_range_partition: %llu pairs do not fit the arena", (unsigned long long)n);
+    return VX_E_NOMEM;
+  }
+  char *p = buf.as<char>();
+  RadixBufs b;
+  b.keys[0] = (uint64_t *)p;
+  b.keys[1] = (uint64_t *)(p + kb);
+  b.vals[0] = (uint32_t *)(p + 2 * kb);
+  b.vals[1] = (uint32_t *)(p + 2 * kb + vb);
+  char *temp = p + 2 * kb + 2 * vb;
+  uint64_t *d_spl = (uint64_t *)(temp + radix_temp_bytes(std::max<uint64_t>(n, 1)));
+  cudaStream_t s = ctx->s_compute;
+  if (n_partitions > 1) VX_CUDA_TRY(cudaMemcpyAsync(d_spl, splitters, 8 * (n_partitions - 1), cudaMemcpyHostToDevice, s));
+  if (n) {
+    VX_CUDA_TRY(cudaMemcpyAsync(b.keys[0], keys, 8 * n, cudaMemcpyHostToDevice, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(b.vals[0], vals, 4 * n, cudaMemcpyHostToDevice, s));
+  }
+  VX_TRY(range_partition_enqueue(b, n, d_spl, n_partitions, temp, s));
+  RadixState *st = radix_state_of(temp);
+  VX_CUDA_TRY(cudaMemcpyAsync(boundary, st->base, 8ull * (n_partitions + 1), cudaMemcpyDeviceToHost, s));
+  if (n) {
+    VX_CUDA_TRY(cudaMemcpyAsync(out_keys, b.keys[1], 8 * n, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaMemcpyAsync(out_vals, b.vals[1], 4 * n, cudaMemcpyDeviceToHost, s));
+  }
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  boundary[n_partitions] = n;
+  return VX_OK;
+}
+
+VX_API vx_status vx_sort_splitters(vx_ctx *ctx, int32_t key_col, int32_t partitioner, uint32_t n_partitions,
+                                   uint64_t sample_size, uint64_t seed, uint64_t *splitters_out) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const Column *kc = get_col(ctx, key_col, VX_U64);
+  if (!kc) return VX_E_INVAL;
+  if (n_partitions < 2 || n_partitions > 256 || !splitters_out || kc->n_rows == 0) {
+    set_error("vx_sort_splitters: need 2..256 partitions, output, non-empty column");
+    return VX_E_INVAL;
+  }
+  const uint64_t m = std::min<uint64_t>(sample_size ? sample_size : (1ull << 20), kc->n_rows);
+  DevBuf sbuf, splbuf;
+  uint64_t *sorted = nullptr;
+  VX_TRY(sample_and_sort(ctx, (const uint64_t *)kc->dev, kc->n_rows, m, seed, sbuf, &sorted));
+  splbuf.arena = &ctx->arena;
+  splbuf.p = ctx->arena.alloc(8 * 256 + 8 * (kPLSegments + 1));
+  if (!splbuf.p) return VX_E_NOMEM;
+  uint64_t *d_spl = splbuf.as<uint64_t>();
+  double ms = 0;
+  VX_TRY(splitters_from_sample(ctx, partitioner, sorted, m, n_partitions, d_spl, d_spl + 256, 0, &ms));
+  VX_CUDA_TRY(cudaMemcpyAsync(splitters_out, d_spl, 8 * (n_partitions - 1), cudaMemcpyDeviceToHost, ctx->s_compute));
+  VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  return VX_OK;
+}

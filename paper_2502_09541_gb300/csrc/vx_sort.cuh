@@ -1,0 +1,25 @@
+// Shared declarations of the sort, partition and learned-partitioner code.
+#pragma once
+#include <cstdint>
+
+#include "vx_internal.h"
+#include "vx_radix.cuh"
+
+namespace vx {
+
+constexpr uint32_t kPLSegments = 1024;  // piecewise-linear CDF model segments
+constexpr int kMlpHidden = 32;          // width of the monotone CDF MLP
+constexpr int kMlpParams = 3 * kMlpHidden + 1;
+
+uint64_t radix_temp_bytes(uint64_t cap);
+RadixState *radix_state_of(char *temp);
+vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms);
+vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, uint32_t P, char *temp,
+                                  cudaStream_t s);
+vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t m, uint64_t seed,
+                          DevBuf &sorted_out, uint64_t **sorted_ptr);
+// trains the monotone CDF MLP on the sorted sample and writes P-1 splitters
+vx_status mlp_splitters(vx_ctx *ctx, const uint64_t *sorted, uint64_t m, uint32_t P, uint32_t steps, uint64_t *d_spl,
+                        double *ms_train);
+
+}  // namespace vx

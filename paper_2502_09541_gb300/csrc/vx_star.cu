@@ -135,16 +135,39 @@ __global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
       for (int j = 0; j < kRows; ++j) alive[j] = alive[j] && pred_ok(v[j], p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
     }
     for (int d = 0; d < p.n_dims; ++d) {
+      const uint64_t *__restrict__ slots = p.ht[d];
+      const uint32_t l2c = p.ht_log2[d];
+      const uint32_t mask = (1u << l2c) - 1u;
       int32_t key[kRows];
+      uint32_t h[kRows];
+      uint64_t sl[kRows];
 #pragma unroll
       for (int j = 0; j < kRows; ++j) key[j] = alive[j] ? load_role(p, p.dim_role[d], row[j]) : 0;
+      // first probe of every row issued before any is resolved (memory-level
+      // parallelism); linear probing continues only on collisions
 #pragma unroll
       for (int j = 0; j < kRows; ++j) {
-        uint32_t val = 0;
-        if (alive[j]) {
-          alive[j] = ht_lookup(p.ht[d], p.ht_log2[d], key[j], val);
-          g[j] += val;
+        h[j] = ht_hash32(key[j], l2c);
+        sl[j] = alive[j] ? __ldg(&slots[h[j]]) : HT_EMPTY;
+      }
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        if (!alive[j]) continue;
+        uint64_t s = sl[j];
+        uint32_t hh = h[j];
+        bool hit = false;
+        for (uint32_t n = 0; n <= mask; ++n) {
+          const uint32_t v = (uint32_t)(s >> 32);
+          if (v == HT_EMPTY_VAL) break;
+          if ((int32_t)(uint32_t)s == key[j]) {
+            hit = v != HT_FILTERED;
+            g[j] += v;
+            break;
+          }
+          hh = (hh + 1u) & mask;
+          s = __ldg(&slots[hh]);
         }
+        alive[j] = hit;
       }
     }
     for (int k = 0; k < p.n_fgk; ++k) {
@@ -160,11 +183,16 @@ __global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
         g[j] += (uint32_t)code * p.fgk_stride[k];
       }
     }
+    int32_t av[kRows], bv[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {  // aggregate inputs of all rows in flight together
+      av[j] = (alive[j] && p.agg_a_role >= 0) ? load_role(p, p.agg_a_role, row[j]) : 0;
+      bv[j] = (alive[j] && p.agg_b_role >= 0) ? load_role(p, p.agg_b_role, row[j]) : 0;
+    }
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       if (!alive[j]) continue;
-      int64_t a = p.agg_a_role >= 0 ? load_role(p, p.agg_a_role, row[j]) : 0;
-      int64_t b = p.agg_b_role >= 0 ? load_role(p, p.agg_b_role, row[j]) : 0;
+      const int64_t a = av[j], b = bv[j];
       int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
       if (kSmem) {
         atomicAdd(&ssum[g[j]], (unsigned long long)v);
@@ -187,11 +215,17 @@ __global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
 }
 
 // Fraction of sampled rows passing the fact predicates (planner estimate);
-// reads the sampled rows through mapped host memory.
+// reads the sampled rows through mapped host memory, in runs of kSampleRun
+// consecutive rows so that a few host pages are touched.
+constexpr uint32_t kSampleRun = 64;
 __global__ void sample_preds_kernel(const SampleParams p) {
   unsigned long long c = 0;
+  const uint32_t n_seg = (p.n_samples + kSampleRun - 1) / kSampleRun;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < p.n_samples; s += gridDim.x * blockDim.x) {
-    const uint64_t i = p.row_begin + (uint64_t)s * p.n / p.n_samples;
+    const uint64_t seg = s / kSampleRun, k = s % kSampleRun;
+    const uint64_t off = seg * p.n / n_seg + k;
+    if (off >= p.n) continue;
+    const uint64_t i = p.row_begin + off;
     bool ok = true;
     for (int q = 0; q < p.n_preds && ok; ++q) ok = pred_ok(p.col[q][i], p.op[q], p.lo[q], p.hi[q]);
     c += ok;
@@ -391,18 +425,18 @@ struct StarExKernel : ExKernel {
     p.n = rows_of(it);
     for (size_t k = 0; k < staged_cols.size(); ++k) p.staged[staged_role[k]] = (const int32_t *)(slot + col_off(k));
     int threads = ctx->cfg.block_threads > 256 ? 256 : ctx->cfg.block_threads;
-    int g = grid_for(ctx, (p.n + 3) / 4, threads);
+    int g = grid_for(ctx, (p.n + 7) / 8, threads);
     if (smem) {
       static bool attr_set = false;
       if (!attr_set) {
-        VX_CUDA_TRY(cudaFuncSetAttribute(star_chunk_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        VX_CUDA_TRY(cudaFuncSetAttribute(star_chunk_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(16 * kSmemGroups)));
         attr_set = true;
       }
-      star_chunk_kernel<true, 4><<<g, threads, smem_bytes, s>>>(p);
+      star_chunk_kernel<true, 8><<<g, threads, smem_bytes, s>>>(p);
     }
     else
-      star_chunk_kernel<false, 4><<<g, threads, 0, s>>>(p);
+      star_chunk_kernel<false, 8><<<g, threads, 0, s>>>(p);
     VX_CUDA_TRY(cudaGetLastError());
     return VX_OK;
   }
@@ -610,6 +644,8 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
     sp.row_begin = row_begin;
     sp.n = n_rows;
     sp.n_samples = (uint32_t)std::min<uint64_t>(n_rows, 8192);
+    sp.n_samples = sp.n_samples / kSampleRun * kSampleRun;
+    if (sp.n_samples == 0) sp.n_samples = (uint32_t)n_rows;  // fewer rows than one run: all rows
     sp.out = (unsigned long long *)(d_cnt + 15);
     sample_preds_kernel<<<16, 256, 0, ctx->s_compute>>>(sp);
     VX_CUDA_TRY(cudaGetLastError());

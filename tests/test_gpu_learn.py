@@ -1,0 +1,94 @@
+"""GPU forward/backward and Adam kernels of the monotone CDF MLP against the
+fp64 oracle, and what the trained network gains over the partitioner without
+it (equal-width range cuts over [min key, max key])."""
+import numpy as np
+import pytest
+
+import datagen as G
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+vx = pytest.importorskip("paper_2502_09541_gb300")
+H = 32
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = vx.vx_open(256 << 20)
+    yield c
+    vx.vx_close(c)
+
+
+def _points(m, dist="zipf"):
+    if dist == "zipf_rank":
+        k = G.u64_zipf(200_000, 1 << 20, 0.8, 0, 77, hashed=False)
+    else:
+        k, _ = G.sort_input(200_000, dist)
+    s = np.sort(k)
+    idx = np.linspace(0, len(s) - 1, m).astype(np.int64)
+    x = ((s[idx] - s[0]).astype(np.float64) / float(s[-1] - s[0])).astype(np.float32)
+    t = ((idx + 0.5) / len(s)).astype(np.float32)
+    return x, t
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_loss_and_gradient_match_fp64_oracle(ctx, seed):
+    rng = np.random.default_rng(seed)
+    theta = rng.normal(size=3 * H + 1).astype(np.float32)
+    x, t = _points(8192)
+    L, g = vx.vx_mlp_loss_grad(ctx, theta, H, x, t)
+    Lo, go = O.mlp_loss_grad(theta.astype(np.float64), H, x.astype(np.float64), t.astype(np.float64))
+    assert abs(L - Lo) <= 1e-3 * abs(Lo) + 1e-6
+    # fp32 forward/backward with atomically reduced sums vs fp64: relative
+    # error below 1e-3 of the gradient's scale
+    scale = np.abs(go).max()
+    assert np.all(np.abs(g - go) <= 1e-3 * np.abs(go) + 1e-4 * scale), np.abs(g - go).max()
+
+
+def test_one_adam_step_matches_oracle(ctx):
+    rng = np.random.default_rng(7)
+    theta = rng.normal(size=3 * H + 1).astype(np.float32)
+    x, t = _points(4096)
+    got, _ = vx.vx_mlp_train(ctx, theta, H, x, t, 1, 0.01)
+    th = theta.astype(np.float64)
+    _, go = O.mlp_loss_grad(th, H, x.astype(np.float64), t.astype(np.float64))
+    m1, m2 = np.zeros_like(th), np.zeros_like(th)
+    O.adam_step(th, go, m1, m2, 1, lr=0.01)
+    # first Adam step moves by ~lr*sign(g): compare the step itself
+    assert np.allclose(got - theta, th - theta.astype(np.float64), atol=2e-4, rtol=1e-2)
+
+
+def test_training_reduces_loss_and_beats_equal_width(ctx):
+    x, t = _points(16384, "zipf_rank")
+    theta0 = np.zeros(3 * H + 1, np.float32)
+    # start from the library's uniform-CDF initialisation (slope 2H steps)
+    for j in range(H):
+        theta0[j] = 2 * H
+        theta0[H + j] = -2 * H * ((j + 0.5) / H)
+        theta0[2 * H + j] = np.log(np.expm1(1.0 / H))
+    L0, _ = vx.vx_mlp_loss_grad(ctx, theta0, H, x, t)
+    th, L1 = vx.vx_mlp_train(ctx, theta0, H, x, t, 400, 0.01)
+    assert L1 < 0.2 * L0, (L0, L1)
+    # monotone after training (oracle forward in fp64)
+    ys = [O.mlp_forward(th.astype(np.float64), H, v) for v in np.linspace(0, 1, 201)]
+    assert np.all(np.diff(ys) >= -1e-9)
+
+
+def test_trained_partitioner_gain_over_equal_width():
+    """Keys = Zipf ranks (small keys hot): equal-width cuts over [min, max]
+    put almost every key in the first partition; the trained network's cuts
+    balance them."""
+    n, P = 1_000_000, 16
+    k = G.u64_zipf(n, 1 << 20, 0.8, 0, 77, hashed=False)
+    c = vx.vx_open(256 << 20)
+    try:
+        cid = vx.vx_register_host_column(c, "k", k)
+        spl = vx.vx_sort_splitters(c, cid, vx.VX_PART_LEARNED_MLP, P, 200_000, 1)
+    finally:
+        vx.vx_close(c)
+    lo, hi = int(k.min()), int(k.max())
+    eq = np.array([lo + (hi - lo) * p // P for p in range(1, P)], np.uint64)
+    imb = lambda s: np.bincount(np.searchsorted(s, k, side="right"), minlength=P).max() / (n / P)
+    learned, equal = imb(spl), imb(eq)
+    assert learned < 2.0 and equal > 4 * learned, (learned, equal)

@@ -401,3 +401,14 @@ def test_threshold_reduces_to_paper_value():
     # one link of zero-copy bandwidth B against copies spread over N equal links
     th = O.zero_copy_threshold(E, C, 1.0, N)
     assert th == float(g["threshold"]) == 1 / 64
+
+
+def test_isolate_splitters_separates_heavy_keys():
+    s = O.isolate_splitters(np.array([5, 9, 9, 9, 12, 12, 2**64 - 1, 2**64 - 1], np.uint64))
+    assert s.tolist() == [5, 9, 10, 11, 12, 13, 2**64 - 1, 2**64 - 1]
+    # a heavy key repeated among sample quantiles ends in a partition of its own
+    k = np.array([3] * 50 + list(range(100, 150)), np.uint64)
+    spl = O.isolate_splitters(O.sample_splitters(O.sorted_u64(k), 8))
+    pid = np.searchsorted(spl, k, side="right")
+    heavy = set(pid[k == 3].tolist())
+    assert len(heavy) == 1 and set(k[pid == heavy.pop()].tolist()) == {3}
