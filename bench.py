@@ -220,7 +220,7 @@ def run_ours(args):
     plans = [vx.make_plan(tmpls[n], fid, did, G.STAR_ATTR_CARD) for n in TEMPLATES]
 
     # link peak measured in this run (pinned copies, 64 MiB chunks)
-    h2d_peak, d2h_peak, bid_peak = vx.vx_probe_link(ctx, 2 << 30, 64 << 20)
+    h2d_peak, d2h_peak, bid_peak = vx.vx_probe_link(ctx, min(2 << 30, budget // 4), 64 << 20)
 
     def step(collect):
         for p in plans:

@@ -284,6 +284,39 @@ vx_status vx_range_partition(vx_ctx *ctx, const uint64_t *keys, const uint32_t *
 vx_status vx_sort_splitters(vx_ctx *ctx, int32_t key_col, int32_t partitioner, uint32_t n_partitions,
                             uint64_t sample_size, uint64_t seed, uint64_t *splitters_out);
 
+/* ---------------------------------------------------------------- join */
+typedef struct {
+  int32_t partitioner;  /* VX_PART_*: splitters over the build keys when P > 1 */
+  int32_t n_partitions; /* 0 = smallest P whose hash tables fit the budget; <= 256 */
+  uint64_t seed;        /* sample positions */
+  uint64_t sample_size; /* build keys sampled for the splitters (0 = 1 Mi) */
+  double load_factor;   /* hash-table load (0 = 0.8) */
+  int32_t count_pass;   /* 1: size tables from an exact count pass over the build keys (plain
+                           form); 0: from the partition sizes the model implies, rebuilding a
+                           table that overflows (learned form) */
+  int32_t reserved;
+} vx_join_opts;
+
+typedef struct {
+  uint64_t count;       /* matching (probe, build) pairs */
+  uint64_t payload_sum; /* sum of matched build payloads, mod 2^64 */
+  uint64_t pair_fp;     /* sum over matches of mix64(probe_row ^ rotl(payload, 17)), mod 2^64;
+                           mix64 = SplitMix64 finalizer */
+  uint32_t n_partitions, overflow_retries;
+  uint64_t max_partition, bytes_h2d, kernel_launches;
+  double ms_sample, ms_train, ms_build, ms_probe, ms_kernel, ms_total;
+} vx_join_result;
+
+/* Equi-join of a build table (unique 64-bit keys, 64-bit payload) with a
+ * probe key column, all in registered host memory and possibly larger than
+ * the budget (Section 6.2; A.key == B.key).  The build keys are cut into
+ * n_partitions key ranges; for each range an open-addressing table is built
+ * in HBM from the streamed build side and the streamed probe side probes it
+ * (Section 5.3 executor for every stream).  Returns VX_E_DUPKEY if a build
+ * key repeats. */
+vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, int32_t probe_key, const vx_join_opts *opts,
+                  vx_join_result *out);
+
 /* ---------------------------------------------------------------- learned CDF model */
 
 /* Monotone CDF MLP with H hidden units (fp32):

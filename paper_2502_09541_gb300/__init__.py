@@ -108,6 +108,24 @@ class vx_sort_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class vx_join_opts(ctypes.Structure):
+    _fields_ = [("partitioner", ctypes.c_int32), ("n_partitions", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("sample_size", ctypes.c_uint64), ("load_factor", ctypes.c_double), ("count_pass", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class vx_join_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("payload_sum", ctypes.c_uint64), ("pair_fp", ctypes.c_uint64),
+                ("n_partitions", ctypes.c_uint32), ("overflow_retries", ctypes.c_uint32),
+                ("max_partition", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("ms_sample", ctypes.c_double), ("ms_train", ctypes.c_double),
+                ("ms_build", ctypes.c_double), ("ms_probe", ctypes.c_double), ("ms_kernel", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = ctypes.POINTER
 _vp, _u64, _i32, _u32, _dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
 _f32 = ctypes.c_float
@@ -132,6 +150,7 @@ SIGNATURES = {
     "vx_sort_splitters": ([_vp, _i32, _i32, _u32, _u64, _u64, _vp], _i32),
     "vx_mlp_loss_grad": ([_vp, _vp, _i32, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_mlp_train": ([_vp, _vp, _i32, _vp, _vp, _u64, _u32, _f32, _vp], _i32),
+    "vx_join": ([_vp, _i32, _i32, _i32, _P(vx_join_opts), _P(vx_join_result)], _i32),
 }
 
 
@@ -271,6 +290,13 @@ def vx_sort(ctx, key_col: int, rowid_col: int, out_keys: np.ndarray, out_rowids:
     _check(load().vx_sort(ctx, key_col, rowid_col, out_keys.ctypes.data, out_rowids.ctypes.data,
                           None if opts is None else ctypes.byref(opts), ctypes.byref(st)))
     return st.as_dict()
+
+
+def vx_join(ctx, build_key: int, build_payload: int, probe_key: int, opts: vx_join_opts | None = None) -> dict:
+    r = vx_join_result()
+    _check(load().vx_join(ctx, build_key, build_payload, probe_key, None if opts is None else ctypes.byref(opts),
+                          ctypes.byref(r)))
+    return r.as_dict()
 
 
 def vx_radix_sort_pairs(ctx, keys, vals):

@@ -121,15 +121,20 @@ __global__ void adam_kernel(float *theta, const float *grad, AdamState *st, int 
   if (threadIdx.x == 0) st->t = step;
 }
 
-// initial parameters: H sigmoid steps of slope 2H centred at (j + 0.5)/H with
-// height 1/H, i.e. close to the uniform CDF on [0, 1]
-__global__ void mlp_init_kernel(float *theta, int H) {
+// data-driven initial parameters from the (sorted) training points: unit j is
+// a sigmoid step of height 1/H centred at the (j + 0.5)/H quantile of x, with a
+// slope inverse to the width of its quantile bin, so the untrained network is
+// already a smoothed H-segment quantile model that training then refines
+__global__ void mlp_init_from_points_kernel(const float *x, uint32_t M, float *theta, int H) {
   for (int j = threadIdx.x; j < H; j += blockDim.x) {
-    const float slope = 2.f * H;
-    theta[j] = slope + log1pf(-expf(-slope));  // softplus^-1(slope)
-    theta[H + j] = -slope * ((j + 0.5f) / H);
-    const float h = 1.f / H;
-    theta[2 * H + j] = logf(expm1f(h));  // softplus^-1(h)
+    const uint32_t a = (uint32_t)((uint64_t)j * M / H), b = (uint32_t)((uint64_t)(j + 1) * M / H);
+    const uint32_t c = (uint32_t)(((uint64_t)2 * j + 1) * M / (2 * H));
+    const float lo = x[a < M ? a : M - 1], hi = x[b < M ? b : M - 1], mid = x[c < M ? c : M - 1];
+    const float width = fmaxf(hi - lo, 1e-7f);
+    const float slope = fminf(4.f / width, 1e7f);
+    theta[j] = slope > 20.f ? slope : logf(expm1f(slope));  // softplus^-1(slope)
+    theta[H + j] = -slope * mid;
+    theta[2 * H + j] = logf(expm1f(1.f / H));  // softplus^-1(1/H)
   }
   if (threadIdx.x == 0) theta[3 * H] = 0.f;
 }
@@ -276,7 +281,7 @@ vx_status mlp_splitters(vx_ctx *ctx, const uint64_t *sorted, uint64_t m, uint32_
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
   mlp_points_kernel<<<(M + 255) / 256, 256, 0, s>>>(sorted, m, M, w.x, w.t);
-  mlp_init_kernel<<<1, 64, 0, s>>>(w.theta, kMlpHidden);
+  mlp_init_from_points_kernel<<<1, 64, 0, s>>>(w.x, M, w.theta, kMlpHidden);
   VX_CUDA_TRY(cudaGetLastError());
   VX_TRY(train(ctx, kMlpHidden, w, M, steps ? steps : 300, 1e-2f));
   mlp_splitters_kernel<kMlpHidden><<<1, 256, 0, s>>>(w.theta, sorted, m, P, d_spl);
