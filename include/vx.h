@@ -277,12 +277,16 @@ vx_status vx_range_partition(vx_ctx *ctx, const uint64_t *keys, const uint32_t *
                              const uint64_t *splitters, uint32_t n_partitions, uint64_t *out_keys,
                              uint32_t *out_vals, uint64_t *boundary);
 
-/* Splitters for n_partitions of a registered uint64 column: sample_size keys
- * at counter-based positions (seed), sorted on the device, then the chosen
- * partitioner; repeated splitters are separated so that a heavy key forms its
- * own partition. */
+/* Splitters for n_partitions (2..128) requested partitions of a registered
+ * uint64 column: sample_size keys at positions mix64(seed * 0x9E3779B97F4A7C15
+ * + i) mod n (mix64 = SplitMix64 finalizer), sorted on the device, then the
+ * chosen partitioner; then heavy-key isolation: a splitter not above the last
+ * kept one becomes that one + 1, and a kept value occurring at least m/(2P)
+ * times in the sample is followed by value + 1 so it forms its own partition.
+ * splitters_out needs room for 2 * (n_partitions - 1) values; *n_out receives
+ * the count. */
 vx_status vx_sort_splitters(vx_ctx *ctx, int32_t key_col, int32_t partitioner, uint32_t n_partitions,
-                            uint64_t sample_size, uint64_t seed, uint64_t *splitters_out);
+                            uint64_t sample_size, uint64_t seed, uint64_t *splitters_out, uint32_t *n_out);
 
 /* ---------------------------------------------------------------- join */
 typedef struct {

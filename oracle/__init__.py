@@ -106,7 +106,7 @@ def lib():
                 "or_mlp_loss_grad": ([vp, ci, vp, vp, u64, vp], dbl),
                 "or_adam_step": ([vp, vp, vp, vp, ci, ci, dbl, dbl, dbl, dbl], None),
                 "or_zero_copy_threshold": ([dbl, dbl, dbl, dbl], dbl),
-                "or_isolate_splitters": ([vp, u32], None),
+                "or_isolate_splitters": ([vp, u32, vp, u64, u32, vp], u32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -316,11 +316,14 @@ def pl_splitters(knots, P):
     return out
 
 
-def isolate_splitters(splitters):
-    s = np.array(splitters, dtype=np.uint64, copy=True)
-    if len(s):
-        lib().or_isolate_splitters(_p(s), len(s))
-    return s
+def isolate_splitters(splitters, sorted_sample, P):
+    """Heavy-key isolation: de-duplicate, then give every splitter value that
+    holds at least half a partition's share of the sample its own [v, v+1)."""
+    s = _c(splitters, np.uint64)
+    smp = _c(sorted_sample, np.uint64)
+    out = np.zeros(max(2 * len(s), 1), np.uint64)
+    k = lib().or_isolate_splitters(_p(s), len(s), _p(smp), len(smp), P, _p(out))
+    return out[:k].copy()
 
 
 # ---------------------------------------------------------------- MLP CDF model

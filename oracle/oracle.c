@@ -460,11 +460,25 @@ OR_EXPORT double or_zero_copy_threshold(double elem_bytes, double gather_bytes, 
   return (elem_bytes / gather_bytes) * (bw_zero_copy / bw_copy);
 }
 
-/* Heavy-key isolation of splitters: walking left to right, a splitter that is
- * not above its predecessor v becomes v + 1 (v = UINT64_MAX stays), so that a
- * key value repeated among the sample quantiles gets a partition [v, v + 1)
- * of its own and no partition is empty by construction. */
-OR_EXPORT void or_isolate_splitters(uint64_t *spl, uint32_t n_spl) {
-  for (uint32_t i = 1; i < n_spl; ++i)
-    if (spl[i] <= spl[i - 1]) spl[i] = spl[i - 1] == UINT64_MAX ? UINT64_MAX : spl[i - 1] + 1;
+/* Heavy-key isolation of splitters (P requested partitions, sorted sample of
+ * m keys).  Walking the splitters left to right: a splitter not above the last
+ * one kept becomes that one + 1 (one at UINT64_MAX is dropped); then, if the
+ * kept value v occurs at least m / (2P) times in the sample (half a
+ * partition's share), v + 1 is added as the next boundary so that [v, v + 1)
+ * holds v alone.  Returns the number of splitters written (at most 2(P-1)). */
+OR_EXPORT uint32_t or_isolate_splitters(const uint64_t *spl, uint32_t n_spl, const uint64_t *sample, uint64_t m,
+                                        uint32_t P, uint64_t *out) {
+  uint32_t k = 0;
+  for (uint32_t j = 0; j < n_spl; ++j) {
+    uint64_t v = spl[j];
+    if (k > 0 && v <= out[k - 1]) {
+      if (out[k - 1] == UINT64_MAX) continue;
+      v = out[k - 1] + 1;
+    }
+    out[k++] = v;
+    uint64_t c = 0;
+    for (uint64_t i = 0; i < m; ++i) c += sample[i] == v;
+    if (c * 2 * (uint64_t)P >= m && v != UINT64_MAX) out[k++] = v + 1;
+  }
+  return k;
 }

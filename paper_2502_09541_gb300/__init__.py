@@ -147,7 +147,7 @@ SIGNATURES = {
     "vx_sort": ([_vp, _i32, _i32, _vp, _vp, _P(vx_sort_opts), _P(vx_sort_stats)], _i32),
     "vx_radix_sort_pairs": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_range_partition": ([_vp, _vp, _vp, _u64, _vp, _u32, _vp, _vp, _vp], _i32),
-    "vx_sort_splitters": ([_vp, _i32, _i32, _u32, _u64, _u64, _vp], _i32),
+    "vx_sort_splitters": ([_vp, _i32, _i32, _u32, _u64, _u64, _vp, _P(_u32)], _i32),
     "vx_mlp_loss_grad": ([_vp, _vp, _i32, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_mlp_train": ([_vp, _vp, _i32, _vp, _vp, _u64, _u32, _f32, _vp], _i32),
     "vx_join": ([_vp, _i32, _i32, _i32, _P(vx_join_opts), _P(vx_join_result)], _i32),
@@ -320,9 +320,11 @@ def vx_range_partition(ctx, keys, vals, splitters):
 
 
 def vx_sort_splitters(ctx, key_col: int, partitioner: int, n_partitions: int, sample_size=0, seed=0):
-    out = np.zeros(n_partitions - 1, np.uint64)
-    _check(load().vx_sort_splitters(ctx, key_col, partitioner, n_partitions, sample_size, seed, out.ctypes.data))
-    return out
+    out = np.zeros(2 * (n_partitions - 1), np.uint64)
+    k = ctypes.c_uint32()
+    _check(load().vx_sort_splitters(ctx, key_col, partitioner, n_partitions, sample_size, seed, out.ctypes.data,
+                                    ctypes.byref(k)))
+    return out[:k.value].copy()
 
 
 def vx_mlp_loss_grad(ctx, theta, H, x, t):

@@ -256,15 +256,14 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
   cudaStream_t s = ctx->s_compute;
   DevBuf accb;
   accb.arena = &ctx->arena;
-  accb.p = ctx->arena.alloc(sizeof(JoinAcc) + 8 * 258 + 8 * 258 + 8 * (kPLSegments + 1) + 1024);
+  accb.p = ctx->arena.alloc(256 + kSplitterBufBytes + 8 * 258 + 1024);
   if (!accb.p) {
     set_error("vx_join: arena exhausted");
     return VX_E_NOMEM;
   }
   JoinAcc *acc = accb.as<JoinAcc>();
   uint64_t *d_spl = (uint64_t *)(accb.as<char>() + 256);
-  unsigned long long *d_counts = (unsigned long long *)(d_spl + 258);
-  uint64_t *d_knots = (uint64_t *)(d_counts + 258);
+  unsigned long long *d_counts = (unsigned long long *)((char *)d_spl + kSplitterBufBytes);
   VX_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(JoinAcc), s));
 
   // staging per slot: build side 16 B/row; slots sized by chunk_bytes
@@ -281,22 +280,25 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
   // ---- partitions: P such that each table (at the load factor) fits
   uint32_t P = o.n_partitions > 0 ? (uint32_t)o.n_partitions
                                   : (uint32_t)std::max<double>(1.0, std::ceil(nb / (o.load_factor * slots_max) * 1.05));
-  if (P > 256) {
-    set_error("vx_join: more than 256 partitions needed");
+  if (P > kMaxRequestedPartitions) {
+    set_error("vx_join: more than %u partitions needed", kMaxRequestedPartitions);
     return VX_E_UNSUPPORTED;
   }
   std::vector<uint64_t> spl;
   std::vector<uint64_t> part_n(P, nb);
   double tsp = now_ms();
   if (P > 1) {
-    const uint64_t m = std::min<uint64_t>(o.sample_size ? o.sample_size : (1ull << 20), nb);
+    uint64_t m = std::min<uint64_t>(o.sample_size ? o.sample_size : (1ull << 20), nb);
     DevBuf sbuf;
     uint64_t *sorted = nullptr;
     VX_TRY(sample_and_sort(ctx, (const uint64_t *)bk->dev, nb, m, o.seed, sbuf, &sorted));
     double ms_train = 0;
-    VX_TRY(splitters_from_sample(ctx, o.partitioner, sorted, m, P, d_spl, d_knots, 0, &ms_train));
-    spl.resize(P - 1);
-    VX_CUDA_TRY(cudaMemcpyAsync(spl.data(), d_spl, 8 * (P - 1), cudaMemcpyDeviceToHost, s));
+    uint32_t n_spl = 0;
+    VX_TRY(splitters_from_sample(ctx, o.partitioner, sorted, m, P, d_spl, 0, &ms_train, &n_spl));
+    P = n_spl + 1;  // after heavy-key isolation
+    part_n.assign(P, nb);
+    spl.resize(n_spl);
+    if (n_spl) VX_CUDA_TRY(cudaMemcpyAsync(spl.data(), d_spl, 8ull * n_spl, cudaMemcpyDeviceToHost, s));
     VX_CUDA_TRY(cudaStreamSynchronize(s));
     res.ms_train = ms_train;
     if (o.count_pass) {  // plain form: exact partition sizes from one pass over the build keys

@@ -288,18 +288,39 @@ __global__ void pl_splitters_kernel(const uint64_t *knots, uint32_t S, uint32_t 
   }
 }
 
-// Heavy keys: a value repeated among consecutive splitters would leave empty
-// partitions and one partition [v, next) holding all copies of v plus other
-// keys; the repeat is replaced by v + 1 (if that keeps the order), so that
-// [v, v+1) isolates v as a single-key partition.
-__global__ void isolate_splitters_kernel(uint64_t *spl, uint32_t n_spl) {
+// Heavy keys.  A value repeated among consecutive splitters would leave empty
+// partitions, and one partition [v, next) would hold all copies of v plus
+// other keys.  Walking left to right, a splitter not above the last kept one
+// becomes that one + 1 (dropped at UINT64_MAX); a kept value v that occurs at
+// least m / (2P) times in the sorted sample (half a partition's share) is
+// followed by the boundary v + 1, so [v, v + 1) holds v alone.  At most
+// 2(P-1) splitters result; their count goes to *n_out.
+__global__ void isolate_splitters_kernel(const uint64_t *raw, uint32_t n_raw, const uint64_t *sorted, uint64_t m,
+                                         uint32_t P, uint64_t *out, uint32_t *n_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (uint32_t i = 1; i < n_spl; ++i) {
-    if (spl[i] <= spl[i - 1]) {
-      const uint64_t v = spl[i - 1];
-      spl[i] = v == UINT64_MAX ? v : v + 1;
+  uint32_t k = 0;
+  for (uint32_t j = 0; j < n_raw; ++j) {
+    uint64_t v = raw[j];
+    if (k > 0 && v <= out[k - 1]) {
+      if (out[k - 1] == UINT64_MAX) continue;
+      v = out[k - 1] + 1;
     }
+    out[k++] = v;
+    uint64_t a = 0, b = m;  // lower bound of v
+    while (a < b) {
+      const uint64_t mid = (a + b) >> 1;
+      if (sorted[mid] < v) a = mid + 1;
+      else b = mid;
+    }
+    uint64_t c = a, d = m;  // upper bound of v
+    while (c < d) {
+      const uint64_t mid = (c + d) >> 1;
+      if (sorted[mid] <= v) c = mid + 1;
+      else d = mid;
+    }
+    if ((c - a) * 2 * (uint64_t)P >= m && v != UINT64_MAX) out[k++] = v + 1;
   }
+  *n_out = k;
 }
 
 // ================================================================== host helpers
@@ -362,31 +383,50 @@ vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, 
 }
 
 
-// splitters for P partitions from the sorted sample (device), then heavy-key isolation
+// Splitters for P requested partitions from the sorted sample (device), then
+// heavy-key isolation.  spl_buf has kSplitterBufBytes: [out 256 | raw 256 |
+// knots 1025 | count]; returns the number of splitters in *n_spl (<= 2(P-1)).
 vx_status splitters_from_sample(vx_ctx *ctx, int32_t kind, const uint64_t *sorted, uint64_t m, uint32_t P,
-                                uint64_t *d_spl, uint64_t *d_knots, uint32_t mlp_steps, double *ms_train) {
+                                uint64_t *spl_buf, uint32_t mlp_steps, double *ms_train, uint32_t *n_spl) {
   cudaStream_t s = ctx->s_compute;
+  *n_spl = 0;
   if (P < 2) return VX_OK;
+  if (P > kMaxRequestedPartitions) {
+    set_error("at most %u partitions per pass", kMaxRequestedPartitions);
+    return VX_E_UNSUPPORTED;
+  }
+  uint64_t *d_out = spl_buf, *d_raw = spl_buf + 256, *d_knots = spl_buf + 512;
+  uint32_t *d_n = (uint32_t *)(spl_buf + 512 + kPLSegments + 1);
   if (kind == VX_PART_SAMPLE) {
-    sample_splitters_kernel<<<1, 256, 0, s>>>(sorted, m, P, d_spl);
+    sample_splitters_kernel<<<1, 256, 0, s>>>(sorted, m, P, d_raw);
   } else if (kind == VX_PART_LEARNED_PL) {
     pl_knots_kernel<<<(kPLSegments + 256) / 256, 256, 0, s>>>(sorted, m, kPLSegments, d_knots);
-    pl_splitters_kernel<<<1, 256, 0, s>>>(d_knots, kPLSegments, P, d_spl);
+    pl_splitters_kernel<<<1, 256, 0, s>>>(d_knots, kPLSegments, P, d_raw);
   } else if (kind == VX_PART_LEARNED_MLP) {
-    VX_TRY(mlp_splitters(ctx, sorted, m, P, mlp_steps, d_spl, ms_train));
+    VX_TRY(mlp_splitters(ctx, sorted, m, P, mlp_steps, d_raw, ms_train));
   } else {
     set_error("unknown partitioner %d", kind);
     return VX_E_INVAL;
   }
-  isolate_splitters_kernel<<<1, 32, 0, s>>>(d_spl, P - 1);
+  isolate_splitters_kernel<<<1, 32, 0, s>>>(d_raw, P - 1, sorted, m, P, d_out, d_n);
   VX_CUDA_TRY(cudaGetLastError());
+  VX_CUDA_TRY(cudaMemcpyAsync(n_spl, d_n, 4, cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
   return VX_OK;
 }
 
-// samples m keys of a mapped column and sorts them on the device
-vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t m, uint64_t seed,
+// samples m keys of a mapped column and sorts them on the device; m shrinks to
+// what the free arena holds
+vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t &m, uint64_t seed,
                           DevBuf &sorted_out, uint64_t **sorted_ptr) {
   cudaStream_t s = ctx->s_compute;
+  const uint64_t freeb = ctx->arena.largest_free();
+  const uint64_t m_fit = freeb > (64u << 10) ? (freeb - (64u << 10)) / 25 : 0;
+  m = std::min(m, m_fit);
+  if (m == 0) {
+    set_error("no room in the arena for a key sample");
+    return VX_E_NOMEM;
+  }
   uint64_t bytes = 2 * m * 12 + radix_temp_bytes(m) + 1024;
   sorted_out.arena = &ctx->arena;
   sorted_out.p = ctx->arena.alloc(bytes);
@@ -602,32 +642,36 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     return VX_OK;
   }
   // ---- splitters from a sample
+  // requested partitions: 30% headroom at the top level, 2x inside a recursion
+  const double over = depth == 0 ? 1.3 : 2.0;
   uint32_t P = o.n_partitions > 1 ? (uint32_t)o.n_partitions
-                                  : (uint32_t)std::min<uint64_t>(256, (uint64_t)std::ceil(1.3 * (double)n / cap));
+                                  : (uint32_t)std::min<uint64_t>(kMaxRequestedPartitions,
+                                                                 (uint64_t)std::ceil(over * (double)n / cap));
   if (P < 2) P = 2;
-  if (P > 256) {
-    set_error("vx_sort: at most 256 partitions per pass");
+  if (P > kMaxRequestedPartitions) {
+    set_error("vx_sort: at most %u partitions per pass", kMaxRequestedPartitions);
     return VX_E_UNSUPPORTED;
   }
-  const uint64_t m = std::min<uint64_t>(o.sample_size ? o.sample_size : (1ull << 20), n);
+  uint64_t m = std::min<uint64_t>(o.sample_size ? o.sample_size : (1ull << 20), n);
   DevBuf sbuf, splbuf;
   uint64_t *sorted = nullptr;
   double ts = now_ms();
   VX_TRY(sample_and_sort(ctx, dev_keys, n, m, o.seed + (uint64_t)depth * 7919, sbuf, &sorted));
   splbuf.arena = &ctx->arena;
-  splbuf.p = ctx->arena.alloc(8 * 256 + 8 * (kPLSegments + 1));
+  splbuf.p = ctx->arena.alloc(kSplitterBufBytes);
   if (!splbuf.p) return VX_E_NOMEM;
   uint64_t *d_spl = splbuf.as<uint64_t>();
-  uint64_t *d_knots = d_spl + 256;
   double ms_train = 0;
-  VX_TRY(splitters_from_sample(ctx, o.partitioner, sorted, m, P, d_spl, d_knots, o.mlp_steps, &ms_train));
-  std::vector<uint64_t> spl(P - 1);
-  VX_CUDA_TRY(cudaMemcpyAsync(spl.data(), d_spl, 8 * (P - 1), cudaMemcpyDeviceToHost, ctx->s_compute));
+  uint32_t n_spl = 0;
+  VX_TRY(splitters_from_sample(ctx, o.partitioner, sorted, m, P, d_spl, o.mlp_steps, &ms_train, &n_spl));
+  P = n_spl + 1;  // partitions after heavy-key isolation
+  std::vector<uint64_t> spl(n_spl);
+  if (n_spl) VX_CUDA_TRY(cudaMemcpyAsync(spl.data(), d_spl, 8 * n_spl, cudaMemcpyDeviceToHost, ctx->s_compute));
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
   sbuf.release();
   ss.ms_sample += now_ms() - ts - ms_train;
   ss.ms_train += ms_train;
-  if (depth == 0 && o.splitters_out) memcpy(o.splitters_out, spl.data(), 8 * (P - 1));
+  if (depth == 0 && o.splitters_out) memcpy(o.splitters_out, spl.data(), 8 * n_spl);
 
   // ---- host intermediate
   uint64_t *mid_keys = nullptr;
@@ -894,27 +938,29 @@ VX_API vx_status vx_range_partition(vx_ctx *ctx, const uint64_t *keys, const uin
 }
 
 VX_API vx_status vx_sort_splitters(vx_ctx *ctx, int32_t key_col, int32_t partitioner, uint32_t n_partitions,
-                                   uint64_t sample_size, uint64_t seed, uint64_t *splitters_out) {
+                                   uint64_t sample_size, uint64_t seed, uint64_t *splitters_out, uint32_t *n_out) {
   clear_error();
   VX_TRY(check_ctx(ctx));
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
   const Column *kc = get_col(ctx, key_col, VX_U64);
   if (!kc) return VX_E_INVAL;
-  if (n_partitions < 2 || n_partitions > 256 || !splitters_out || kc->n_rows == 0) {
-    set_error("vx_sort_splitters: need 2..256 partitions, output, non-empty column");
+  if (n_partitions < 2 || n_partitions > kMaxRequestedPartitions || !splitters_out || !n_out || kc->n_rows == 0) {
+    set_error("vx_sort_splitters: need 2..%u partitions, outputs, non-empty column", kMaxRequestedPartitions);
     return VX_E_INVAL;
   }
-  const uint64_t m = std::min<uint64_t>(sample_size ? sample_size : (1ull << 20), kc->n_rows);
+  uint64_t m = std::min<uint64_t>(sample_size ? sample_size : (1ull << 20), kc->n_rows);
   DevBuf sbuf, splbuf;
   uint64_t *sorted = nullptr;
   VX_TRY(sample_and_sort(ctx, (const uint64_t *)kc->dev, kc->n_rows, m, seed, sbuf, &sorted));
   splbuf.arena = &ctx->arena;
-  splbuf.p = ctx->arena.alloc(8 * 256 + 8 * (kPLSegments + 1));
+  splbuf.p = ctx->arena.alloc(kSplitterBufBytes);
   if (!splbuf.p) return VX_E_NOMEM;
   uint64_t *d_spl = splbuf.as<uint64_t>();
   double ms = 0;
-  VX_TRY(splitters_from_sample(ctx, partitioner, sorted, m, n_partitions, d_spl, d_spl + 256, 0, &ms));
-  VX_CUDA_TRY(cudaMemcpyAsync(splitters_out, d_spl, 8 * (n_partitions - 1), cudaMemcpyDeviceToHost, ctx->s_compute));
+  uint32_t k = 0;
+  VX_TRY(splitters_from_sample(ctx, partitioner, sorted, m, n_partitions, d_spl, 0, &ms, &k));
+  if (k) VX_CUDA_TRY(cudaMemcpyAsync(splitters_out, d_spl, 8ull * k, cudaMemcpyDeviceToHost, ctx->s_compute));
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  *n_out = k;
   return VX_OK;
 }

@@ -16,11 +16,15 @@ RadixState *radix_state_of(char *temp);
 vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms);
 vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, uint32_t P, char *temp,
                                   cudaStream_t s);
-vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t m, uint64_t seed,
+constexpr uint32_t kMaxRequestedPartitions = 128;  // isolation may add up to P-1 boundaries
+constexpr uint64_t kSplitterBufBytes = 8ull * (512 + kPLSegments + 1 + 8);
+
+vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t &m, uint64_t seed,
                           DevBuf &sorted_out, uint64_t **sorted_ptr);
-// P-1 splitters from a sorted device sample with partitioner `kind`, then heavy-key isolation
+// splitters for P requested partitions from a sorted device sample with
+// partitioner `kind`, then heavy-key isolation; *n_spl receives their count
 vx_status splitters_from_sample(vx_ctx *ctx, int32_t kind, const uint64_t *sorted, uint64_t m, uint32_t P,
-                                uint64_t *d_spl, uint64_t *d_knots, uint32_t mlp_steps, double *ms_train);
+                                uint64_t *spl_buf, uint32_t mlp_steps, double *ms_train, uint32_t *n_spl);
 // trains the monotone CDF MLP on the sorted sample and writes P-1 splitters
 vx_status mlp_splitters(vx_ctx *ctx, const uint64_t *sorted, uint64_t m, uint32_t P, uint32_t steps, uint64_t *d_spl,
                         double *ms_train);

@@ -94,7 +94,7 @@ def test_splitters_bit_exact(ctx, dist, kind, P):
         vx.vx_unregister_host_column(ctx, cid)
     s = O.sorted_u64(_library_sample(k, m, seed))
     exp = O.sample_splitters(s, P) if kind == "sample" else O.pl_splitters(O.pl_knots(s, 1024), P)
-    assert np.array_equal(got, O.isolate_splitters(exp))
+    assert np.array_equal(got, O.isolate_splitters(exp, s, P))
 
 
 def test_mlp_splitters_monotone_and_cover(ctx):

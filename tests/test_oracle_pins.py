@@ -404,11 +404,21 @@ def test_threshold_reduces_to_paper_value():
 
 
 def test_isolate_splitters_separates_heavy_keys():
-    s = O.isolate_splitters(np.array([5, 9, 9, 9, 12, 12, 2**64 - 1, 2**64 - 1], np.uint64))
-    assert s.tolist() == [5, 9, 10, 11, 12, 13, 2**64 - 1, 2**64 - 1]
-    # a heavy key repeated among sample quantiles ends in a partition of its own
-    k = np.array([3] * 50 + list(range(100, 150)), np.uint64)
-    spl = O.isolate_splitters(O.sample_splitters(O.sorted_u64(k), 8))
-    pid = np.searchsorted(spl, k, side="right")
-    heavy = set(pid[k == 3].tolist())
-    assert len(heavy) == 1 and set(k[pid == heavy.pop()].tolist()) == {3}
+    smp = np.array([1, 2, 9, 9, 9, 9, 11, 12, 12, 20], np.uint64)  # m = 10
+    # P = 4: a value is heavy if it occurs >= 10 / 8 times -> 9 (4x) and 12 (2x)
+    s = O.isolate_splitters(np.array([9, 9, 12], np.uint64), smp, 4)
+    assert s.tolist() == [9, 10, 11, 12, 13]
+    s = O.isolate_splitters(np.array([5, 5, 2**64 - 1, 2**64 - 1], np.uint64), smp, 5)
+    assert s.tolist() == [5, 6, 2**64 - 1]
+    # a key holding >= 1/P of the sample covers a quantile, so it is a
+    # splitter and ends in a partition of its own, also when it is the
+    # smallest key or sits on a single quantile
+    for k in (np.array([3] * 60 + list(range(100, 140)), np.uint64),
+              np.array(list(range(0, 33)) + [50] * 35 + list(range(60, 92)), np.uint64),
+              np.array(list(range(0, 20)) + [50] * 36 + list(range(60, 104)), np.uint64)):
+        sk = O.sorted_u64(k)
+        spl = O.isolate_splitters(O.sample_splitters(sk, 3), sk, 3)
+        pid = np.searchsorted(spl, k, side="right")
+        heavy = int(np.bincount(k.astype(np.int64)).argmax())
+        parts = set(pid[k == heavy].tolist())
+        assert len(parts) == 1 and set(k[pid == parts.pop()].tolist()) == {heavy}
