@@ -129,6 +129,36 @@ typedef struct {
 vx_status vx_filter(vx_ctx *ctx, const vx_pred *preds, int32_t n_preds, uint64_t row_begin,
                     uint64_t row_end, uint64_t *out_rows, uint64_t cap, uint64_t *out_count);
 
+/* Allocation-free filter over device-resident columns.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate device memory — code running inside another framework's memory
+ * manager that owns all device memory and hands out only input and output
+ * buffers, and latency-critical paths where a cudaMalloc/cudaFree (which may
+ * synchronise the device) is not acceptable.  It needs no context.
+ *
+ * cols: host array of n_cols device pointers to int32 columns of n_rows
+ * elements; preds[q].col indexes cols.  Writes the ascending ids row0 + i of
+ * the rows satisfying every predicate to the device buffer out_rows[0 ..
+ * min(count, cap)) and the full count to *out_count (host).  stream: the
+ * caller's cudaStream_t (NULL = default stream); the call returns after the
+ * work on that stream has finished.
+ *
+ * Scratch lives in a fixed file-scope device array (256 KiB + 256 B, held on
+ * every GPU that loads the library until the process exits); it allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  Limits and
+ * behaviour:
+ *   - n_rows above 67,108,864 (2^26) returns VX_E_INVAL;
+ *   - count > cap returns VX_E_CAPACITY after writing the first cap ids;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture;
+ *   - every call shares the one array, so calls whose work overlaps on the
+ *     GPU (other streams, other host threads) race and give wrong results:
+ *     serialise them. */
+vx_status vx_filter_device_static(const int32_t *const *cols, int32_t n_cols, const vx_pred *preds,
+                                  int32_t n_preds, uint64_t n_rows, uint64_t row0, uint64_t *out_rows,
+                                  uint64_t cap, uint64_t *out_count, void *stream);
+
 /* ---------------------------------------------------------------- plans */
 enum { VX_AGG_COUNT = 0, VX_AGG_SUM = 1, VX_AGG_MUL = 2, VX_AGG_SUB = 3 };
 #define VX_MAX_DIMS 8

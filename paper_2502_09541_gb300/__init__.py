@@ -151,6 +151,7 @@ SIGNATURES = {
     "vx_mlp_loss_grad": ([_vp, _vp, _i32, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_mlp_train": ([_vp, _vp, _i32, _vp, _vp, _u64, _u32, _f32, _vp], _i32),
     "vx_join": ([_vp, _i32, _i32, _i32, _P(vx_join_opts), _P(vx_join_result)], _i32),
+    "vx_filter_device_static": ([_vp, _i32, _P(vx_pred), _i32, _u64, _u64, _vp, _u64, _P(_u64), _vp], _i32),
 }
 
 
@@ -228,6 +229,19 @@ def vx_filter(ctx, preds, row_begin=0, row_end=0, out: np.ndarray | None = None)
     cnt = ctypes.c_uint64()
     st = load().vx_filter(ctx, arr, len(preds), row_begin, row_end, None if out is None else out.ctypes.data,
                           0 if out is None else len(out), ctypes.byref(cnt))
+    if st not in (VX_OK, VX_E_CAPACITY):
+        _check(st)
+    return st, cnt.value
+
+
+def vx_filter_device_static(col_ptrs, preds, n_rows: int, row0: int, out_ptr: int, cap: int, stream: int = 0):
+    """Allocation-free filter over device columns (col_ptrs: device addresses;
+    preds: (index into col_ptrs, op, lo, hi)).  Returns (status, count)."""
+    cols = (ctypes.c_void_p * len(col_ptrs))(*col_ptrs)
+    arr = (vx_pred * len(preds))(*[vx_pred(*p) for p in preds])
+    cnt = ctypes.c_uint64()
+    st = load().vx_filter_device_static(cols, len(col_ptrs), arr, len(preds), n_rows, row0, out_ptr or None, cap,
+                                        ctypes.byref(cnt), stream or None)
     if st not in (VX_OK, VX_E_CAPACITY):
         _check(st)
     return st, cnt.value
