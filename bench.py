@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -47,6 +48,11 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=4.0)
     ap.add_argument("--cpu-sample-rows", type=int, default=0, help="oracle sample rows (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip serving, sort and join measurements")
+    ap.add_argument("--serve-queries", type=int, default=400)
+    ap.add_argument("--sort-pairs", type=int, default=1_000_000_000)
+    ap.add_argument("--join-build", type=int, default=250_000_000)
+    ap.add_argument("--join-probe", type=int, default=2_000_000_000)
     return ap.parse_args()
 
 
@@ -194,6 +200,119 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(vx, G, ctx, fid, did, args):
+    """Continuous batching: Poisson arrivals of star queries (templates mixed,
+    sizes log-uniform over [1M rows, whole table], random offsets); mean
+    inter-arrival = half the mean single-query link time at the measured peak."""
+    rng = __import__("numpy").random.default_rng(1)
+    names = TEMPLATES
+    n = args.rows
+    qs = []
+    for _ in range(args.serve_queries):
+        size = int(math.exp(rng.uniform(math.log(1_000_000), math.log(n))))
+        rb = int(rng.integers(0, n - size + 1))
+        qs.append((names[int(rng.integers(0, len(names)))], rb, rb + size))
+    mean_rows = sum(q[2] - q[1] for q in qs) / len(qs)
+    gap_s = 0.5 * mean_rows * 20 / 210e9
+    tmpls = G.star_templates()
+    vx.vx_serve_start(ctx, chunk_rows=1 << 21, max_active=32)
+    t0 = time.perf_counter()
+    tickets = []
+    next_t = t0
+    for name, rb, re in qs:
+        now = time.perf_counter()
+        if next_t > now:
+            time.sleep(next_t - now)
+        tickets.append(vx.vx_submit(ctx, vx.make_plan(tmpls[name], fid, did, G.STAR_ATTR_CARD,
+                                                      vx.VX_LATE_AUTO, rb, re)))
+        next_t += float(rng.exponential(gap_s))
+    for t in tickets:
+        st = vx.vx_wait(ctx, t)[0]
+        assert st == vx.VX_OK
+    wall = time.perf_counter() - t0
+    s = vx.vx_serve_stats_get(ctx)
+    vx.vx_serve_stop(ctx)
+    logical = sum((q[2] - q[1]) * 4 * (len(tmpls[q[0]]["dims"]) + len(tmpls[q[0]]["fact_preds"]) + 2)
+                  for q in qs)
+    return {"queries": len(qs), "p50_ms": round(s["p50_ms"], 3), "p99_ms": round(s["p99_ms"], 3),
+            "mean_ms": round(s["mean_ms"], 3), "max_ms": round(s["max_ms"], 3),
+            "qps": round(len(qs) / wall, 2), "host_gbs": round(logical / wall / 1e9, 3),
+            "scan_h2d_gbs": round(s["bytes_h2d"] / wall / 1e9, 3), "active_peak": int(s["active_peak"]),
+            "mean_interarrival_ms": round(gap_s * 1e3, 3), "form": "shared circular scan"}
+
+
+def run_sort_extra(vx, G, args):
+    """Out-of-core sort of (uint64 key, uint32 row id) pairs, Zipf(1.1) keys,
+    16 GiB budget: sample splitters (plain) vs learned PL and MLP models."""
+    import numpy as np
+    n = args.sort_pairs
+    t0 = time.perf_counter()
+    k, r = G.sort_input(n, "zipf")
+    gen = time.perf_counter() - t0
+    ok = np.empty(n, np.uint64)
+    orr = np.empty(n, np.uint32)
+    scratch = np.empty(12 * n, np.uint8)
+    ctx = vx.vx_open(16 << 30)
+    out = {"pairs": n, "dist": "zipf(1.1)", "budget_gib": 16, "generate_s": round(gen, 1)}
+    try:
+        kc = vx.vx_register_host_column(ctx, "k", k)
+        rc = vx.vx_register_host_column(ctx, "r", r)
+        # page-lock the output and scratch buffers once, outside the timed sorts
+        for buf in (ok, orr, scratch):
+            vx.vx_register_host_column(ctx, "pin", buf.view(np.uint32) if buf.dtype != np.uint32 else buf)
+        for name, part in (("plain_sample", vx.VX_PART_SAMPLE), ("learned_pl", vx.VX_PART_LEARNED_PL),
+                           ("learned_mlp", vx.VX_PART_LEARNED_MLP)):
+            o = vx.vx_sort_opts()
+            o.partitioner = part
+            o.host_scratch = scratch.ctypes.data
+            o.host_scratch_bytes = scratch.nbytes
+            o.sample_size = 1 << 20
+            st = vx.vx_sort(ctx, kc, rc, ok, orr, o)
+            out[name] = {"gpairs_s": round(n / st["ms_total"] / 1e6, 3), "ms": round(st["ms_total"], 1),
+                         "partitions": st["n_partitions"], "imbalance": round(st["imbalance"], 3),
+                         "passthrough": st["passthrough_partitions"], "overflow_retries": st["overflow_retries"],
+                         "ms_partition": round(st["ms_partition"], 1), "ms_sort": round(st["ms_sort"], 1),
+                         "ms_train": round(st["ms_train"], 1),
+                         "link_gbs": round((st["bytes_h2d"] + st["bytes_d2h"]) / st["ms_total"] / 1e6, 1)}
+        out["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
+    finally:
+        vx.vx_close(ctx)
+    return out
+
+
+def run_join_extra(vx, G, args):
+    """Partitioned hash join: unique build keys with payload, uniform probe
+    keys at match rate 1.0, 24 GiB budget; plain (exact count pass) vs learned
+    (model-implied table sizes) at P = 2, and the planner's own P."""
+    nb, npr = args.join_build, args.join_probe
+    t0 = time.perf_counter()
+    bk, bp = G.build_side(nb)
+    pk = G.probe_side(npr, nb, 1.0, 0.0)
+    gen = time.perf_counter() - t0
+    ctx = vx.vx_open(24 << 30)
+    out = {"build_rows": nb, "probe_rows": npr, "budget_gib": 24, "generate_s": round(gen, 1)}
+    try:
+        a = vx.vx_register_host_column(ctx, "bk", bk)
+        b = vx.vx_register_host_column(ctx, "bp", bp)
+        p = vx.vx_register_host_column(ctx, "pk", pk)
+        for name, P, cp, part in (("planner", 0, 0, vx.VX_PART_LEARNED_PL), ("plain_p2", 2, 1, vx.VX_PART_SAMPLE),
+                                  ("learned_p2", 2, 0, vx.VX_PART_LEARNED_PL)):
+            o = vx.vx_join_opts()
+            o.n_partitions = P
+            o.count_pass = cp
+            o.partitioner = part
+            r = vx.vx_join(ctx, a, b, p, o)
+            out[name] = {"gtuples_s": round((nb + npr) / r["ms_total"] / 1e6, 3), "ms": round(r["ms_total"], 1),
+                         "partitions": r["n_partitions"], "count": r["count"],
+                         "link_gbs": round(r["bytes_h2d"] / r["ms_total"] / 1e6, 1),
+                         "overflow_retries": r["overflow_retries"], "ms_build": round(r["ms_build"], 1),
+                         "ms_probe": round(r["ms_probe"], 1), "ms_kernel": round(r["ms_kernel"], 1)}
+        out["count_ok"] = out["planner"]["count"] == npr
+    finally:
+        vx.vx_close(ctx)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -222,35 +341,47 @@ def run_ours(args):
     # link peak measured in this run (pinned copies, 64 MiB chunks)
     h2d_peak, d2h_peak, bid_peak = vx.vx_probe_link(ctx, min(2 << 30, budget // 4), 64 << 20)
 
-    def step(collect):
-        for p in plans:
+    def step(collect, plan_list=None):
+        for p in plan_list or plans:
             st, gid, s, c, stats = vx.vx_run_plan(ctx, p)
             assert st == vx.VX_OK
             collect.append(stats)
 
-    for _ in range(max(args.warmup, 3)):
-        step([])
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    stats_all = []
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def timed(n_steps, plan_list=None):
+        """n_steps steps between CUDA events on the library's compute stream."""
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        out = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
-            step(stats_all)
+        for _ in range(n_steps):
+            step(out, plan_list)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / n_steps, out
+
+    # ---- plain form: executor with host-issued copies, 64 MiB chunks, one
+    # late/early decision per plan; its warm-up steps log per-chunk statistics
+    cfg = vx.vx_get_config(ctx)
+    cfg.log_chunk_stats = 1
+    vx.vx_set_config(ctx, cfg)
+    for _ in range(max(args.warmup, 3)):
+        step([])
+    cfg.log_chunk_stats = 0
+    vx.vx_set_config(ctx, cfg)
+    with ClockSampler(local) as clk:
+        ms_step, stats_all = timed(args.steps)
+    clocks = clk.summary()
     logical = sum(s["bytes_logical"] for s in stats_all) / args.steps
     link = sum(s["bytes_h2d"] + s["bytes_zero_copy"] for s in stats_all) / args.steps
-    host_gbs = logical * world / (ms_step * 1e6)
+    plain_gbs = logical * world / (ms_step * 1e6)
     link_gbs = link / (ms_step * 1e6)
     launches = int(sum(s["kernel_launches"] for s in stats_all))
     kern_ms = sum(s["ms_kernel"] for s in stats_all)
@@ -273,6 +404,34 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": round(staged_bytes / max(1, launches)),
                 "avg_launch_us": round(1000 * kern_ms / max(1, launches), 2)}
 
+    # ---- learned / batched form: regressor trained on the plain form's log,
+    # per-chunk late/early decisions, autotuned chunking, captured graphs
+    w, n_log = vx.vx_regressor_train(ctx, 1e-6)
+    tuned = vx.vx_autotune(ctx, plans[TEMPLATES.index("T3_1")], min(args.rows, 100_000_000))
+    cfg = vx.vx_get_config(ctx)
+    cfg.use_graphs = 1
+    vx.vx_set_config(ctx, cfg)
+    lplans = [vx.make_plan(tmpls[n], fid, did, G.STAR_ATTR_CARD, vx.VX_LATE_PER_CHUNK) for n in TEMPLATES]
+    step([], lplans)  # captures the graphs
+    with ClockSampler(local) as clk2:
+        ms_learned, stats_l = timed(args.steps, lplans)
+    learned_gbs = sum(s["bytes_logical"] for s in stats_l) / args.steps * world / (ms_learned * 1e6)
+    link_l = sum(s["bytes_h2d"] + s["bytes_zero_copy"] for s in stats_l) / args.steps / (ms_learned * 1e6)
+    forms = {
+        "plain": {"value": round(plain_gbs, 3), "ms_per_step": round(ms_step, 3), "link_gbs": round(link_gbs, 1),
+                  "chunk_bytes": 64 << 20, "sched": "immediate", "late": "per plan"},
+        "learned": {"value": round(learned_gbs, 3), "ms_per_step": round(ms_learned, 3),
+                    "link_gbs": round(link_l, 1), "chunk_bytes": int(tuned.chunk_bytes),
+                    "n_slots": int(tuned.n_slots), "graphs": True, "late": "per chunk (regressor)",
+                    "regressor_chunks_logged": int(n_log), "clocks": clk2.summary()},
+    }
+    use_learned = learned_gbs >= plain_gbs
+    host_gbs = learned_gbs if use_learned else plain_gbs
+    cfg.use_graphs = 0
+    cfg.chunk_bytes = 64 << 20
+    cfg.n_slots = 3
+    vx.vx_set_config(ctx, cfg)
+
     # end to end through the public call: dimension tables rebuilt from host
     # columns every step, fact chunks copied from pinned host memory, results
     # read back to host
@@ -287,14 +446,18 @@ def run_ours(args):
     e2e_d2h = sum(s["bytes_d2h"] for s in e2e_stats) / args.steps
     e2e_gbs = logical * world / (e2e_s * 1e9)
 
+    serving = run_serving(vx, G, ctx, fid, did, args) if not args.no_extras else None
+
     line = {
         "metric": METRIC, "value": round(host_gbs, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_learned if use_learned else ms_step, 3),
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"star join: {args.rows}-row fact (8 int32 cols, host-resident), dims 2556/200000/"
                                f"2000000/30000, templates {TEMPLATES}, budget {args.budget_gb} GiB",
                    "rows": args.rows, "l2": "inputs larger than L2 (fact columns stream from host)",
-                   "chunk_bytes": int(vx.vx_get_config(ctx).chunk_bytes), "form": "plain"},
+                   "form": "learned" if use_learned else "plain"},
+        "forms": forms,
         "link": {"h2d_peak_gbs": round(h2d_peak, 1), "d2h_peak_gbs": round(d2h_peak, 1),
                  "bidir_peak_gbs": round(bid_peak, 1), "link_gbs": round(link_gbs, 1),
                  "link_frac": round(link_gbs / h2d_peak, 4), "host_frac": round(host_gbs / world / h2d_peak, 4)},
@@ -304,15 +467,22 @@ def run_ours(args):
         "e2e": {"value": round(e2e_gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": int(e2e_h2d),
                 "d2h_bytes_per_step": int(e2e_d2h)},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "setup_s": {"generate": round(t_gen, 1)},
     }
+    if serving:
+        line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = args.cpu_sample_rows or min(args.rows, 20_000_000)
         v, cores, dt = cpu_baseline(fact, dims, sample)
         line["cpu_baseline"] = {"value": round(v, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                                 "sample": f"first {sample} fact rows x 6 templates ({dt:.1f} s)"}
     vx.vx_close(ctx)
+    del arena
+    if rank == 0 and world == 1 and not args.no_extras:
+        del fact
+        line["sort"] = run_sort_extra(vx, G, args)
+        line["join"] = run_join_extra(vx, G, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

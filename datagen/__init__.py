@@ -86,6 +86,7 @@ def lib():
                 "vxg_date_of_key": ([i32, vp, vp], None),
                 "vxg_fill_child_code": ([vp, vp, u64, i32, i32, u64, u64], None),
                 "vxg_sample_positions": ([vp, u64, u64, u64, u64], None),
+                "vxg_fill_i32_ramp": ([vp, u64, u64, u64, i32, ci], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -227,13 +228,19 @@ def star_dims(seed=0):
     return dims
 
 
-def star_fact(n, seed=0, row0=0, out=None):
-    """Eight fact columns (int32): four uniform foreign keys and four measures."""
+def star_fact(n, seed=0, row0=0, out=None, clustered_date=False, total=None):
+    """Eight fact columns (int32): four uniform foreign keys and four measures.
+    clustered_date: date_fk ascends with the row (a table appended in date
+    order) instead of being uniform; `total` is the table's full row count."""
     out = out or {}
     rng = {"date_fk": (0, 2555), "fk_supp": (0, 199_999), "fk_part": (0, 1_999_999),
            "fk_cust": (0, 29_999), "quantity": (1, 50), "discount": (0, 10),
            "price": (90_000, 10_000_000), "cost": (1_000, 100_000)}
-    return {c: i32_uniform(n, lo, hi, seed, SALT[c], row0, out.get(c)) for c, (lo, hi) in rng.items()}
+    cols = {c: i32_uniform(n, lo, hi, seed, SALT[c], row0, out.get(c)) for c, (lo, hi) in rng.items()}
+    if clustered_date:
+        d = cols["date_fk"]
+        lib().vxg_fill_i32_ramp(_ptr(d), n, row0, total or n, DATE_ROWS, NTHREADS)
+    return cols
 
 
 def star_templates():

@@ -379,6 +379,21 @@ VXG_EXPORT void vxg_fill_child_code(int32_t *out, const int32_t *parent, uint64_
   }
 }
 
+/* Clustered column: row g of a total-row table gets floor(g * card / total), a
+ * non-decreasing ramp (a fact table appended in key order). */
+static void f_ramp(const job *j, uint64_t b, uint64_t e) {
+  int32_t *o = (int32_t *)j->out;
+  for (uint64_t i = b; i < e; ++i)
+    o[i] = (int32_t)(((unsigned __int128)(j->row0 + i) * (uint64_t)j->hi) / j->n_items);
+}
+
+VXG_EXPORT void vxg_fill_i32_ramp(int32_t *out, uint64_t n, uint64_t row0, uint64_t total, int32_t card,
+                                  int nthreads) {
+  job p = {0};
+  p.fn = f_ramp; p.out = out; p.row0 = row0; p.n_items = total ? total : 1; p.hi = card;
+  fan_out(p, n, nthreads);
+}
+
 /* Sample positions: m positions drawn uniformly with replacement from [0, n). */
 VXG_EXPORT void vxg_sample_positions(uint64_t *out, uint64_t m, uint64_t n, uint64_t seed, uint64_t salt) {
   uint64_t base = vxg_base(seed, salt);

@@ -60,7 +60,12 @@ typedef struct vx_ctx vx_ctx;
 
 /* ---------------------------------------------------------------- config */
 enum { VX_SCHED_IMMEDIATE = 0, VX_SCHED_DAG = 1 };
-enum { VX_LATE_AUTO = 0, VX_LATE_FORCE_EARLY = 1, VX_LATE_FORCE_LATE = 2 };
+/* Late materialization of a plan's aggregate columns (Section 6.3):
+ * AUTO decides once per plan (estimated selectivity below TH -> zero-copy);
+ * PER_CHUNK decides per chunk from the per-chunk cardinality regressor's
+ * predicted selectivity (or the chunk's sampled selectivity while no
+ * regressor is trained). */
+enum { VX_LATE_AUTO = 0, VX_LATE_FORCE_EARLY = 1, VX_LATE_FORCE_LATE = 2, VX_LATE_PER_CHUNK = 3 };
 
 typedef struct {
   uint64_t chunk_bytes;     /* staged host bytes per chunk, all staged columns (default 64 MiB) */
@@ -74,6 +79,9 @@ typedef struct {
   int32_t block_threads;    /* threads per block of the chunk kernels (default 256) */
   int32_t blocks_per_sm;    /* resident blocks per SM of the chunk kernels (default 4) */
   uint32_t wait_timeout_ms; /* limit of every host-side wait (default 60000) */
+  int32_t log_chunk_stats;  /* vx_run_plan logs per-chunk features and survivor fractions (the
+                               cardinality regressor's training data); not with use_graphs */
+  int32_t reserved;
 } vx_config;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -219,6 +227,7 @@ typedef struct {
   double ms_total;         /* wall time of the call */
   double ms_kernel;        /* summed device time of the chunk kernels (CUDA events) */
   uint64_t kernel_launches;/* kernels launched by the call */
+  uint64_t late_chunks;    /* VX_LATE_PER_CHUNK: chunks whose aggregate columns were read by zero-copy */
 } vx_query_stats;
 
 /* Result of vx_run_plan / vx_groupby: groups with count > 0 in ascending group
@@ -241,6 +250,40 @@ vx_status vx_run_plan(vx_ctx *ctx, const vx_plan *plan, vx_result *out);
  * dimensions): keys are int32 fact columns with codes in [0, card). */
 vx_status vx_groupby(vx_ctx *ctx, const vx_plan_gkey *keys, int32_t n_keys, int32_t agg_op, int32_t agg_a,
                      int32_t agg_b, const vx_pred *preds, int32_t n_preds, vx_result *out);
+
+/* ---------------------------------------------------------------- cardinality regressor */
+
+/* Ridge least squares on the device: w = argmin |X w - y|^2 + lambda |w|^2 for
+ * n host rows of d <= 8 fp32 features (row-major X), from the normal equations
+ * accumulated in fp64 and solved by Cholesky factorisation.  VX_E_INVAL if the
+ * system is singular. */
+vx_status vx_regressor_fit(vx_ctx *ctx, const float *X, const float *y, uint64_t n, int32_t d, float lambda,
+                           float *w_out);
+
+/* Per-chunk cardinality regressor: fits the statistics that plans logged
+ * with log_chunk_stats (per chunk, from 256 sampled rows: features [1, f_fact
+ * (fraction passing the fact predicates), f_all (fraction passing every
+ * predicate and probe), f_fact x the product over dimensions of the fraction
+ * whose key passes that dimension's filter]; target = exact survivor
+ * fraction) and keeps
+ * the 4 weights in the context; VX_LATE_PER_CHUNK plans then decide late vs
+ * early materialization per chunk from the predicted selectivity against TH
+ * (Section 6.3 decides from an estimator S_c given before the operator runs). */
+vx_status vx_regressor_train(vx_ctx *ctx, float lambda, float *w_out, uint64_t *n_used);
+
+/* Copies up to cap logged (features, target) rows; *n = rows logged. */
+vx_status vx_chunk_log(vx_ctx *ctx, float *X, float *y, uint64_t cap, uint64_t *n);
+/* Clears the log and the trained regressor. */
+vx_status vx_chunk_log_clear(vx_ctx *ctx);
+
+/* Autotuner of the executor for one plan: times the plan over its first
+ * sample_rows fact rows for every chunk size in {8, 16, 32, 64, 128, 256} MiB
+ * and staging ring depth in {2, 3, 4} that fits the arena (best of two timed
+ * runs after one warm-up each), keeps the fastest in the context's config and
+ * returns it.  Section 8.1 sweeps Exchange's packet size the same way (fixed
+ * per-copy overhead against pipeline depth).  Results do not depend on the
+ * configuration, only the time does. */
+vx_status vx_autotune(vx_ctx *ctx, const vx_plan *plan, uint64_t sample_rows, vx_config *best);
 
 /* Frees the dimension hash tables that vx_run_plan keeps resident on the
  * device between calls (Section 7.1 keeps filtered dimension tables on the
@@ -366,6 +409,42 @@ vx_status vx_mlp_loss_grad(vx_ctx *ctx, const float *theta, int32_t H, const flo
  * final loss. */
 vx_status vx_mlp_train(vx_ctx *ctx, float *theta, int32_t H, const float *x, const float *t, uint64_t m,
                        uint32_t steps, float lr, float *loss_out);
+
+/* ---------------------------------------------------------------- serving */
+typedef struct {
+  uint64_t chunk_rows;  /* rows per chunk of the shared scan, multiple of 1024 (0 = 1 Mi) */
+  uint32_t max_active;  /* queries attached to the scan at once (0 = 32, <= 256) */
+  uint32_t n_slots;     /* staging slots (0 = 3) */
+} vx_serve_opts;
+
+typedef struct {
+  uint64_t submitted, completed, failed, cycles, bytes_h2d, active_peak;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency from vx_submit to completion */
+  double wall_ms;                         /* since vx_serve_start */
+} vx_serve_stats;
+
+/* Starts the serving engine of a context: a thread that runs one shared
+ * circular scan over the registered fact columns.  Each cycle stages one chunk
+ * (the union of the columns its attached queries read, copied once) and runs
+ * one persistent multi-query kernel over it.  Submitted star plans are
+ * admitted when their accumulators and dimension tables fit the device budget
+ * (tables stay resident and are shared by plans with equal dimension
+ * filters) and attach at the current chunk (continuous batching); a query
+ * completes once it has seen every chunk of its row range.  Results equal
+ * vx_run_plan's.  While serving, other calls on the context are serialised
+ * with the engine. */
+vx_status vx_serve_start(vx_ctx *ctx, const vx_serve_opts *opts);
+/* Queues a plan; *ticket identifies it.  Does not block on device work. */
+vx_status vx_submit(vx_ctx *ctx, const vx_plan *plan, uint64_t *ticket);
+/* *done = 1 once the query finished; then fills out (groups, stats with
+ * stats.ms_total = latency) and returns the query's status. */
+vx_status vx_poll(vx_ctx *ctx, uint64_t ticket, vx_result *out, int32_t *done);
+/* Blocks until the query finished or timeout_ms passed (VX_E_TIMEOUT). */
+vx_status vx_wait(vx_ctx *ctx, uint64_t ticket, vx_result *out, uint32_t timeout_ms);
+/* Counters and latency percentiles of completed queries. */
+vx_status vx_serve_stats_get(vx_ctx *ctx, vx_serve_stats *out);
+/* Stops the engine (pending queries are dropped); vx_close also does this. */
+vx_status vx_serve_stop(vx_ctx *ctx);
 
 /* ---------------------------------------------------------------- link probe */
 

@@ -22,7 +22,7 @@ VX_OK, VX_E_INVAL, VX_E_NOMEM, VX_E_CUDA, VX_E_CAPACITY, VX_E_TIMEOUT, VX_E_BUSY
     VX_E_DUPKEY, VX_E_RANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 VX_I32, VX_U32, VX_I64, VX_U64 = 0, 1, 2, 3
 VX_SCHED_IMMEDIATE, VX_SCHED_DAG = 0, 1
-VX_LATE_AUTO, VX_LATE_FORCE_EARLY, VX_LATE_FORCE_LATE = 0, 1, 2
+VX_LATE_AUTO, VX_LATE_FORCE_EARLY, VX_LATE_FORCE_LATE, VX_LATE_PER_CHUNK = 0, 1, 2, 3
 VX_BETWEEN, VX_EQ, VX_NE, VX_LT, VX_LE, VX_GT, VX_GE = range(7)
 VX_AGG_COUNT, VX_AGG_SUM, VX_AGG_MUL, VX_AGG_SUB = range(4)
 VX_MAX_DIMS, VX_MAX_PREDS, VX_MAX_GKEYS = 8, 8, 4
@@ -43,7 +43,8 @@ class vx_config(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint64), ("n_slots", ctypes.c_int32), ("sched", ctypes.c_int32),
                 ("late_mat", ctypes.c_int32), ("zc_threshold", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("wait_timeout_ms", ctypes.c_uint32)]
+                ("wait_timeout_ms", ctypes.c_uint32), ("log_chunk_stats", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class vx_pred(ctypes.Structure):
@@ -74,7 +75,8 @@ class vx_query_stats(ctypes.Structure):
                 ("bytes_h2d", ctypes.c_uint64), ("bytes_d2h", ctypes.c_uint64), ("bytes_zero_copy", ctypes.c_uint64),
                 ("bytes_logical", ctypes.c_uint64), ("late_mask", ctypes.c_uint32),
                 ("overflow_retries", ctypes.c_uint32), ("est_selectivity", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+                ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
+                ("late_chunks", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,6 +128,20 @@ class vx_join_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class vx_serve_opts(ctypes.Structure):
+    _fields_ = [("chunk_rows", ctypes.c_uint64), ("max_active", ctypes.c_uint32), ("n_slots", ctypes.c_uint32)]
+
+
+class vx_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cycles", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64), ("active_peak", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = ctypes.POINTER
 _vp, _u64, _i32, _u32, _dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
 _f32 = ctypes.c_float
@@ -151,6 +167,17 @@ SIGNATURES = {
     "vx_mlp_loss_grad": ([_vp, _vp, _i32, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_mlp_train": ([_vp, _vp, _i32, _vp, _vp, _u64, _u32, _f32, _vp], _i32),
     "vx_join": ([_vp, _i32, _i32, _i32, _P(vx_join_opts), _P(vx_join_result)], _i32),
+    "vx_autotune": ([_vp, _P(vx_plan), _u64, _P(vx_config)], _i32),
+    "vx_regressor_fit": ([_vp, _vp, _vp, _u64, _i32, _f32, _vp], _i32),
+    "vx_regressor_train": ([_vp, _f32, _vp, _P(_u64)], _i32),
+    "vx_chunk_log": ([_vp, _vp, _vp, _u64, _P(_u64)], _i32),
+    "vx_chunk_log_clear": ([_vp], _i32),
+    "vx_serve_start": ([_vp, _P(vx_serve_opts)], _i32),
+    "vx_submit": ([_vp, _P(vx_plan), _P(_u64)], _i32),
+    "vx_poll": ([_vp, _u64, _P(vx_result), _P(_i32)], _i32),
+    "vx_wait": ([_vp, _u64, _P(vx_result), _u32], _i32),
+    "vx_serve_stats_get": ([_vp, _P(vx_serve_stats)], _i32),
+    "vx_serve_stop": ([_vp], _i32),
     "vx_filter_device_static": ([_vp, _i32, _P(vx_pred), _i32, _u64, _u64, _vp, _u64, _P(_u64), _vp], _i32),
 }
 
@@ -277,6 +304,90 @@ def vx_groupby(ctx, keys, agg_op, agg_a, agg_b, preds, cap: int = 1 << 16):
 
 def vx_drop_resident(ctx):
     _check(load().vx_drop_resident(ctx))
+
+
+def vx_regressor_fit(ctx, X, y, lam=0.0):
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    w = np.zeros(X.shape[1], np.float32)
+    _check(load().vx_regressor_fit(ctx, X.ctypes.data, y.ctypes.data, X.shape[0], X.shape[1], lam, w.ctypes.data))
+    return w
+
+
+def vx_regressor_train(ctx, lam=1e-6):
+    w = np.zeros(4, np.float32)
+    n = ctypes.c_uint64()
+    _check(load().vx_regressor_train(ctx, lam, w.ctypes.data, ctypes.byref(n)))
+    return w, n.value
+
+
+def vx_chunk_log(ctx):
+    n = ctypes.c_uint64()
+    _check(load().vx_chunk_log(ctx, None, None, 0, ctypes.byref(n)))
+    X = np.zeros((n.value, 4), np.float32)
+    y = np.zeros(n.value, np.float32)
+    _check(load().vx_chunk_log(ctx, X.ctypes.data, y.ctypes.data, n.value, ctypes.byref(n)))
+    return X, y
+
+
+def vx_chunk_log_clear(ctx):
+    _check(load().vx_chunk_log_clear(ctx))
+
+
+def vx_serve_start(ctx, chunk_rows=0, max_active=0, n_slots=0):
+    o = vx_serve_opts(chunk_rows, max_active, n_slots)
+    _check(load().vx_serve_start(ctx, ctypes.byref(o)))
+
+
+def vx_submit(ctx, plan: vx_plan) -> int:
+    t = ctypes.c_uint64()
+    _check(load().vx_submit(ctx, ctypes.byref(plan), ctypes.byref(t)))
+    return t.value
+
+
+def _result_arrays(cap):
+    gid = np.zeros(cap, np.uint64)
+    s = np.zeros(cap, np.int64)
+    c = np.zeros(cap, np.uint64)
+    return gid, s, c, vx_result(cap, gid.ctypes.data, s.ctypes.data, c.ctypes.data, 0, vx_query_stats())
+
+
+def vx_poll(ctx, ticket: int, cap: int = 1 << 13):
+    """Returns None while running, else (status, gid, sum, cnt, stats)."""
+    gid, s, c, res = _result_arrays(cap)
+    done = ctypes.c_int32()
+    st = load().vx_poll(ctx, ticket, ctypes.byref(res), ctypes.byref(done))
+    if not done.value:
+        if st != VX_OK:
+            _check(st)
+        return None
+    n = min(res.n_out, cap)
+    return st, gid[:n], s[:n], c[:n], res.stats.as_dict()
+
+
+def vx_wait(ctx, ticket: int, timeout_ms: int = 600_000, cap: int = 1 << 13):
+    gid, s, c, res = _result_arrays(cap)
+    st = load().vx_wait(ctx, ticket, ctypes.byref(res), timeout_ms)
+    if st not in (VX_OK, VX_E_CAPACITY):
+        _check(st)
+    n = min(res.n_out, cap)
+    return st, gid[:n], s[:n], c[:n], res.stats.as_dict()
+
+
+def vx_serve_stats_get(ctx) -> dict:
+    s = vx_serve_stats()
+    _check(load().vx_serve_stats_get(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def vx_serve_stop(ctx):
+    _check(load().vx_serve_stop(ctx))
+
+
+def vx_autotune(ctx, plan: vx_plan, sample_rows: int) -> vx_config:
+    c = vx_config()
+    _check(load().vx_autotune(ctx, ctypes.byref(plan), sample_rows, ctypes.byref(c)))
+    return c
 
 
 def vx_last_stats(ctx) -> dict:

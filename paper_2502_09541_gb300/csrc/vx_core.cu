@@ -188,11 +188,13 @@ VX_API vx_status vx_open_ex(void *dev_arena, uint64_t bytes, void *stream, vx_ct
 VX_API vx_status vx_close(vx_ctx *ctx) {
   if (!ctx) return VX_OK;
   cudaSetDevice(ctx->device);
+  serve_shutdown(ctx);  // the engine thread takes the context lock: stop it first
   {
     std::lock_guard<std::recursive_mutex> g(ctx->mu);
     if (ctx->s_compute) cudaStreamSynchronize(ctx->s_compute);
     if (ctx->s_h2d) cudaStreamSynchronize(ctx->s_h2d);
     if (ctx->s_d2h) cudaStreamSynchronize(ctx->s_d2h);
+    ctx->graphs.clear();
     ctx->resident.clear();
     for (auto &c : ctx->cols)
       if (c.live && c.we_registered) cudaHostUnregister((void *)c.host);
@@ -224,6 +226,10 @@ VX_API vx_status vx_set_config(vx_ctx *ctx, const vx_config *cfg) {
     return VX_E_INVAL;
   }
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  if (memcmp(&ctx->cfg, cfg, sizeof *cfg) != 0) {
+    cudaStreamSynchronize(ctx->s_compute);
+    ctx->graphs.clear();  // captured pipelines follow the old chunking and launch shape
+  }
   ctx->cfg = *cfg;
   return VX_OK;
 }
@@ -282,7 +288,8 @@ VX_API vx_status vx_unregister_host_column(vx_ctx *ctx, int32_t col_id) {
   Column &c = ctx->cols[col_id];
   cudaStreamSynchronize(ctx->s_compute);
   cudaStreamSynchronize(ctx->s_h2d);
-  ctx->resident.clear();  // cached tables may refer to the column
+  ctx->graphs.clear();  // captured pipelines and cached tables may refer to the column
+  ctx->resident.clear();
   if (c.we_registered) cudaHostUnregister((void *)c.host);
   c.live = false;
   return VX_OK;
@@ -293,6 +300,7 @@ VX_API vx_status vx_drop_resident(vx_ctx *ctx) {
   VX_TRY(check_ctx(ctx));
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  ctx->graphs.clear();
   ctx->resident.clear();
   return VX_OK;
 }

@@ -113,6 +113,7 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k) == cudaSuccess) st->ms_kernel += ms;
         cudaGetLastError();
+        k.on_retire(next_retire);
         if (k.has_outputs()) {
           ops.clear();
           VX_TRY(k.outputs(next_retire, base + (next_retire % S) * slot_bytes, ops));
@@ -173,6 +174,47 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
   }
   st->chunks += N;
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_d2h));
+  return VX_OK;
+}
+
+vx_status enqueue_pipeline_for_capture(vx_ctx *ctx, ExKernel &k, char *ring, int S, ExecStats *st) {
+  const uint64_t N = k.size();
+  const uint64_t slot_bytes = (k.slot_bytes() + 255) & ~255ull;
+  EventSet es;
+  es.s.resize(S);
+  for (auto &x : es.s) {
+    VX_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_in, cudaEventDisableTiming));
+    VX_CUDA_TRY(cudaEventCreateWithFlags(&x.ev_k, cudaEventDisableTiming));
+  }
+  cudaEvent_t fork = nullptr, join = nullptr;
+  VX_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  VX_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+  struct Free {
+    cudaEvent_t a, b;
+    ~Free() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } fr{fork, join};
+  VX_CUDA_TRY(cudaEventRecord(fork, ctx->s_compute));
+  VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_h2d, fork, 0));
+  std::vector<CopyOp> ops;
+  for (uint64_t it = 0; it < N; ++it) {
+    SlotState &sl = es.s[it % S];
+    char *slot = ring + (it % S) * slot_bytes;
+    if (it >= (uint64_t)S) VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_h2d, sl.ev_k, 0));
+    ops.clear();
+    k.inputs(it, slot, ops);
+    VX_TRY(issue_copies(ops, cudaMemcpyHostToDevice, ctx->s_h2d, &st->bytes_h2d));
+    VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
+    VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
+    VX_TRY(k.kernel(slot, it, ctx->s_compute));
+    st->kernel_launches += 1;
+    VX_CUDA_TRY(cudaEventRecord(sl.ev_k, ctx->s_compute));
+  }
+  VX_CUDA_TRY(cudaEventRecord(join, ctx->s_h2d));
+  VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, join, 0));
+  st->chunks += N;
   return VX_OK;
 }
 

@@ -111,6 +111,7 @@ inline uint32_t dtype_size(int32_t dt) { return (dt == VX_I64 || dt == VX_U64) ?
 
 // ------------------------------------------------------------------ context
 struct ResidentHT;  // cached dimension hash table (serving)
+struct GraphEntry;  // captured chunk pipeline of one plan (batching)
 
 }  // namespace vx
 
@@ -133,7 +134,20 @@ struct vx_ctx {
   static constexpr int kScalars = 4096;
   // resident dimension hash tables, keyed by a signature string
   std::map<std::string, std::shared_ptr<vx::ResidentHT>> resident;
+  // captured pipelines (use_graphs), keyed by plan signature; released before
+  // the resident tables and the arena
+  std::map<std::string, std::shared_ptr<vx::GraphEntry>> graphs;
+  // per-chunk statistics logged by plans (features, survivor fraction) and the
+  // cardinality regressor fitted on them
+  std::vector<float> chunk_log_x, chunk_log_y;
+  float reg_w[8] = {0};
+  bool reg_trained = false;
+  void *serve = nullptr;  // serving engine (vx_serve_start .. vx_serve_stop)
 };
+
+namespace vx {
+void serve_shutdown(vx_ctx *ctx);  // stops and frees the serving engine, if any
+}
 
 namespace vx {
 
@@ -160,6 +174,8 @@ struct ExKernel {
   virtual void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) = 0;
   virtual vx_status kernel(char *slot, uint64_t it, cudaStream_t s) = 0;
   virtual bool has_outputs() { return false; }
+  // called once the kernel of chunk `it` has completed (immediate schedule)
+  virtual void on_retire(uint64_t it) {}
   // called after kernel(it) has completed on the device
   virtual vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) { return VX_OK; }
 };
@@ -172,5 +188,10 @@ struct ExecStats {
 // Runs all chunks of `k` through a ring of cfg.n_slots staging slots allocated
 // from the arena (Section 5.3 pipelined executor).
 vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st);
+
+// Enqueues every chunk of `k` as a stream/event DAG into a caller-owned ring
+// while the compute stream is being captured: the copy stream is forked from
+// and joined back into the compute stream, nothing is synchronised.
+vx_status enqueue_pipeline_for_capture(vx_ctx *ctx, ExKernel &k, char *ring, int n_slots, ExecStats *st);
 
 }  // namespace vx

@@ -185,10 +185,27 @@ __global__ void __launch_bounds__(256) join_probe_kernel(const uint64_t *__restr
     s += __shfl_down_sync(0xffffffffu, s, off);
     f += __shfl_down_sync(0xffffffffu, f, off);
   }
-  if ((threadIdx.x & 31) == 0 && c) {
-    atomicAdd(&acc->count, c);
-    atomicAdd(&acc->psum, s);
-    atomicAdd(&acc->fp, f);
+  // one set of global atomics per block (wrapping sums are order-free)
+  __shared__ unsigned long long bc[8], bs[8], bf[8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    bc[w] = c;
+    bs[w] = s;
+    bf[w] = f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tc = 0, ts = 0, tf = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      tc += bc[i];
+      ts += bs[i];
+      tf += bf[i];
+    }
+    if (tc) {
+      atomicAdd(&acc->count, tc);
+      atomicAdd(&acc->psum, ts);
+      atomicAdd(&acc->fp, tf);
+    }
   }
 }
 
@@ -396,7 +413,7 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
       ppass.n = np;
       ppass.R = 2 * R;
       ppass.fn = [&](const uint64_t *k, const uint64_t *, uint64_t n, uint64_t row0, cudaStream_t st) -> vx_status {
-        join_probe_kernel<4><<<grid_of(ctx, (n + 3) / 4, 256, 8), 256, 0, st>>>(k, n, row0, lo, hi, last, t, cap,
+        join_probe_kernel<8><<<grid_of(ctx, (n + 7) / 8, 256, 8), 256, 0, st>>>(k, n, row0, lo, hi, last, t, cap,
                                                                                acc);
         VX_CUDA_TRY(cudaGetLastError());
         return VX_OK;

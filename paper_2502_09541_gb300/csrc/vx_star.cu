@@ -108,16 +108,20 @@ __device__ __forceinline__ int32_t load_role(const ChunkParams &p, int r, uint64
 // coalescing) — fact predicates, chained probes into the dimension tables,
 // mixed-radix group id, aggregate.  Accumulators live in shared memory when
 // the groups fit (kSmem), else in global memory.
-template <bool kSmem, int kRows>
-__global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
-  extern __shared__ unsigned long long sacc[];  // [2 * n_groups]
-  unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
-  if (kSmem) {
-    for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
-    __syncthreads();
-  }
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kRows;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x * kRows + threadIdx.x; base < p.n; base += stride) {
+// survivors of one block tile, collected in shared memory (split mode)
+struct SurvTile {
+  unsigned int n, base;
+  uint2 e[kStarTileRows];  // (chunk row, group id)
+};
+
+// rows base + j * blockDim.x (j < kRows) of one chunk.  kSplit: surviving
+// rows are appended to the block's survivor list instead of being aggregated
+// (their late payload columns are read by star_gather_kernel).
+template <bool kSmem, int kRows, bool kSplit = false>
+__device__ __forceinline__ void star_rows(const ChunkParams &p, uint64_t base, unsigned long long *ssum,
+                                          unsigned long long *scnt, unsigned long long &surv,
+                                          SurvTile *st = nullptr) {
+  {
     uint64_t row[kRows];
     bool alive[kRows];
     uint32_t g[kRows];
@@ -183,6 +187,19 @@ __global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
         g[j] += (uint32_t)code * p.fgk_stride[k];
       }
     }
+    if (p.chunk_surv) {
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) surv += alive[j];
+    }
+    if (kSplit) {
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        if (!alive[j]) continue;
+        const unsigned int k = atomicAdd(&st->n, 1u);
+        st->e[k] = make_uint2((uint32_t)row[j], g[j]);
+      }
+      return;
+    }
     int32_t av[kRows], bv[kRows];
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {  // aggregate inputs of all rows in flight together
@@ -203,6 +220,61 @@ __global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
       }
     }
   }
+}
+
+// Split mode, pass 1: filter, probe and group id per row; survivors of each
+// block tile go to the chunk's survivor list (one global atomic per tile).
+// The loop runs over whole block tiles so that every thread reaches the
+// barriers.
+__global__ void __launch_bounds__(256) star_split_kernel(const ChunkParams p) {
+  __shared__ SurvTile st;
+  if (threadIdx.x == 0) st.n = 0;
+  __syncthreads();
+  unsigned long long surv = 0;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * kStarTileRows; t0 < p.n; t0 += (uint64_t)gridDim.x * kStarTileRows) {
+    star_rows<false, kStarTileRows / 256, true>(p, t0 + threadIdx.x, nullptr, nullptr, surv, &st);
+    __syncthreads();
+    const unsigned int n = st.n;
+    if (n) {
+      if (threadIdx.x == 0) st.base = atomicAdd(p.surv_cnt, n);
+      __syncthreads();
+      for (unsigned int k = threadIdx.x; k < n; k += blockDim.x) p.surv_list[st.base + k] = st.e[k];
+      __syncthreads();
+      if (threadIdx.x == 0) st.n = 0;
+      __syncthreads();
+    }
+  }
+  if (p.chunk_surv) {
+    for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+    if ((threadIdx.x & 31) == 0 && surv) atomicAdd(&p.chunk_surv[p.chunk_idx], surv);
+  }
+}
+
+// Split mode, pass 2: late payload columns of every survivor, read through
+// mapped host memory with one independent load per survivor in flight, and
+// aggregated into the group accumulators.
+template <bool kSmem>
+__global__ void __launch_bounds__(256) star_gather_kernel(const ChunkParams p) {
+  extern __shared__ unsigned long long sacc[];
+  unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
+  if (kSmem) {
+    for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
+    __syncthreads();
+  }
+  const unsigned int n = *p.surv_cnt;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint2 e = p.surv_list[i];
+    const int64_t a = p.agg_a_role >= 0 ? load_role(p, p.agg_a_role, e.x) : 0;
+    const int64_t b = p.agg_b_role >= 0 ? load_role(p, p.agg_b_role, e.x) : 0;
+    const int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
+    if (kSmem) {
+      atomicAdd(&ssum[e.y], (unsigned long long)v);
+      atomicAdd(&scnt[e.y], 1ull);
+    } else {
+      atomicAdd(&p.g_sum[e.y], (unsigned long long)v);
+      atomicAdd(&p.g_cnt[e.y], 1ull);
+    }
+  }
   if (kSmem) {
     __syncthreads();
     for (uint32_t q = threadIdx.x; q < p.n_groups; q += blockDim.x) {
@@ -212,6 +284,171 @@ __global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
       }
     }
   }
+}
+
+template <bool kSmem, int kRows>
+__global__ void __launch_bounds__(256) star_chunk_kernel(const ChunkParams p) {
+  extern __shared__ unsigned long long sacc[];  // [2 * n_groups]
+  unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
+  if (kSmem) {
+    for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
+    __syncthreads();
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kRows;
+  unsigned long long surv = 0;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x * kRows + threadIdx.x; base < p.n; base += stride)
+    star_rows<kSmem, kRows>(p, base, ssum, scnt, surv);
+  if (kSmem) {
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < p.n_groups; q += blockDim.x) {
+      if (scnt[q]) {
+        atomicAdd(&p.g_sum[q], ssum[q]);
+        atomicAdd(&p.g_cnt[q], scnt[q]);
+      }
+    }
+  }
+  if (p.chunk_surv) {
+    for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+    if ((threadIdx.x & 31) == 0 && surv) atomicAdd(&p.chunk_surv[p.chunk_idx], surv);
+  }
+}
+
+// Persistent multi-query kernel of the serving engine: one launch per staged
+// chunk; resident blocks pull (query, tile) work items from a device counter,
+// so queries covering uneven parts of the chunk share the launch.  A tile is
+// kMultiTile rows of one query; accumulation goes straight to that query's
+// global accumulators.
+__global__ void __launch_bounds__(256) star_multi_kernel(const ChunkParams *__restrict__ ps,
+                                                          const MultiItem *__restrict__ items, uint32_t n_items,
+                                                          unsigned int *next) {
+  __shared__ unsigned int s_item;
+  __shared__ ChunkParams sp;
+  unsigned long long surv = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1u);
+    __syncthreads();
+    const unsigned int it = s_item;
+    if (it >= n_items) break;
+    const MultiItem m = items[it];
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&ps[m.q]);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+    for (uint32_t k = threadIdx.x; k < sizeof(ChunkParams) / 4; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    star_rows<false, 8>(sp, (uint64_t)m.tile * kMultiTile + threadIdx.x, nullptr, nullptr, surv);
+    __syncthreads();  // sp and s_item are rewritten by the next item
+  }
+}
+
+vx_status launch_star_multi(vx_ctx *ctx, const ChunkParams *d_params, const MultiItem *d_items, uint32_t n_items,
+                            unsigned int *d_next, cudaStream_t s) {
+  if (!n_items) return VX_OK;
+  VX_CUDA_TRY(cudaMemsetAsync(d_next, 0, 4, s));
+  const uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)ctx->num_sms * 4);
+  star_multi_kernel<<<grid, 256, 0, s>>>(d_params, d_items, n_items, d_next);
+  VX_CUDA_TRY(cudaGetLastError());
+  return VX_OK;
+}
+
+// Per-chunk features of the cardinality regressor (one block per chunk): 256
+// sampled rows (4 runs of 64 consecutive rows) read through mapped host
+// memory; f_fact = fraction passing the fact predicates, f_all = fraction
+// passing everything (predicates, every probe, group-key ranges).  All roles
+// of p are zero-copy; p.row0 is the plan's first row.
+__global__ void __launch_bounds__(kChunkSampleRows) chunk_features_kernel(const ChunkParams p, uint64_t n_rows,
+                                                                          uint64_t chunk_rows, float dim_sel,
+                                                                          float *feats) {
+  __shared__ unsigned int cf, ca, cs, cd[VX_MAX_DIMS];
+  if (threadIdx.x == 0) cf = ca = cs = 0;
+  if (threadIdx.x < VX_MAX_DIMS) cd[threadIdx.x] = 0;
+  __syncthreads();
+  (void)dim_sel;
+  const uint64_t c0 = (uint64_t)blockIdx.x * chunk_rows;
+  const uint64_t cn = c0 + chunk_rows <= n_rows ? chunk_rows : n_rows - c0;
+  const uint32_t run = threadIdx.x / 64, k = threadIdx.x % 64;
+  const uint64_t off = (uint64_t)run * cn / 4 + k;
+  if (off < cn) {
+    const uint64_t i = c0 + off;
+    bool ok = true;
+    for (int q = 0; q < p.n_fact_preds && ok; ++q)
+      ok = pred_ok(p.zc[p.fp_role[q]][p.row0 + i], p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+    bool all = ok;
+    for (int d = 0; d < p.n_dims; ++d) {  // every probe, for the per-dimension marginals
+      uint32_t v = 0;
+      const bool hit = ht_lookup(p.ht[d], p.ht_log2[d], p.zc[p.dim_role[d]][p.row0 + i], v);
+      if (hit) atomicAdd(&cd[d], 1u);
+      all = all && hit;
+    }
+    for (int q = 0; q < p.n_fgk && all; ++q) {
+      const int32_t code = p.zc[p.fgk_role[q]][p.row0 + i];
+      all = code >= 0 && code < p.fgk_card[q];
+    }
+    atomicAdd(&cs, 1u);
+    if (ok) atomicAdd(&cf, 1u);
+    if (all) atomicAdd(&ca, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float n = cs ? (float)cs : 1.f;
+    float *f = feats + (uint64_t)blockIdx.x * kChunkFeatures;
+    float indep = cf / n;  // per-chunk independence estimate: fact fraction x dimension marginals
+    for (int d = 0; d < p.n_dims; ++d) indep *= cd[d] / n;
+    f[0] = 1.f;
+    f[1] = cf / n;
+    f[2] = ca / n;
+    f[3] = indep;
+  }
+}
+
+// Normal equations of ridge regression: acc[0 .. d*d) += X^T X, acc[d*d ..
+// d*d+d) += X^T y, in fp64 (shared-memory partial sums, one global add per
+// block and entry)
+__global__ void ridge_accumulate_kernel(const float *X, const float *y, uint64_t n, int d, double *acc) {
+  __shared__ double s[8 * 8 + 8];
+  for (int k = threadIdx.x; k < d * d + d; k += blockDim.x) s[k] = 0.0;
+  __syncthreads();
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+    const float *x = X + r * d;
+    for (int a = 0; a < d; ++a) {
+      for (int b = 0; b < d; ++b) atomicAdd(&s[a * d + b], (double)x[a] * (double)x[b]);
+      atomicAdd(&s[d * d + a], (double)x[a] * (double)y[r]);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < d * d + d; k += blockDim.x) atomicAdd(&acc[k], s[k]);
+}
+
+// (X^T X + lambda I) w = X^T y by Cholesky factorisation, one thread (d <= 8)
+__global__ void ridge_solve_kernel(const double *acc, int d, double lambda, float *w, uint32_t *err) {
+  if (threadIdx.x || blockIdx.x) return;
+  double A[8][8], L[8][8], z[8], x[8];
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) A[a][b] = acc[a * d + b] + (a == b ? lambda : 0.0);
+  for (int j = 0; j < d; ++j) {
+    double sum = A[j][j];
+    for (int k = 0; k < j; ++k) sum -= L[j][k] * L[j][k];
+    if (!(sum > 1e-10 * A[j][j])) {  // pivot lost to cancellation: (numerically) singular
+      *err = 1;
+      return;
+    }
+    L[j][j] = sqrt(sum);
+    for (int i = j + 1; i < d; ++i) {
+      double t = A[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / L[j][j];
+    }
+  }
+  for (int i = 0; i < d; ++i) {  // L z = X^T y
+    double t = acc[d * d + i];
+    for (int k = 0; k < i; ++k) t -= L[i][k] * z[k];
+    z[i] = t / L[i][i];
+  }
+  for (int i = d - 1; i >= 0; --i) {  // L^T x = z
+    double t = z[i];
+    for (int k = i + 1; k < d; ++k) t -= L[k][i] * x[k];
+    x[i] = t / L[i][i];
+  }
+  for (int i = 0; i < d; ++i) w[i] = (float)x[i];
+  *err = 0;
 }
 
 // Fraction of sampled rows passing the fact predicates (planner estimate);
@@ -408,24 +645,89 @@ struct StarExKernel : ExKernel {
   bool smem = true;
   size_t smem_bytes = 0;
   int grid = 1;
+  // per-chunk late materialization: staged columns k with switchable[k] are
+  // read through mapped host memory in chunks with chunk_late[it] set
+  std::vector<uint8_t> switchable, chunk_late;
+
+  // split mode (late roles): survivor list region after the staged columns
+  bool any_late = false;
+  // per-slot events around the fused kernel (its own duration, immediate schedule)
+  std::vector<cudaEvent_t> ev_a, ev_b;
+  std::vector<uint8_t> ev_used;
+  double ms_main = 0;
+  uint64_t main_launches = 0, launches = 0;
+  ~StarExKernel() override {
+    for (auto e : ev_a) cudaEventDestroy(e);
+    for (auto e : ev_b) cudaEventDestroy(e);
+  }
 
   uint64_t size() override { return (n_rows + chunk_rows - 1) / chunk_rows; }
-  uint64_t slot_bytes() override { return (uint64_t)staged_cols.size() * chunk_rows * 4 + 256 * staged_cols.size(); }
+  uint64_t cols_bytes() const { return (uint64_t)staged_cols.size() * ((chunk_rows * 4 + 255) & ~255ull); }
+  uint64_t slot_bytes() override { return cols_bytes() + (any_late ? chunk_rows * 8 + 256 : 0); }
   uint64_t col_off(size_t k) const { return k * ((chunk_rows * 4 + 255) & ~255ull); }
+  bool chunk_has_late(uint64_t it) const {
+    if (!any_late) return false;
+    if (chunk_late.empty()) return true;  // one decision for the whole plan
+    return chunk_late[it] != 0;
+  }
+  void on_retire(uint64_t it) override {
+    const size_t k = it % ev_a.size();
+    if (ev_a.empty() || !ev_used[k]) return;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, ev_a[k], ev_b[k]) == cudaSuccess) {
+      ms_main += ms;
+      main_launches += 1;
+    }
+    cudaGetLastError();
+    ev_used[k] = 0;
+  }
   uint64_t rows_of(uint64_t it) const { return std::min(chunk_rows, n_rows - it * chunk_rows); }
+  bool late_in(size_t k, uint64_t it) const {
+    return k < switchable.size() && switchable[k] && it < chunk_late.size() && chunk_late[it];
+  }
 
   void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) override {
     const uint64_t r0 = row_begin + it * chunk_rows, n = rows_of(it);
     for (size_t k = 0; k < staged_cols.size(); ++k)
-      h2d.push_back({(const char *)staged_cols[k]->host + r0 * 4, slot + col_off(k), n * 4});
+      if (!late_in(k, it)) h2d.push_back({(const char *)staged_cols[k]->host + r0 * 4, slot + col_off(k), n * 4});
   }
   vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
     ChunkParams p = proto;
     p.row0 = row_begin + it * chunk_rows;
     p.n = rows_of(it);
-    for (size_t k = 0; k < staged_cols.size(); ++k) p.staged[staged_role[k]] = (const int32_t *)(slot + col_off(k));
+    p.chunk_idx = it;
+    for (size_t k = 0; k < staged_cols.size(); ++k)
+      p.staged[staged_role[k]] = late_in(k, it) ? nullptr : (const int32_t *)(slot + col_off(k));
     int threads = ctx->cfg.block_threads > 256 ? 256 : ctx->cfg.block_threads;
     int g = grid_for(ctx, (p.n + 7) / 8, threads);
+    const size_t ek = ev_a.empty() ? 0 : it % ev_a.size();
+    const bool timed = !ev_a.empty() && ctx->cfg.sched == VX_SCHED_IMMEDIATE;
+    if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
+    if (chunk_has_late(it)) {  // filter/probe pass, then the late-column gather
+      p.surv_list = (uint2 *)(slot + cols_bytes());
+      p.surv_cnt = (unsigned int *)(slot + cols_bytes() + chunk_rows * 8);
+      VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
+      const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
+      star_split_kernel<<<gs, 256, 0, s>>>(p);
+      if (timed) VX_CUDA_TRY(cudaEventRecord(ev_b[ek], s));
+      const int gg = ctx->num_sms * 4;
+      if (smem) {
+        static bool attr_g = false;
+        if (!attr_g) {
+          VX_CUDA_TRY(cudaFuncSetAttribute(star_gather_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(16 * kSmemGroups)));
+          attr_g = true;
+        }
+        star_gather_kernel<true><<<gg, 256, smem_bytes, s>>>(p);
+      } else {
+        star_gather_kernel<false><<<gg, 256, 0, s>>>(p);
+      }
+      VX_CUDA_TRY(cudaGetLastError());
+      launches += 2;
+      if (timed) ev_used[ek] = 1;
+      return VX_OK;
+    }
+    launches += 1;
     if (smem) {
       static bool attr_set = false;
       if (!attr_set) {
@@ -438,15 +740,96 @@ struct StarExKernel : ExKernel {
     else
       star_chunk_kernel<false, 8><<<g, threads, 0, s>>>(p);
     VX_CUDA_TRY(cudaGetLastError());
+    if (timed) {
+      VX_CUDA_TRY(cudaEventRecord(ev_b[ek], s));
+      ev_used[ek] = 1;
+    }
     return VX_OK;
   }
 };
 
+// Finds or captures the CUDA graph of a star pipeline (batching).  The key is
+// everything the captured work depends on: the kernel parameters (tables,
+// predicates, roles), the staged host columns, the chunking and the launch
+// shape.  On a full arena the other cached graphs are released and the
+// capture retried once; if it still does not fit, *out stays null and the
+// caller runs the executor instead.
+vx_status star_graph(vx_ctx *ctx, StarExKernel &ek, const std::vector<std::shared_ptr<ResidentHT>> &tables,
+                     uint64_t G, std::shared_ptr<GraphEntry> *out) {
+  ChunkParams kp = ek.proto;
+  kp.g_sum = kp.g_cnt = nullptr;
+  kp.err = nullptr;
+  kp.row0 = kp.n = 0;
+  std::string key((const char *)&kp, sizeof kp);
+  for (const Column *c : ek.staged_cols) key.append((const char *)&c->host, sizeof(void *));
+  const uint64_t dims[6] = {ek.row_begin, ek.n_rows, ek.chunk_rows, (uint64_t)ctx->cfg.n_slots,
+                            (uint64_t)ctx->cfg.block_threads, (uint64_t)ctx->cfg.blocks_per_sm};
+  key.append((const char *)dims, sizeof dims);
+  key.append(ek.switchable.begin(), ek.switchable.end());
+  key.append(ek.chunk_late.begin(), ek.chunk_late.end());
+  auto it = ctx->graphs.find(key);
+  if (it != ctx->graphs.end()) {
+    *out = it->second;
+    return VX_OK;
+  }
+  const int S = std::max(2, ctx->cfg.n_slots);
+  const uint64_t slot = (ek.slot_bytes() + 255) & ~255ull;
+  auto e = std::make_shared<GraphEntry>();
+  e->tables = tables;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    e->ring.arena = e->acc.arena = e->err.arena = &ctx->arena;
+    e->ring.p = ctx->arena.alloc(slot * S);
+    e->acc.p = ctx->arena.alloc(16 * G);
+    e->err.p = ctx->arena.alloc(256);
+    if (e->ring.p && e->acc.p && e->err.p) break;
+    e->ring.release();
+    e->acc.release();
+    e->err.release();
+    ctx->graphs.clear();
+  }
+  if (!e->ring.p) return VX_OK;  // no room: run without a graph
+  ChunkParams gp = ek.proto;
+  gp.g_sum = e->acc.as<unsigned long long>();
+  gp.g_cnt = gp.g_sum + G;
+  gp.err = e->err.as<uint32_t>();
+  StarExKernel gk = ek;
+  gk.proto = gp;
+  gk.ev_a.clear();  // the events belong to ek
+  gk.ev_b.clear();
+  gk.ev_used.clear();
+  cudaStream_t s = ctx->s_compute;
+  VX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  ExecStats est;
+  vx_status st = VX_OK;
+  if (cudaMemsetAsync(e->acc.p, 0, 16 * G, s) != cudaSuccess || cudaMemsetAsync(e->err.p, 0, 4, s) != cudaSuccess) {
+    set_error("graph capture: memset failed");
+    st = VX_E_CUDA;
+  }
+  if (st == VX_OK) st = enqueue_pipeline_for_capture(ctx, gk, e->ring.as<char>(), S, &est);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (st != VX_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  VX_CUDA_TRY(ce);
+  ce = cudaGraphInstantiate(&e->exec, g, 0);
+  cudaGraphDestroy(g);
+  VX_CUDA_TRY(ce);
+  e->chunks = est.chunks;
+  e->bytes_h2d = est.bytes_h2d;
+  e->launches = est.kernel_launches;
+  ctx->graphs[key] = e;
+  *out = e;
+  return VX_OK;
+}
+
 // planner: resolves a plan into dimension specs and chunk-kernel parameters
-vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_resident) {
+vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_resident, PreparedStar *prep) {
   const double t_start = now_ms();
   vx_query_stats qs{};
-  if (!plan || !out) {
+  if (!plan || (!out && !prep)) {
     set_error("vx_run_plan: null argument");
     return VX_E_INVAL;
   }
@@ -656,9 +1039,10 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   }
   qs.est_selectivity = est;
   const double TH = ctx->cfg.zc_threshold > 0 ? ctx->cfg.zc_threshold : kDefaultZeroCopyTH;
+  const bool per_chunk = plan->late_mat == VX_LATE_PER_CHUNK;
   bool late = plan->late_mat == VX_LATE_FORCE_LATE || (plan->late_mat == VX_LATE_AUTO && est < TH);
   // aggregate roles: a column already staged for the row logic stays staged
-  uint32_t late_mask = 0;
+  uint32_t late_mask = 0, switch_mask = 0;
   for (int j = 0; j < 2; ++j) {
     if (agg_cols[j] < 0) continue;
     size_t before = role_col.size();
@@ -666,6 +1050,7 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
     bool is_new = role_col.size() > before;
     if (j == 0) P.agg_a_role = r; else P.agg_b_role = r;
     if (is_new && late) late_mask |= 1u << j;
+    if (is_new && per_chunk) switch_mask |= 1u << j;
   }
   if (role_col.size() > (size_t)kMaxRoles) {
     set_error("plan references %zu fact columns; at most %d", role_col.size(), kMaxRoles);
@@ -690,14 +1075,18 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   ek.n_rows = n_rows;
   for (size_t r = 0; r < role_col.size(); ++r) {
     const Column *c = &ctx->cols[role_col[r]];
-    bool is_late = false;
+    bool is_late = false, is_switch = false;
     if ((int)r == P.agg_a_role && (late_mask & 1u)) is_late = true;
     if ((int)r == P.agg_b_role && (late_mask & 2u)) is_late = true;
+    if ((int)r == P.agg_a_role && (switch_mask & 1u)) is_switch = true;
+    if ((int)r == P.agg_b_role && (switch_mask & 2u)) is_switch = true;
     if (is_late) {
       P.zc[r] = (const int32_t *)c->dev;
     } else {
+      if (is_switch) P.zc[r] = (const int32_t *)c->dev;
       ek.staged_cols.push_back(c);
       ek.staged_role.push_back((int)r);
+      ek.switchable.push_back(is_switch ? 1 : 0);
     }
   }
   (void)n_row_roles;
@@ -711,16 +1100,117 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   ek.chunk_rows = cr;
   ek.smem = G <= kSmemGroups;
   ek.smem_bytes = ek.smem ? 16 * G : 0;
+  ek.any_late = late_mask != 0 || switch_mask != 0;
+  if (!ctx->cfg.use_graphs && ctx->cfg.sched == VX_SCHED_IMMEDIATE && !prep) {
+    const int S = std::max(2, ctx->cfg.n_slots);
+    ek.ev_a.resize(S);
+    ek.ev_b.resize(S);
+    ek.ev_used.assign(S, 0);
+    for (int i = 0; i < S; ++i) {
+      VX_CUDA_TRY(cudaEventCreate(&ek.ev_a[i]));
+      VX_CUDA_TRY(cudaEventCreate(&ek.ev_b[i]));
+    }
+  }
+  const uint64_t n_chunks = n_rows ? (n_rows + cr - 1) / cr : 0;
+
+  if (prep) {  // planning only: hand the query to another driver
+    prep->P = P;
+    prep->acc = std::move(acc);
+    prep->scratch = std::move(scratch);
+    prep->tables = tables;
+    prep->role_col = role_col;
+    prep->staged_cols = ek.staged_cols;
+    prep->staged_role = ek.staged_role;
+    prep->G = G;
+    prep->row_begin = row_begin;
+    prep->n_rows = n_rows;
+    prep->late_mask = late_mask;
+    prep->est = est;
+    return VX_OK;
+  }
+  // ---- per-chunk statistics (logged for the regressor) and per-chunk
+  // late/early decisions from the regressor's predicted selectivity
+  const bool want_log = ctx->cfg.log_chunk_stats && !ctx->cfg.use_graphs;
+  std::vector<float> feats;
+  DevBuf fbuf;
+  uint32_t late_chunks = 0;
+  if ((per_chunk || want_log) && n_chunks) {
+    fbuf.arena = &ctx->arena;
+    fbuf.p = ctx->arena.alloc(n_chunks * (4 * kChunkFeatures + 8) + 512);
+    if (!fbuf.p) {
+      set_error("per-chunk statistics do not fit the arena");
+      return VX_E_NOMEM;
+    }
+    float *d_feats = fbuf.as<float>();
+    unsigned long long *d_surv =
+        (unsigned long long *)(fbuf.as<char>() + ((n_chunks * 4 * kChunkFeatures + 255) & ~255ull));
+    ChunkParams pz = P;
+    for (size_t r = 0; r < role_col.size(); ++r) {
+      pz.staged[r] = nullptr;
+      pz.zc[r] = (const int32_t *)ctx->cols[role_col[r]].dev;
+    }
+    pz.row0 = row_begin;
+    double dsel = 1.0;
+    for (int d = 0; d < plan->n_dims; ++d)
+      dsel *= tables[d]->dim.rows ? (double)tables[d]->dim.passed / (double)tables[d]->dim.rows : 0.0;
+    chunk_features_kernel<<<(unsigned)n_chunks, kChunkSampleRows, 0, ctx->s_compute>>>(pz, n_rows, cr, (float)dsel,
+                                                                                       d_feats);
+    VX_CUDA_TRY(cudaGetLastError());
+    feats.resize(n_chunks * kChunkFeatures);
+    VX_CUDA_TRY(cudaMemcpyAsync(feats.data(), d_feats, 4 * feats.size(), cudaMemcpyDeviceToHost, ctx->s_compute));
+    if (want_log) {
+      VX_CUDA_TRY(cudaMemsetAsync(d_surv, 0, 8 * n_chunks, ctx->s_compute));
+      P.chunk_surv = d_surv;
+    }
+    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+    if (per_chunk) {
+      ek.chunk_late.resize(n_chunks);
+      for (uint64_t c = 0; c < n_chunks; ++c) {
+        const float *f = &feats[c * kChunkFeatures];
+        double yhat = f[2];  // sampled selectivity when no regressor is trained
+        if (ctx->reg_trained) {
+          yhat = 0;
+          for (int k = 0; k < kChunkFeatures; ++k) yhat += (double)ctx->reg_w[k] * f[k];
+        }
+        ek.chunk_late[c] = yhat < TH ? 1 : 0;
+        late_chunks += ek.chunk_late[c];
+      }
+    }
+  }
   ek.proto = P;
 
   ExecStats es;
-  if (n_rows) VX_TRY(run_pipeline(ctx, ek, &es));
+  void *res_acc = acc.p;
+  uint32_t *res_err = d_err;
+  std::shared_ptr<GraphEntry> ge;
+  if (n_rows && ctx->cfg.use_graphs) {
+    VX_TRY(star_graph(ctx, ek, tables, G, &ge));
+    if (ge) {
+      VX_CUDA_TRY(cudaGraphLaunch(ge->exec, ctx->s_compute));
+      es.chunks = ge->chunks;
+      es.bytes_h2d = ge->bytes_h2d;
+      es.kernel_launches = ge->launches;
+      res_acc = ge->acc.p;
+      res_err = ge->err.as<uint32_t>();
+    }
+  }
+  if (!ge && n_rows) VX_TRY(run_pipeline(ctx, ek, &es));
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
-  VX_TRY(check_err_word(ctx, d_err));
+  VX_TRY(check_err_word(ctx, res_err));
+  if (want_log && n_chunks && !ge) {  // statistics log: features and the exact survivor fraction per chunk
+    std::vector<unsigned long long> sv(n_chunks);
+    VX_CUDA_TRY(cudaMemcpy(sv.data(), P.chunk_surv, 8 * n_chunks, cudaMemcpyDeviceToHost));
+    for (uint64_t c = 0; c < n_chunks; ++c) {
+      const uint64_t rows_c = std::min(cr, n_rows - c * cr);
+      ctx->chunk_log_x.insert(ctx->chunk_log_x.end(), feats.begin() + c * kChunkFeatures,
+                              feats.begin() + (c + 1) * kChunkFeatures);
+      ctx->chunk_log_y.push_back((float)((double)sv[c] / (double)rows_c));
+    }
+  }
 
   // ---- results: non-empty groups in ascending id
   std::vector<uint64_t> h(2 * G);
-  VX_CUDA_TRY(cudaMemcpy(h.data(), acc.p, 16 * G, cudaMemcpyDeviceToHost));
+  VX_CUDA_TRY(cudaMemcpy(h.data(), res_acc, 16 * G, cudaMemcpyDeviceToHost));
   uint64_t n_out = 0, surv = 0;
   vx_status st = VX_OK;
   for (uint64_t g = 0; g < G; ++g) {
@@ -744,11 +1234,18 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   qs.chunks = es.chunks;
   qs.bytes_h2d = es.bytes_h2d;
   qs.bytes_d2h = es.bytes_d2h + 16 * G;
-  qs.late_mask = late_mask;
+  qs.late_mask = late_mask | (late_chunks ? switch_mask : 0);
   qs.bytes_zero_copy = surv * 64ull * (uint64_t)__builtin_popcount(late_mask);
+  if (late_chunks) {  // survivors of late chunks, estimated from the per-chunk sample
+    double zs = 0;
+    for (uint64_t c = 0; c < n_chunks; ++c)
+      if (ek.chunk_late[c]) zs += feats[c * kChunkFeatures + 2] * (double)std::min(cr, n_rows - c * cr);
+    qs.bytes_zero_copy += (uint64_t)(zs * 64.0 * __builtin_popcount(switch_mask));
+  }
+  qs.late_chunks = late_chunks;
   qs.bytes_logical = n_rows * 4ull * role_col.size();
-  qs.ms_kernel = es.ms_kernel;
-  qs.kernel_launches = es.kernel_launches;
+  qs.ms_kernel = ek.main_launches ? ek.ms_main : es.ms_kernel;  // the fused kernel's own time when timed
+  qs.kernel_launches = ge ? es.kernel_launches : ek.launches;
   qs.ms_total = now_ms() - t_start;
   out->stats = qs;
   ctx->last = qs;
@@ -807,11 +1304,172 @@ struct FilterExKernel : ExKernel {
 
 using namespace vx;
 
+namespace vx {
+// Frees captured graphs and the resident dimension tables that nothing else
+// references (the cache holds the only reference); returns whether anything
+// was freed.  Callers retry an allocation that failed.
+bool evict_unused_resident(vx_ctx *ctx) {
+  bool freed = !ctx->graphs.empty();
+  cudaStreamSynchronize(ctx->s_compute);
+  ctx->graphs.clear();
+  for (auto it = ctx->resident.begin(); it != ctx->resident.end();) {
+    if (it->second.use_count() == 1) {
+      it = ctx->resident.erase(it);
+      freed = true;
+    } else {
+      ++it;
+    }
+  }
+  return freed;
+}
+}  // namespace vx
+
 VX_API vx_status vx_run_plan(vx_ctx *ctx, const vx_plan *plan, vx_result *out) {
   clear_error();
   VX_TRY(check_ctx(ctx));
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
-  return run_star(ctx, plan, out, true);
+  vx_status st = run_star(ctx, plan, out, true);
+  if (st == VX_E_NOMEM && evict_unused_resident(ctx)) {  // device budget: make room, once
+    clear_error();
+    st = run_star(ctx, plan, out, true);
+  }
+  return st;
+}
+
+static vx_status regressor_fit(vx_ctx *ctx, const float *X, const float *y, uint64_t n, int32_t d, float lambda,
+                               float *w_out) {
+  if (!X || !y || !w_out || n == 0 || d < 1 || d > 8 || !(lambda >= 0.f)) {
+    set_error("regressor fit: need n > 0 rows, 1 <= d <= 8 features, lambda >= 0");
+    return VX_E_INVAL;
+  }
+  DevBuf b;
+  b.arena = &ctx->arena;
+  const uint64_t xb = (4 * n * d + 255) & ~255ull, yb = (4 * n + 255) & ~255ull;
+  b.p = ctx->arena.alloc(xb + yb + 8 * 80 + 256);
+  if (!b.p) {
+    set_error("regressor fit: %llu rows do not fit the arena", (unsigned long long)n);
+    return VX_E_NOMEM;
+  }
+  float *dX = b.as<float>();
+  float *dy = (float *)(b.as<char>() + xb);
+  double *acc = (double *)(b.as<char>() + xb + yb);
+  float *dw = (float *)(acc + 72);
+  uint32_t *derr = (uint32_t *)(dw + 8);
+  cudaStream_t s = ctx->s_compute;
+  VX_CUDA_TRY(cudaMemcpyAsync(dX, X, 4 * n * d, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(dy, y, 4 * n, cudaMemcpyHostToDevice, s));
+  VX_CUDA_TRY(cudaMemsetAsync(acc, 0, 8 * 72, s));
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 4));
+  ridge_accumulate_kernel<<<grid, 256, 0, s>>>(dX, dy, n, d, acc);
+  ridge_solve_kernel<<<1, 32, 0, s>>>(acc, d, (double)lambda, dw, derr);
+  VX_CUDA_TRY(cudaGetLastError());
+  uint32_t err = 0;
+  VX_CUDA_TRY(cudaMemcpyAsync(w_out, dw, 4 * d, cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaMemcpyAsync(&err, derr, 4, cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) {
+    set_error("regressor fit: normal equations are singular (add lambda > 0)");
+    return VX_E_INVAL;
+  }
+  return VX_OK;
+}
+
+VX_API vx_status vx_regressor_fit(vx_ctx *ctx, const float *X, const float *y, uint64_t n, int32_t d, float lambda,
+                                  float *w_out) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  return regressor_fit(ctx, X, y, n, d, lambda, w_out);
+}
+
+VX_API vx_status vx_regressor_train(vx_ctx *ctx, float lambda, float *w_out, uint64_t *n_used) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const uint64_t n = ctx->chunk_log_y.size();
+  if (n_used) *n_used = n;
+  if (n < (uint64_t)kChunkFeatures) {
+    set_error("vx_regressor_train: %llu logged chunks; at least %d needed", (unsigned long long)n, kChunkFeatures);
+    return VX_E_INVAL;
+  }
+  float w[kChunkFeatures];
+  VX_TRY(regressor_fit(ctx, ctx->chunk_log_x.data(), ctx->chunk_log_y.data(), n, kChunkFeatures, lambda, w));
+  for (int k = 0; k < kChunkFeatures; ++k) ctx->reg_w[k] = w[k];
+  ctx->reg_trained = true;
+  if (w_out) memcpy(w_out, w, sizeof w);
+  return VX_OK;
+}
+
+VX_API vx_status vx_chunk_log(vx_ctx *ctx, float *X, float *y, uint64_t cap, uint64_t *n) {
+  clear_error();
+  if (!ctx || !n) return VX_E_INVAL;
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const uint64_t m = ctx->chunk_log_y.size();
+  *n = m;
+  const uint64_t k = std::min(m, cap);
+  if (X && k) memcpy(X, ctx->chunk_log_x.data(), 4 * k * kChunkFeatures);
+  if (y && k) memcpy(y, ctx->chunk_log_y.data(), 4 * k);
+  return m > cap && (X || y) ? VX_E_CAPACITY : VX_OK;
+}
+
+VX_API vx_status vx_chunk_log_clear(vx_ctx *ctx) {
+  if (!ctx) return VX_E_INVAL;
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  ctx->chunk_log_x.clear();
+  ctx->chunk_log_y.clear();
+  ctx->reg_trained = false;
+  return VX_OK;
+}
+
+VX_API vx_status vx_autotune(vx_ctx *ctx, const vx_plan *plan, uint64_t sample_rows, vx_config *best) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (!plan || !best || sample_rows == 0) {
+    set_error("vx_autotune: need a plan, an output and sample_rows > 0");
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const vx_config base = ctx->cfg;
+  vx_plan p = *plan;
+  p.row_end = p.row_begin + sample_rows;
+  const uint64_t chunks_mb[] = {8, 16, 32, 64, 128, 256};
+  const int slots[] = {2, 3, 4};
+  double best_ms = 1e300;
+  vx_config best_cfg = base;
+  for (uint64_t mb : chunks_mb) {
+    for (int S : slots) {
+      vx_config c = base;
+      c.chunk_bytes = mb << 20;
+      c.n_slots = S;
+      if ((uint64_t)S * c.chunk_bytes * 2 > ctx->arena.capacity()) continue;
+      ctx->cfg = c;
+      ctx->graphs.clear();
+      double ms = 1e300;
+      for (int rep = 0; rep < 3; ++rep) {  // first run warms tables and graphs
+        vx_result r{};
+        r.cap = UINT64_MAX;
+        vx_status st = run_star(ctx, &p, &r, true);
+        if (st != VX_OK) {
+          ms = 1e300;
+          break;
+        }
+        if (rep > 0) ms = std::min(ms, r.stats.ms_total);
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_cfg = c;
+      }
+    }
+  }
+  ctx->graphs.clear();
+  ctx->cfg = best_cfg;
+  *best = best_cfg;
+  if (best_ms >= 1e300) {
+    set_error("vx_autotune: no candidate configuration ran");
+    ctx->cfg = base;
+    return VX_E_NOMEM;
+  }
+  return VX_OK;
 }
 
 VX_API vx_status vx_groupby(vx_ctx *ctx, const vx_plan_gkey *keys, int32_t n_keys, int32_t agg_op, int32_t agg_a,

@@ -94,7 +94,26 @@ struct ChunkParams {
   unsigned long long *g_sum, *g_cnt;
   uint32_t *err;
   uint64_t row0, n;
+  unsigned long long *chunk_surv;  // optional per-chunk survivor counts (statistics log)
+  uint64_t chunk_idx;
+  uint2 *surv_list;                // split mode: (chunk row, group id) of every survivor
+  unsigned int *surv_cnt;
 };
+
+constexpr uint32_t kStarTileRows = 2048;  // rows of one block tile (256 threads x 8 rows)
+
+// work item of the persistent multi-query kernel: rows [tile * kMultiTile,
+// (tile + 1) * kMultiTile) of query q's part of the staged chunk
+struct MultiItem {
+  uint32_t q, tile;
+};
+constexpr uint32_t kMultiTile = 256 * 8;
+vx_status launch_star_multi(vx_ctx *ctx, const ChunkParams *d_params, const MultiItem *d_items, uint32_t n_items,
+                            unsigned int *d_next, cudaStream_t s);
+
+// per-chunk features of the cardinality regressor: [1, f_fact, f_all, f_fact * dim_sel]
+constexpr int kChunkFeatures = 4;
+constexpr int kChunkSampleRows = 256;  // 4 runs of 64 consecutive rows per chunk
 
 struct SampleParams {
   int n_preds;
@@ -113,8 +132,41 @@ struct FilterParams {
   uint64_t row0, n;
 };
 
+// A plan's whole chunk pipeline captured as one CUDA graph: it owns the
+// staging ring and accumulators the graph writes and keeps the dimension
+// tables it reads alive.
+struct GraphEntry {
+  DevBuf ring, acc, err;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<std::shared_ptr<ResidentHT>> tables;
+  uint64_t chunks = 0, bytes_h2d = 0, launches = 0;
+  ~GraphEntry() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 vx_status build_dim_table(vx_ctx *ctx, const DimSpec &d, BuiltDim *out, uint32_t *d_err, uint64_t *d_passed);
 vx_status check_err_word(vx_ctx *ctx, const uint32_t *d_err);
-vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_resident);
+// A planned star query ready to be executed chunk by chunk by another driver
+// (the serving engine): kernel parameters (tables, predicates, roles, late
+// columns as zero-copy pointers), zeroed accumulators and the columns to stage.
+struct PreparedStar {
+  ChunkParams P{};
+  DevBuf acc, scratch;
+  std::vector<std::shared_ptr<ResidentHT>> tables;
+  std::vector<int32_t> role_col;          // role -> column id
+  std::vector<const Column *> staged_cols;
+  std::vector<int> staged_role;
+  uint64_t G = 0, row_begin = 0, n_rows = 0;
+  uint32_t late_mask = 0;
+  double est = 0;
+};
+
+bool evict_unused_resident(vx_ctx *ctx);
+
+// Plans and runs a star query; with prep != nullptr it only plans (tables
+// built, accumulators zeroed) and moves the plan into *prep.
+vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_resident,
+                   PreparedStar *prep = nullptr);
 
 }  // namespace vx

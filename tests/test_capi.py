@@ -36,13 +36,32 @@ def test_library_exports_every_declared_symbol():
     assert set(vx.SIGNATURES) <= declared_functions()
 
 
-def test_struct_layouts_match_header():
+STRUCTS = ["vx_config", "vx_pred", "vx_plan_dim", "vx_plan_gkey", "vx_plan", "vx_query_stats", "vx_result",
+           "vx_sort_opts", "vx_sort_stats", "vx_join_opts", "vx_join_result", "vx_serve_opts", "vx_serve_stats"]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets the C
+    compiler gives the header's structures."""
+    import subprocess
+
     import paper_2502_09541_gb300 as vx
-    # sizes follow the C layout of include/vx.h on LP64 targets
-    assert ctypes.sizeof(vx.vx_pred) == 16
-    assert ctypes.sizeof(vx.vx_plan_gkey) == 16
-    assert ctypes.sizeof(vx.vx_plan_dim) == 4 * (3 + 4 + 1 + 16)
-    assert ctypes.sizeof(vx.vx_config) == 48
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vx.h"', "int main(void) {"]
+    for s in STRUCTS:
+        lines.append(f'  printf("{s} %zu\\n", sizeof({s}));')
+        for f, _ in getattr(vx, s)._fields_:
+            lines.append(f'  printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for s in STRUCTS:
+        cls = getattr(vx, s)
+        assert int(out[s]) == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(out[f"{s}.{f}"]) == getattr(cls, f).offset, (s, f)
 
 
 def test_null_and_bad_arguments_fail_without_a_device():

@@ -1,0 +1,84 @@
+"""Batching: the star pipeline captured as one CUDA graph and replayed, and the
+chunk-size / ring-depth autotuner.  Results must be identical to the oracle
+(and to the executor's) on every replay."""
+import numpy as np
+import pytest
+
+import datagen as G
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+vx = pytest.importorskip("paper_2502_09541_gb300")
+
+
+@pytest.fixture(scope="module")
+def star():
+    n = 4_000_003
+    fact = G.star_fact(n, seed=13)
+    dims = G.star_dims(0)
+    ctx = vx.vx_open(512 << 20)
+    fid = {c: vx.vx_register_host_column(ctx, c, fact[c]) for c in fact}
+    did = {d: {a: vx.vx_register_host_column(ctx, f"{d}.{a}", arr) for a, arr in dims[d].items()} for d in dims}
+    yield ctx, fact, dims, fid, did
+    vx.vx_close(ctx)
+
+
+def _expect(T, fact, dims, rb=0, re=None):
+    es, ec = O.star(T, fact, dims, rb, re, nthreads=8)
+    nz = np.nonzero(ec)[0]
+    return nz.astype(np.uint64), es[nz], ec[nz]
+
+
+@pytest.mark.parametrize("name", ["T1", "T2_1", "T3_10", "T3_0.1"])
+def test_graph_replay_bit_exact(star, name):
+    ctx, fact, dims, fid, did = star
+    cfg = vx.vx_get_config(ctx)
+    cfg.use_graphs = 1
+    cfg.chunk_bytes = 8 << 20
+    vx.vx_set_config(ctx, cfg)
+    T = G.star_templates()[name]
+    if name == "T1":
+        T = dict(T, dims=[{"dim": "date", "fk": "date_fk", "preds": [("year", 1, 1)]}])
+    plan = vx.make_plan(T, fid, did, G.STAR_ATTR_CARD)
+    gid_e, s_e, c_e = _expect(T, fact, dims)
+    first = None
+    for rep in range(3):  # capture, then two replays
+        st, gid, s, c, stats = vx.vx_run_plan(ctx, plan)
+        assert st == vx.VX_OK
+        assert np.array_equal(gid, gid_e) and np.array_equal(s, s_e) and np.array_equal(c, c_e)
+        if first is None:
+            first = stats
+        assert stats["chunks"] == first["chunks"] > 1
+    cfg.use_graphs = 0
+    vx.vx_set_config(ctx, cfg)
+
+
+def test_graph_survives_table_rebuild_and_ranges(star):
+    ctx, fact, dims, fid, did = star
+    cfg = vx.vx_get_config(ctx)
+    cfg.use_graphs = 1
+    vx.vx_set_config(ctx, cfg)
+    T = G.star_templates()["T2_10"]
+    for rb, re in [(0, 0), (12_345, 3_000_001), (0, 0)]:
+        vx.vx_drop_resident(ctx)
+        plan = vx.make_plan(T, fid, did, G.STAR_ATTR_CARD, vx.VX_LATE_AUTO, rb, re)
+        st, gid, s, c, _ = vx.vx_run_plan(ctx, plan)
+        gid_e, s_e, c_e = _expect(T, fact, dims, rb, None if re == 0 else re)
+        assert np.array_equal(gid, gid_e) and np.array_equal(s, s_e) and np.array_equal(c, c_e)
+    cfg.use_graphs = 0
+    vx.vx_set_config(ctx, cfg)
+
+
+def test_autotuner_picks_a_candidate_and_keeps_results(star):
+    ctx, fact, dims, fid, did = star
+    T = G.star_templates()["T3_1"]
+    plan = vx.make_plan(T, fid, did, G.STAR_ATTR_CARD)
+    best = vx.vx_autotune(ctx, plan, 2_000_000)
+    assert best.chunk_bytes in [m << 20 for m in (8, 16, 32, 64, 128, 256)]
+    assert best.n_slots in (2, 3, 4)
+    cur = vx.vx_get_config(ctx)
+    assert cur.chunk_bytes == best.chunk_bytes and cur.n_slots == best.n_slots
+    st, gid, s, c, _ = vx.vx_run_plan(ctx, plan)
+    gid_e, s_e, c_e = _expect(T, fact, dims)
+    assert np.array_equal(gid, gid_e) and np.array_equal(s, s_e) and np.array_equal(c, c_e)
