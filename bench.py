@@ -140,16 +140,16 @@ def traffic_per_row():
     return None
 
 
-def make_data(rows, pinned=False):
-    """Fact columns (optionally in page-locked host memory allocated by
-    PyTorch, the 'pinned host memory' the workload holds its table in) and
-    the four dimensions."""
+def make_data(rows, pinned=False, row0=0):
+    """Fact rows [row0, row0 + rows) (optionally in page-locked host memory
+    allocated by PyTorch, the 'pinned host memory' the workload holds its
+    table in) and the four dimensions."""
     import datagen as G
     out = None
     if pinned:
         import torch
         out = {c: torch.empty(rows, dtype=torch.int32, pin_memory=True).numpy() for c in G.STAR_FACT_COLS}
-    fact = G.star_fact(rows, out=out)
+    fact = G.star_fact(rows, row0=row0, out=out)
     dims = G.star_dims(0)
     return fact, dims
 
@@ -325,8 +325,10 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     vx.load()
+    from paper_2502_09541_gb300.dist import shard_rows
     t_gen = time.perf_counter()
-    fact, dims = make_data(args.rows, pinned=True)
+    row0, _ = shard_rows(rank, world, args.rows)  # weak scaling: a disjoint shard of equal size per rank
+    fact, dims = make_data(args.rows, pinned=True, row0=row0)
     t_gen = time.perf_counter() - t_gen
 
     budget = int(args.budget_gb * (1 << 30))

@@ -81,7 +81,7 @@ __global__ void join_count_kernel(const uint64_t *keys, uint64_t n, const uint64
 
 __global__ void join_build_kernel(const uint64_t *keys, const uint64_t *payload, uint64_t n, uint64_t lo, uint64_t hi,
                                   bool last, JoinSlot *t, uint64_t cap, JoinAcc *acc) {
-  unsigned long long ins = 0;
+  unsigned long long ins = 0, disp = 0;  // per-thread count and longest displacement
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
     if (!in_range(k, lo, hi, last)) continue;
@@ -99,7 +99,7 @@ __global__ void join_build_kernel(const uint64_t *keys, const uint64_t *payload,
       const unsigned long long old = atomicCAS(&t[h].key, kJoinEmpty, k);
       if (old == kJoinEmpty) {
         t[h].payload = pay;
-        atomicMax(&acc->max_disp, (unsigned long long)step);
+        disp = step > disp ? step : disp;
         done = true;
         break;
       }
@@ -112,8 +112,15 @@ __global__ void join_build_kernel(const uint64_t *keys, const uint64_t *payload,
     }
     if (!done) atomicOr(&acc->err, ERR_HT_FULL);
   }
-  for (int off = 16; off > 0; off >>= 1) ins += __shfl_down_sync(0xffffffffu, ins, off);
-  if ((threadIdx.x & 31) == 0 && ins) atomicAdd(&acc->inserted, ins);
+  for (int off = 16; off > 0; off >>= 1) {
+    ins += __shfl_down_sync(0xffffffffu, ins, off);
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, disp, off);
+    disp = o > disp ? o : disp;
+  }
+  if ((threadIdx.x & 31) == 0 && ins) {
+    atomicAdd(&acc->inserted, ins);
+    atomicMax(&acc->max_disp, disp);
+  }
 }
 
 // probes the keys of range p; row0 = global row of keys[0]

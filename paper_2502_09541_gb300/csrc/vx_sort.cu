@@ -648,6 +648,9 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
                                   : (uint32_t)std::min<uint64_t>(kMaxRequestedPartitions,
                                                                  (uint64_t)std::ceil(over * (double)n / cap));
   if (P < 2) P = 2;
+  // enough partitions that the sort pass pipelines (loads of partition p+1
+  // and stores of p-1 overlap the sort of p) when the caller leaves P open
+  if (depth == 0 && o.n_partitions <= 1 && n >= kPipelineRows * 4) P = std::max<uint32_t>(P, 16);
   if (P > kMaxRequestedPartitions) {
     set_error("vx_sort: at most %u partitions per pass", kMaxRequestedPartitions);
     return VX_E_UNSUPPORTED;
@@ -692,7 +695,9 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
 
   // ---- pass 1: partition
   double tp = now_ms();
-  const uint64_t R = std::min<uint64_t>(cap, (uint64_t)UINT32_MAX / 2 / kRxTile * kRxTile);
+  // partition-pass chunks of kPipelineRows pairs: long enough for efficient
+  // copies (192 MB), short enough that the pass pipelines over many chunks
+  const uint64_t R = std::min<uint64_t>(cap, kPipelineRows);
   const uint64_t n_chunks = (n + R - 1) / R;
   std::vector<uint64_t> bnd(n_chunks * (P + 1));
   {

@@ -8,6 +8,7 @@
 // aggregate columns whose estimated selectivity is below TH are not staged;
 // the kernel reads them from mapped host memory for qualifying rows only.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 
@@ -61,6 +62,15 @@ __global__ void ht_build_kernel(const DimBuildParams p) {
       val = (uint32_t)g;
       ++passed;
     }
+    if (p.dmap) {  // dense keys: one value per key
+      const uint32_t idx = (uint32_t)(key - p.kmin);
+      if (idx >= p.span) {
+        atomicOr(p.err, ERR_HT_FULL);
+        continue;
+      }
+      if (atomicCAS(&p.dmap[idx], HT_EMPTY_VAL, val) != HT_EMPTY_VAL) atomicOr(p.err, ERR_DUPKEY);
+      continue;
+    }
     const unsigned long long packed = ((unsigned long long)val << 32) | (uint32_t)key;
     uint32_t h = ht_hash32(key, p.log2cap);
     bool done = false;
@@ -97,6 +107,17 @@ __device__ __forceinline__ bool ht_lookup(const uint64_t *__restrict__ slots, ui
     h = (h + 1u) & mask;
   }
   return false;
+}
+
+// lookup in dimension d of a plan: direct map or hash table
+__device__ __forceinline__ bool dim_lookup(const ChunkParams &p, int d, int32_t key, uint32_t &val) {
+  if (p.dspan[d]) {
+    const uint32_t idx = (uint32_t)(key - p.dmin[d]);
+    if (idx >= p.dspan[d]) return false;
+    val = __ldg(reinterpret_cast<const uint32_t *>(p.ht[d]) + idx);
+    return val < HT_FILTERED;
+  }
+  return ht_lookup(p.ht[d], p.ht_log2[d], key, val);
 }
 
 __device__ __forceinline__ int32_t load_role(const ChunkParams &p, int r, uint64_t i) {
@@ -147,6 +168,24 @@ __device__ __forceinline__ void star_rows(const ChunkParams &p, uint64_t base, u
       uint64_t sl[kRows];
 #pragma unroll
       for (int j = 0; j < kRows; ++j) key[j] = alive[j] ? load_role(p, p.dim_role[d], row[j]) : 0;
+      if (p.dspan[d]) {  // direct map: one load per row, no probing
+        const uint32_t *__restrict__ map = reinterpret_cast<const uint32_t *>(slots);
+        const int32_t kmin = p.dmin[d];
+        const uint32_t span = p.dspan[d];
+        uint32_t v[kRows];
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) {
+          const uint32_t idx = (uint32_t)(key[j] - kmin);
+          v[j] = (alive[j] && idx < span) ? __ldg(&map[idx]) : HT_EMPTY_VAL;
+        }
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) {
+          const bool hit = alive[j] && v[j] < HT_FILTERED;
+          g[j] += hit ? v[j] : 0u;
+          alive[j] = hit;
+        }
+        continue;
+      }
       // first probe of every row issued before any is resolved (memory-level
       // parallelism); linear probing continues only on collisions
 #pragma unroll
@@ -220,6 +259,223 @@ __device__ __forceinline__ void star_rows(const ChunkParams &p, uint64_t base, u
       }
     }
   }
+}
+
+__device__ __forceinline__ int32_t lane4(const int4 &v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+
+// value of row j from the row-logic slot `slot` (compile-time select over the
+// kR loaded vectors, so the values stay in registers)
+template <int kR>
+__device__ __forceinline__ int32_t slot_val(const int4 (&vals)[kR], int slot, int j) {
+  int32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < kR; ++k)
+    if (k == slot) x = lane4(vals[k], j);
+  return x;
+}
+
+// Vector path: 4 consecutive rows r0..r0+3 (r0 a multiple of 4, staged
+// columns 16-byte aligned).  Every row-logic column is loaded with one 16-byte
+// load before any row is evaluated, so the rows' memory latency overlaps;
+// then predicates, probes (direct map or hash, all 4 rows' lookups in flight)
+// and the group id are computed from registers.  Survivors are aggregated
+// (kSplit = false) or appended to the block's survivor list.
+template <bool kSmem, bool kSplit, int kR>
+__device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, unsigned long long *ssum,
+                                           unsigned long long *scnt, unsigned long long &surv, SurvTile *st) {
+  int4 vals[kR];
+  const bool full = r0 + 3 < p.n;
+#pragma unroll
+  for (int k = 0; k < kR; ++k) {
+    const int32_t *col = p.staged[k < p.n_rowroles ? p.rowrole[k] : p.rowrole[0]];
+    if (full) {
+      vals[k] = __ldg(reinterpret_cast<const int4 *>(col + r0));
+    } else {
+      vals[k].x = r0 < p.n ? __ldg(col + r0) : 0;
+      vals[k].y = r0 + 1 < p.n ? __ldg(col + r0 + 1) : 0;
+      vals[k].z = r0 + 2 < p.n ? __ldg(col + r0 + 2) : 0;
+      vals[k].w = 0;
+    }
+  }
+  bool alive[4];
+  uint32_t g[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    alive[j] = r0 + j < p.n;
+    g[j] = 0;
+  }
+  for (int q = 0; q < p.n_fact_preds; ++q) {
+    const int s = p.fp_slot[q];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) alive[j] = alive[j] && pred_ok(slot_val(vals, s, j), p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+  }
+  for (int d = 0; d < p.n_dims; ++d) {
+    const int s = p.dim_slot[d];
+    int32_t key[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) key[j] = slot_val(vals, s, j);
+    if (p.dspan[d]) {
+      const uint32_t *__restrict__ map = reinterpret_cast<const uint32_t *>(p.ht[d]);
+      uint32_t v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t idx = (uint32_t)(key[j] - p.dmin[d]);
+        v[j] = (alive[j] && idx < p.dspan[d]) ? __ldg(&map[idx]) : HT_EMPTY_VAL;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool hit = alive[j] && v[j] < HT_FILTERED;
+        g[j] += hit ? v[j] : 0u;
+        alive[j] = hit;
+      }
+    } else {
+      const uint64_t *__restrict__ slots = p.ht[d];
+      const uint32_t l2c = p.ht_log2[d], mask = (1u << l2c) - 1u;
+      uint32_t h[4];
+      uint64_t sl[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        h[j] = ht_hash32(key[j], l2c);
+        sl[j] = alive[j] ? __ldg(&slots[h[j]]) : HT_EMPTY;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!alive[j]) continue;
+        uint64_t sv = sl[j];
+        uint32_t hh = h[j];
+        bool hit = false;
+        for (uint32_t n = 0; n <= mask; ++n) {
+          const uint32_t v = (uint32_t)(sv >> 32);
+          if (v == HT_EMPTY_VAL) break;
+          if ((int32_t)(uint32_t)sv == key[j]) {
+            hit = v != HT_FILTERED;
+            g[j] += v;
+            break;
+          }
+          hh = (hh + 1u) & mask;
+          sv = __ldg(&slots[hh]);
+        }
+        alive[j] = hit;
+      }
+    }
+  }
+  for (int k = 0; k < p.n_fgk; ++k) {
+    const int s = p.fgk_slot[k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!alive[j]) continue;
+      const int32_t code = slot_val(vals, s, j);
+      if (code < 0 || code >= p.fgk_card[k]) {
+        atomicOr(p.err, ERR_RANGE);
+        alive[j] = false;
+        continue;
+      }
+      g[j] += (uint32_t)code * p.fgk_stride[k];
+    }
+  }
+  if (p.chunk_surv) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) surv += alive[j];
+  }
+  if (kSplit) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (alive[j]) st->e[atomicAdd(&st->n, 1u)] = make_uint2((uint32_t)(r0 + j), g[j]);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!alive[j]) continue;
+    const int64_t a = p.agg_a_role >= 0 ? load_role(p, p.agg_a_role, r0 + j) : 0;
+    const int64_t b = p.agg_b_role >= 0 ? load_role(p, p.agg_b_role, r0 + j) : 0;
+    const int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
+    if (kSmem) {
+      atomicAdd(&ssum[g[j]], (unsigned long long)v);
+      atomicAdd(&scnt[g[j]], 1ull);
+    } else {
+      atomicAdd(&p.g_sum[g[j]], (unsigned long long)v);
+      atomicAdd(&p.g_cnt[g[j]], 1ull);
+    }
+  }
+}
+
+constexpr uint32_t kVecTileRows = 1024;  // 256 threads x 4 rows
+
+// Vector path kernel over whole block tiles of kVecTileRows rows.
+template <bool kSmem, bool kSplit, int kR>
+__global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
+  extern __shared__ unsigned long long sacc[];  // [2 * n_groups] when kSmem
+  __shared__ SurvTile st;
+  unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
+  if (kSmem) {
+    for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
+  }
+  if (threadIdx.x == 0) st.n = 0;
+  __syncthreads();
+  unsigned long long surv = 0;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * kVecTileRows; t0 < p.n; t0 += (uint64_t)gridDim.x * kVecTileRows) {
+    star_rows4<kSmem, kSplit, kR>(p, t0 + 4ull * threadIdx.x, ssum, scnt, surv, &st);
+    if (kSplit) {
+      __syncthreads();
+      const unsigned int n = st.n;
+      if (n) {
+        if (threadIdx.x == 0) st.base = atomicAdd(p.surv_cnt, n);
+        __syncthreads();
+        for (unsigned int k = threadIdx.x; k < n; k += blockDim.x) p.surv_list[st.base + k] = st.e[k];
+        __syncthreads();
+        if (threadIdx.x == 0) st.n = 0;
+        __syncthreads();
+      }
+    }
+  }
+  if (kSmem) {
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < p.n_groups; q += blockDim.x) {
+      if (scnt[q]) {
+        atomicAdd(&p.g_sum[q], ssum[q]);
+        atomicAdd(&p.g_cnt[q], scnt[q]);
+      }
+    }
+  }
+  if (p.chunk_surv) {
+    for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+    if ((threadIdx.x & 31) == 0 && surv) atomicAdd(&p.chunk_surv[p.chunk_idx], surv);
+  }
+}
+
+template <bool kSmem, bool kSplit>
+static void launch_vec(const ChunkParams &p, int kr, int grid, size_t smem, cudaStream_t s) {
+  switch (kr) {
+    case 2: star_vec_kernel<kSmem, kSplit, 2><<<grid, 256, smem, s>>>(p); break;
+    case 4: star_vec_kernel<kSmem, kSplit, 4><<<grid, 256, smem, s>>>(p); break;
+    case 6: star_vec_kernel<kSmem, kSplit, 6><<<grid, 256, smem, s>>>(p); break;
+    default: star_vec_kernel<kSmem, kSplit, 8><<<grid, 256, smem, s>>>(p); break;
+  }
+}
+
+template <bool kSmem, bool kSplit>
+static vx_status vec_attr(size_t smem) {
+  static bool done = false;
+  if (!done && smem > 0) {
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    done = true;
+  }
+  return VX_OK;
+}
+
+// width (2, 4, 6 or 8 loaded columns) of the vector path for a chunk, or 0
+// for the scalar path (no row-logic column, more than 8, or a staged column
+// not 16-byte aligned)
+static int vec_width(const ChunkParams &p) {
+  if (p.n_rowroles < 1 || p.n_rowroles > 8) return 0;
+  for (int k = 0; k < p.n_rowroles; ++k) {
+    const int32_t *c = p.staged[p.rowrole[k]];
+    if (!c || ((uintptr_t)c & 15)) return 0;
+  }
+  return p.n_rowroles <= 2 ? 2 : p.n_rowroles <= 4 ? 4 : p.n_rowroles <= 6 ? 6 : 8;
 }
 
 // Split mode, pass 1: filter, probe and group id per row; survivors of each
@@ -374,7 +630,7 @@ __global__ void __launch_bounds__(kChunkSampleRows) chunk_features_kernel(const 
     bool all = ok;
     for (int d = 0; d < p.n_dims; ++d) {  // every probe, for the per-dimension marginals
       uint32_t v = 0;
-      const bool hit = ht_lookup(p.ht[d], p.ht_log2[d], p.zc[p.dim_role[d]][p.row0 + i], v);
+      const bool hit = dim_lookup(p, d, p.zc[p.dim_role[d]][p.row0 + i], v);
       if (hit) atomicAdd(&cd[d], 1u);
       all = all && hit;
     }
@@ -454,7 +710,7 @@ __global__ void ridge_solve_kernel(const double *acc, int d, double lambda, floa
 // Fraction of sampled rows passing the fact predicates (planner estimate);
 // reads the sampled rows through mapped host memory, in runs of kSampleRun
 // consecutive rows so that a few host pages are touched.
-constexpr uint32_t kSampleRun = 64;
+constexpr uint32_t kSampleRun = 256;  // 32 runs for the 8,192-row sample
 __global__ void sample_preds_kernel(const SampleParams p) {
   unsigned long long c = 0;
   const uint32_t n_seg = (p.n_samples + kSampleRun - 1) / kSampleRun;
@@ -570,25 +826,74 @@ static int grid_for(vx_ctx *ctx, uint64_t work_items, int threads) {
   return want < 1 ? 1 : (int)want;
 }
 
+__global__ void key_minmax_kernel(const int32_t *key, uint64_t n, int *out) {
+  int lo = INT_MAX, hi = INT_MIN;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int k = key[i];
+    lo = min(lo, k);
+    hi = max(hi, k);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    lo = min(lo, __shfl_down_sync(0xffffffffu, lo, off));
+    hi = max(hi, __shfl_down_sync(0xffffffffu, hi, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&out[0], lo);
+    atomicMax(&out[1], hi);
+  }
+}
+
 vx_status build_dim_table(vx_ctx *ctx, const DimSpec &d, BuiltDim *out, uint32_t *d_err, uint64_t *d_passed) {
   const uint64_t rows = d.rows;
-  uint32_t log2cap = ceil_log2(std::max<uint64_t>(2 * rows, 16));
-  if (log2cap > 31) {
-    set_error("dimension of %llu rows is too large for a 32-bit-indexed table", (unsigned long long)rows);
-    return VX_E_UNSUPPORTED;
-  }
-  out->log2cap = log2cap;
+  cudaStream_t s = ctx->s_compute;
   out->rows = rows;
   out->buf.arena = &ctx->arena;
-  out->buf.p = ctx->arena.alloc((1ull << log2cap) * sizeof(uint64_t));
-  if (!out->buf.p) {
-    set_error("dimension hash table of %llu bytes does not fit the arena", (unsigned long long)(8ull << log2cap));
-    return VX_E_NOMEM;
+  // dense keys (span <= 2 x rows) get a direct map of 4-byte values
+  if (rows) {
+    DevBuf mm;
+    mm.arena = &ctx->arena;
+    mm.p = ctx->arena.alloc(256);
+    if (!mm.p) {
+      set_error("arena exhausted");
+      return VX_E_NOMEM;
+    }
+    const int init[2] = {INT_MAX, INT_MIN};
+    int h[2];
+    VX_CUDA_TRY(cudaMemcpyAsync(mm.p, init, 8, cudaMemcpyHostToDevice, s));
+    key_minmax_kernel<<<grid_for(ctx, rows, 256), 256, 0, s>>>(d.key, rows, mm.as<int>());
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_CUDA_TRY(cudaMemcpyAsync(h, mm.p, 8, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint64_t span = (uint64_t)((int64_t)h[1] - (int64_t)h[0]) + 1;
+    if (span <= 2 * rows && span < (1ull << 31)) {
+      out->kmin = h[0];
+      out->span = (uint32_t)span;
+    }
   }
-  cudaStream_t s = ctx->s_compute;
-  uint64_t cap = 1ull << log2cap;
-  fill_u64_kernel<<<grid_for(ctx, cap, 256), 256, 0, s>>>(out->buf.as<uint64_t>(), cap, HT_EMPTY);
-  VX_CUDA_TRY(cudaGetLastError());
+  uint32_t log2cap = 0;
+  if (out->span) {
+    out->buf.p = ctx->arena.alloc(4ull * out->span);
+    if (!out->buf.p) {
+      set_error("dimension map of %llu bytes does not fit the arena", (unsigned long long)(4ull * out->span));
+      return VX_E_NOMEM;
+    }
+    VX_CUDA_TRY(cudaMemsetAsync(out->buf.p, 0xFF, 4ull * out->span, s));  // every value empty
+  } else {
+    log2cap = ceil_log2(std::max<uint64_t>(2 * rows, 16));
+    if (log2cap > 31) {
+      set_error("dimension of %llu rows is too large for a 32-bit-indexed table", (unsigned long long)rows);
+      return VX_E_UNSUPPORTED;
+    }
+    out->log2cap = log2cap;
+    out->buf.p = ctx->arena.alloc((1ull << log2cap) * sizeof(uint64_t));
+    if (!out->buf.p) {
+      set_error("dimension hash table of %llu bytes does not fit the arena", (unsigned long long)(8ull << log2cap));
+      return VX_E_NOMEM;
+    }
+    uint64_t cap = 1ull << log2cap;
+    fill_u64_kernel<<<grid_for(ctx, cap, 256), 256, 0, s>>>(out->buf.as<uint64_t>(), cap, HT_EMPTY);
+    VX_CUDA_TRY(cudaGetLastError());
+  }
   DimBuildParams bp{};
   bp.key = d.key;
   bp.rows = rows;
@@ -605,10 +910,13 @@ vx_status build_dim_table(vx_ctx *ctx, const DimSpec &d, BuiltDim *out, uint32_t
     bp.pred_lo[q] = d.pred_lo[q];
     bp.pred_hi[q] = d.pred_hi[q];
   }
-  bp.slots = out->buf.as<uint64_t>();
+  bp.slots = out->span ? nullptr : out->buf.as<uint64_t>();
   bp.log2cap = log2cap;
   bp.err = d_err;
   bp.passed = (unsigned long long *)d_passed;
+  bp.dmap = out->span ? out->buf.as<uint32_t>() : nullptr;
+  bp.kmin = out->kmin;
+  bp.span = out->span;
   if (rows) {
     ht_build_kernel<<<grid_for(ctx, rows, 256), 256, 0, s>>>(bp);
     VX_CUDA_TRY(cudaGetLastError());
@@ -707,8 +1015,13 @@ struct StarExKernel : ExKernel {
       p.surv_list = (uint2 *)(slot + cols_bytes());
       p.surv_cnt = (unsigned int *)(slot + cols_bytes() + chunk_rows * 8);
       VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
-      const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
-      star_split_kernel<<<gs, 256, 0, s>>>(p);
+      const int kr = vec_width(p);
+      if (kr) {
+        launch_vec<false, true>(p, kr, grid_for(ctx, (p.n + kVecTileRows - 1) / kVecTileRows, 1), 0, s);
+      } else {
+        const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
+        star_split_kernel<<<gs, 256, 0, s>>>(p);
+      }
       if (timed) VX_CUDA_TRY(cudaEventRecord(ev_b[ek], s));
       const int gg = ctx->num_sms * 4;
       if (smem) {
@@ -728,7 +1041,16 @@ struct StarExKernel : ExKernel {
       return VX_OK;
     }
     launches += 1;
-    if (smem) {
+    const int kr = vec_width(p);
+    if (kr) {  // vector path
+      const int gv = grid_for(ctx, (p.n + kVecTileRows - 1) / kVecTileRows, 1);
+      if (smem) {
+        VX_TRY((vec_attr<true, false>(smem_bytes)));
+        launch_vec<true, false>(p, kr, gv, smem_bytes, s);
+      } else {
+        launch_vec<false, false>(p, kr, gv, 0, s);
+      }
+    } else if (smem) {
       static bool attr_set = false;
       if (!attr_set) {
         VX_CUDA_TRY(cudaFuncSetAttribute(star_chunk_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -736,9 +1058,9 @@ struct StarExKernel : ExKernel {
         attr_set = true;
       }
       star_chunk_kernel<true, 8><<<g, threads, smem_bytes, s>>>(p);
-    }
-    else
+    } else {
       star_chunk_kernel<false, 8><<<g, threads, 0, s>>>(p);
+    }
     VX_CUDA_TRY(cudaGetLastError());
     if (timed) {
       VX_CUDA_TRY(cudaEventRecord(ev_b[ek], s));
@@ -1009,6 +1331,8 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
       }
       P.ht[d] = tables[d]->dim.buf.as<uint64_t>();
       P.ht_log2[d] = tables[d]->dim.log2cap;
+      P.dmin[d] = tables[d]->dim.kmin;
+      P.dspan[d] = tables[d]->dim.span;
     }
   }
   // ---- selectivity estimate: dimension pass fractions x sampled fact predicates
@@ -1055,6 +1379,20 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   if (role_col.size() > (size_t)kMaxRoles) {
     set_error("plan references %zu fact columns; at most %d", role_col.size(), kMaxRoles);
     return VX_E_UNSUPPORTED;
+  }
+  {  // vector path: the row-logic roles (always staged) and each reader's slot
+    std::vector<int> rr;
+    auto slot = [&](int role) -> int8_t {
+      for (size_t k = 0; k < rr.size(); ++k)
+        if (rr[k] == role) return (int8_t)k;
+      rr.push_back(role);
+      return (int8_t)(rr.size() - 1);
+    };
+    for (int q = 0; q < P.n_fact_preds; ++q) P.fp_slot[q] = slot(P.fp_role[q]);
+    for (int d = 0; d < P.n_dims; ++d) P.dim_slot[d] = slot(P.dim_role[d]);
+    for (int k = 0; k < P.n_fgk; ++k) P.fgk_slot[k] = slot(P.fgk_role[k]);
+    P.n_rowroles = rr.size() <= 8 ? (int)rr.size() : 0;  // 0: scalar path
+    for (size_t k = 0; k < rr.size() && k < 8; ++k) P.rowrole[k] = (int8_t)rr[k];
   }
   // ---- accumulators
   DevBuf acc;

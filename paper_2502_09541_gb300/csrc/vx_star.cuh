@@ -38,10 +38,15 @@ struct DimSpec {
   int32_t pred_attr[4] = {}, pred_op[4] = {}, pred_lo[4] = {}, pred_hi[4] = {};
 };
 
+// A dimension table on the device: an open-addressing hash table of 8-byte
+// slots, or — when the keys are dense (span <= 2 x rows) — a direct map of one
+// 4-byte value per key in [kmin, kmin + span).
 struct BuiltDim {
   DevBuf buf;
   uint32_t log2cap = 0;
   uint64_t rows = 0, passed = 0;
+  int32_t kmin = 0;
+  uint32_t span = 0;  // > 0: direct map
 };
 
 struct ResidentHT {
@@ -72,6 +77,9 @@ struct DimBuildParams {
   uint32_t log2cap;
   uint32_t *err;
   unsigned long long *passed;
+  uint32_t *dmap;  // non-null: build the direct map instead of the hash table
+  int32_t kmin;
+  uint32_t span;
 };
 
 struct ChunkParams {
@@ -82,8 +90,10 @@ struct ChunkParams {
   int32_t fp_op[VX_MAX_PREDS], fp_lo[VX_MAX_PREDS], fp_hi[VX_MAX_PREDS];
   int n_dims;
   int8_t dim_role[VX_MAX_DIMS];
-  const uint64_t *ht[VX_MAX_DIMS];
+  const uint64_t *ht[VX_MAX_DIMS];  // hash slots, or the uint32 direct map when dspan[d] > 0
   uint32_t ht_log2[VX_MAX_DIMS];
+  int32_t dmin[VX_MAX_DIMS];
+  uint32_t dspan[VX_MAX_DIMS];
   int n_fgk;
   int8_t fgk_role[VX_MAX_GKEYS];
   int32_t fgk_card[VX_MAX_GKEYS];
@@ -98,6 +108,12 @@ struct ChunkParams {
   uint64_t chunk_idx;
   uint2 *surv_list;                // split mode: (chunk row, group id) of every survivor
   unsigned int *surv_cnt;
+  // vector path: the staged roles the row logic reads (predicates, keys,
+  // fact group keys), and where each predicate / key / group key finds its
+  // value among them
+  int n_rowroles;
+  int8_t rowrole[8];
+  int8_t fp_slot[VX_MAX_PREDS], dim_slot[VX_MAX_DIMS], fgk_slot[VX_MAX_GKEYS];
 };
 
 constexpr uint32_t kStarTileRows = 2048;  // rows of one block tile (256 threads x 8 rows)

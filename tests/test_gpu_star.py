@@ -103,6 +103,33 @@ def test_star_templates_bit_exact(star_small, name, late):
     assert np.array_equal(s, es[nz]) and np.array_equal(c, ec[nz])
 
 
+@pytest.mark.parametrize("name", ["T2_10", "T3_1", "T1"])
+def test_star_sparse_dimension_keys_use_hash_tables(name):
+    """Dimension keys spread over a wide range (span > 2x rows) are stored in
+    open-addressing tables instead of direct maps; results are unchanged."""
+    n = 1_500_000
+    fact = G.star_fact(n, seed=23)
+    dims = G.star_dims(0)
+    remap = lambda k: (k.astype(np.int64) * 7919 + 13).astype(np.int32)
+    sdims = {d: dict(v, key=remap(v["key"])) for d, v in dims.items()}
+    sfact = dict(fact)
+    for _, _, fk in G.STAR_DIMS:
+        sfact[fk] = remap(fact[fk])
+    T = G.star_templates()[name]
+    ctx = _open(256 << 20, 16 << 20)
+    try:
+        fid = {c: vx.vx_register_host_column(ctx, c, sfact[c]) for c in sfact}
+        did = {d: {a: vx.vx_register_host_column(ctx, f"{d}.{a}", arr) for a, arr in sdims[d].items()}
+               for d in sdims}
+        for late in (vx.VX_LATE_FORCE_EARLY, vx.VX_LATE_FORCE_LATE):
+            st, gid, s, c, _ = vx.vx_run_plan(ctx, vx.make_plan(T, fid, did, G.STAR_ATTR_CARD, late))
+            es, ec = O.star(T, sfact, sdims, nthreads=8)
+            nz = np.nonzero(ec)[0]
+            assert np.array_equal(gid, nz) and np.array_equal(s, es[nz]) and np.array_equal(c, ec[nz])
+    finally:
+        vx.vx_close(ctx)
+
+
 def test_star_range_and_capacity(star_small):
     ctx, fact, dims, fid, did = star_small
     T = G.star_templates()["T3_10"]
