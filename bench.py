@@ -345,7 +345,9 @@ def run_ours(args):
 
     def step(collect, plan_list=None):
         for p in plan_list or plans:
+            t = time.perf_counter()
             st, gid, s, c, stats = vx.vx_run_plan(ctx, p)
+            stats["host_ms"] = 1e3 * (time.perf_counter() - t)  # the call as the caller sees it
             assert st == vx.VX_OK
             collect.append(stats)
 
@@ -465,6 +467,7 @@ def run_ours(args):
                  "link_frac": round(link_gbs / h2d_peak, 4), "host_frac": round(host_gbs / world / h2d_peak, 4)},
         "rows_per_s": round(rows_step * world / (ms_step / 1000)),
         "query_ms": per_q_ms,
+        "call_overhead_ms": round(statistics.median(s["host_ms"] - s["ms_total"] for s in stats_all), 3),
         "roofline": roofline,
         "e2e": {"value": round(e2e_gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": int(e2e_h2d),
                 "d2h_bytes_per_step": int(e2e_d2h)},

@@ -446,6 +446,18 @@ vx_status vx_serve_stats_get(vx_ctx *ctx, vx_serve_stats *out);
 /* Stops the engine (pending queries are dropped); vx_close also does this. */
 vx_status vx_serve_stop(vx_ctx *ctx);
 
+/* ---------------------------------------------------------------- zero-copy probe */
+
+/* The Section 6.3 micro-benchmark behind TH: for each SEL in sels,
+ *   sum over i < n of (pred[i mod npred] mod SEL == 0 ? v[i] : 0)
+ * with pred (npred = min(n, 2^24) int32) in device memory and v (n int32) in
+ * pinned host memory, timed twice: reading v through mapped host memory
+ * (ms_zero_copy[k]) and after double-buffered copy-engine transfers into HBM
+ * (ms_copy[k]).  The sums of both reads must agree (checksums[k], optional).
+ * Zero-copy wins for SEL above 1/TH. */
+vx_status vx_probe_zero_copy(vx_ctx *ctx, uint64_t n, const int32_t *sels, int32_t n_sel, double *ms_zero_copy,
+                             double *ms_copy, uint64_t *checksums);
+
 /* ---------------------------------------------------------------- link probe */
 
 /* Pinned-copy microbenchmark of the host link (Section 8.1 measures Exchange

@@ -160,6 +160,7 @@ SIGNATURES = {
     "vx_last_stats": ([_vp, _P(vx_query_stats)], _i32),
     "vx_drop_resident": ([_vp], _i32),
     "vx_probe_link": ([_vp, _u64, _u64, _P(_dbl), _P(_dbl), _P(_dbl)], _i32),
+    "vx_probe_zero_copy": ([_vp, _u64, _vp, _i32, _vp, _vp, _vp], _i32),
     "vx_sort": ([_vp, _i32, _i32, _vp, _vp, _P(vx_sort_opts), _P(vx_sort_stats)], _i32),
     "vx_radix_sort_pairs": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_range_partition": ([_vp, _vp, _vp, _u64, _vp, _u32, _vp, _vp, _vp], _i32),
@@ -394,6 +395,16 @@ def vx_last_stats(ctx) -> dict:
     s = vx_query_stats()
     _check(load().vx_last_stats(ctx, ctypes.byref(s)))
     return s.as_dict()
+
+
+def vx_probe_zero_copy(ctx, n: int, sels):
+    """Returns (ms_zero_copy[k], ms_copy[k], checksums[k]) per SEL."""
+    s = np.ascontiguousarray(sels, np.int32)
+    zc = np.zeros(len(s), np.float64)
+    ce = np.zeros(len(s), np.float64)
+    ck = np.zeros(len(s), np.uint64)
+    _check(load().vx_probe_zero_copy(ctx, n, s.ctypes.data, len(s), zc.ctypes.data, ce.ctypes.data, ck.ctypes.data))
+    return zc, ce, ck
 
 
 def vx_probe_link(ctx, nbytes: int, chunk: int):

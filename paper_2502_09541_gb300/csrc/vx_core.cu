@@ -311,6 +311,126 @@ VX_API vx_status vx_last_stats(vx_ctx *ctx, vx_query_stats *out) {
   return VX_OK;
 }
 
+// ------------------------------------------------------------------ zero-copy probe
+// The Section 6.3 micro-benchmark: sum += pred[i % npred] % SEL == 0 ? v[i] : 0
+// with pred in device memory and v in host memory, read either through mapped
+// host memory (zero-copy) or after a copy-engine transfer into HBM.
+namespace vx {
+__global__ void zc_probe_kernel(const int *__restrict__ pred, uint64_t npred, const int *__restrict__ v, uint64_t n,
+                                uint64_t v_off, int sel, unsigned long long *out) {
+  unsigned long long s = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t g = v_off + i;
+    if (pred[g % npred] % sel == 0) s += (unsigned)v[i];
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+__global__ void zc_fill_pred_kernel(int *p, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t x = (i + 1) * 0x9E3779B97F4A7C15ull;
+    x ^= x >> 31;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 29;
+    p[i] = (int)(x & 0x7fffffff);
+  }
+}
+}  // namespace vx
+
+VX_API vx_status vx_probe_zero_copy(vx_ctx *ctx, uint64_t n, const int32_t *sels, int32_t n_sel, double *ms_zero_copy,
+                                    double *ms_copy, uint64_t *checksums) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (!n || !sels || n_sel < 1 || !ms_zero_copy || !ms_copy) {
+    set_error("vx_probe_zero_copy: bad argument");
+    return VX_E_INVAL;
+  }
+  for (int k = 0; k < n_sel; ++k)
+    if (sels[k] < 1) {
+      set_error("vx_probe_zero_copy: SEL must be >= 1");
+      return VX_E_INVAL;
+    }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const uint64_t npred = std::min<uint64_t>(n, 16ull << 20);
+  const uint64_t chunk = 16ull << 20;  // ints per copy chunk (64 MiB)
+  DevBuf pb, cb, ob;
+  pb.arena = cb.arena = ob.arena = &ctx->arena;
+  pb.p = ctx->arena.alloc(4 * npred);
+  cb.p = ctx->arena.alloc(2 * 4 * chunk);
+  ob.p = ctx->arena.alloc(256);
+  if (!pb.p || !cb.p || !ob.p) {
+    set_error("vx_probe_zero_copy: %llu bytes do not fit the arena", (unsigned long long)(4 * npred + 8 * 4 * chunk));
+    return VX_E_NOMEM;
+  }
+  int *hv = nullptr, *dv = nullptr;
+  VX_CUDA_TRY(cudaHostAlloc((void **)&hv, 4 * n, cudaHostAllocMapped));
+  struct FreeHost {
+    void *p;
+    ~FreeHost() { cudaFreeHost(p); }
+  } fh{hv};
+  for (uint64_t i = 0; i < n; ++i) hv[i] = (int)(i & 1023);
+  VX_CUDA_TRY(cudaHostGetDevicePointer((void **)&dv, hv, 0));
+  cudaStream_t s = ctx->s_compute;
+  zc_fill_pred_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(pb.as<int>(), npred);
+  unsigned long long *out = ob.as<unsigned long long>();
+  cudaEvent_t e0, e1, ec[2], ek[2];
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int i = 0; i < 2; ++i) {
+    cudaEventCreateWithFlags(&ec[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ek[i], cudaEventDisableTiming);
+  }
+  const int grid = ctx->num_sms * 8;
+  for (int k = 0; k < n_sel; ++k) {
+    // zero-copy: the kernel reads v through mapped host memory
+    VX_CUDA_TRY(cudaMemsetAsync(out, 0, 8, s));
+    cudaEventRecord(e0, s);
+    zc_probe_kernel<<<grid, 256, 0, s>>>(pb.as<int>(), npred, dv, n, 0, sels[k], out);
+    cudaEventRecord(e1, s);
+    VX_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms_zero_copy[k] = ms;
+    unsigned long long zc_sum = 0;
+    VX_CUDA_TRY(cudaMemcpy(&zc_sum, out, 8, cudaMemcpyDeviceToHost));
+    // copy engine: double-buffered 64 MiB chunks into HBM, same kernel on HBM
+    VX_CUDA_TRY(cudaMemsetAsync(out, 0, 8, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaEventRecord(e0, s);
+    cudaEventRecord(ek[0], s);
+    cudaEventRecord(ek[1], s);
+    for (uint64_t off = 0, c = 0; off < n; off += chunk, ++c) {
+      const uint64_t m = std::min(chunk, n - off);
+      int *buf = cb.as<int>() + (c & 1) * chunk;
+      cudaStreamWaitEvent(ctx->s_h2d, ek[c & 1], 0);
+      cudaMemcpyAsync(buf, hv + off, 4 * m, cudaMemcpyHostToDevice, ctx->s_h2d);
+      cudaEventRecord(ec[c & 1], ctx->s_h2d);
+      cudaStreamWaitEvent(s, ec[c & 1], 0);
+      zc_probe_kernel<<<grid, 256, 0, s>>>(pb.as<int>(), npred, buf, m, off, sels[k], out);
+      cudaEventRecord(ek[c & 1], s);
+    }
+    cudaEventRecord(e1, s);
+    VX_CUDA_TRY(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms_copy[k] = ms;
+    unsigned long long ce_sum = 0;
+    VX_CUDA_TRY(cudaMemcpy(&ce_sum, out, 8, cudaMemcpyDeviceToHost));
+    if (ce_sum != zc_sum) {
+      set_error("vx_probe_zero_copy: the two reads disagree");
+      return VX_E_CUDA;
+    }
+    if (checksums) checksums[k] = zc_sum;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < 2; ++i) {
+    cudaEventDestroy(ec[i]);
+    cudaEventDestroy(ek[i]);
+  }
+  VX_CUDA_TRY(cudaGetLastError());
+  return VX_OK;
+}
+
 // ------------------------------------------------------------------ link probe
 VX_API vx_status vx_probe_link(vx_ctx *ctx, uint64_t bytes, uint64_t chunk, double *h2d, double *d2h,
                                double *bidir) {

@@ -466,6 +466,13 @@ static vx_status vec_attr(size_t smem) {
   return VX_OK;
 }
 
+// one block per tile: the hardware keeps as many resident as registers allow
+// and starts the next as soon as one finishes
+static int vec_grid(uint64_t n) {
+  const uint64_t t = (n + kVecTileRows - 1) / kVecTileRows;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(t, 1u << 30));
+}
+
 // width (2, 4, 6 or 8 loaded columns) of the vector path for a chunk, or 0
 // for the scalar path (no row-logic column, more than 8, or a staged column
 // not 16-byte aligned)
@@ -1017,7 +1024,7 @@ struct StarExKernel : ExKernel {
       VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
       const int kr = vec_width(p);
       if (kr) {
-        launch_vec<false, true>(p, kr, grid_for(ctx, (p.n + kVecTileRows - 1) / kVecTileRows, 1), 0, s);
+        launch_vec<false, true>(p, kr, vec_grid(p.n), 0, s);
       } else {
         const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
         star_split_kernel<<<gs, 256, 0, s>>>(p);
@@ -1043,7 +1050,7 @@ struct StarExKernel : ExKernel {
     launches += 1;
     const int kr = vec_width(p);
     if (kr) {  // vector path
-      const int gv = grid_for(ctx, (p.n + kVecTileRows - 1) / kVecTileRows, 1);
+      const int gv = vec_grid(p.n);
       if (smem) {
         VX_TRY((vec_attr<true, false>(smem_bytes)));
         launch_vec<true, false>(p, kr, gv, smem_bytes, s);

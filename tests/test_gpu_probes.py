@@ -1,0 +1,39 @@
+"""Link probes: pinned-copy bandwidth and the zero-copy vs copy-engine
+micro-benchmark of Section 6.3 that TH rests on."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+vx = pytest.importorskip("paper_2502_09541_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = vx.vx_open(1 << 30)
+    yield c
+    vx.vx_close(c)
+
+
+def test_link_probe_reports_bandwidth(ctx):
+    h2d, d2h, bid = vx.vx_probe_link(ctx, 256 << 20, 32 << 20)
+    assert 20 < h2d < 2000 and 20 < d2h < 2000 and bid > max(h2d, d2h) * 0.8
+
+
+def test_zero_copy_crossover(ctx):
+    sels = [1, 2, 4, 8, 16, 32, 64, 128]
+    n = 64 << 20
+    zc, ce, ck = vx.vx_probe_zero_copy(ctx, n, sels)
+    assert np.all(zc > 0) and np.all(ce > 0)
+    # both reads computed the same sums; a sparser predicate sums less
+    assert np.all(np.diff(ck.astype(np.float64)) <= 0)
+    # every 4-byte row read: zero-copy moves whole granules, no gain over copies
+    assert zc[0] > 0.7 * ce[0]
+    # one row in 128: zero-copy reads a fraction of the granules and wins
+    assert zc[-1] < ce[-1]
+    # the crossover SEL (zero-copy at least 10% faster) is the inverse of the
+    # measured threshold.  With equal zero-copy and copy bandwidth and a 64-byte
+    # granule, the formula's 1/TH = 16 assumes every selected row costs a whole
+    # granule; neighbours sharing granules move the measured crossover lower.
+    cross = next(s for s, a, b in zip(sels, zc, ce) if a < 0.9 * b)
+    assert 2 <= cross <= 32, (cross, zc.tolist(), ce.tolist())
