@@ -367,7 +367,7 @@ typedef struct {
   int32_t n_partitions; /* 0 = smallest P whose hash tables fit the budget; <= 256 */
   uint64_t seed;        /* sample positions */
   uint64_t sample_size; /* build keys sampled for the splitters (0 = 1 Mi) */
-  double load_factor;   /* hash-table load (0 = 0.8) */
+  double load_factor;   /* hash-table load; 0 = automatic: partitions counted at 0.8, each table then spread over the free budget down to 0.5 */
   int32_t count_pass;   /* 1: size tables from an exact count pass over the build keys (plain
                            form); 0: from the partition sizes the model implies, rebuilding a
                            table that overflows (learned form) */

@@ -42,8 +42,15 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// slot of a key: multiply-shift range reduction of a mixed key onto [0, cap)
-__device__ __forceinline__ uint64_t slot_of(uint64_t key, uint64_t cap) { return __umul64hi(fmix64(key ^ 0x2545F4914F6CDD1Dull), cap); }
+// Linear probing whose walk starts at a bucket boundary: the home of a key is
+// the first slot of bucket home_bucket(key) (multiply-shift range reduction of
+// a mixed key onto the nbk = cap / kJoinBucket buckets), so the home bucket of
+// two 16-byte slots is one aligned 32-byte sector.
+constexpr int kJoinBucket = 2;
+constexpr double kJoinMaxAutoLoad = 0.8, kJoinMinAutoLoad = 0.5;
+__device__ __forceinline__ uint64_t home_bucket(uint64_t key, uint64_t nbk) {
+  return __umul64hi(fmix64(key ^ 0x2545F4914F6CDD1Dull), nbk);
+}
 
 __device__ __forceinline__ bool in_range(uint64_t k, uint64_t lo, uint64_t hi, bool last) {
   return k >= lo && (last || k < hi);
@@ -92,7 +99,7 @@ __global__ void join_build_kernel(const uint64_t *keys, const uint64_t *payload,
       acc->sentinel_payload = pay;
       continue;
     }
-    uint64_t h = slot_of(k, cap);
+    uint64_t h = home_bucket(k, cap / kJoinBucket) * kJoinBucket;
     bool done = false;
     const uint64_t limit = cap < kMaxInsertSteps ? cap : kMaxInsertSteps;
     for (uint64_t step = 0; step < limit; ++step) {
@@ -123,67 +130,73 @@ __global__ void join_build_kernel(const uint64_t *keys, const uint64_t *payload,
   }
 }
 
-// probes the keys of range p; row0 = global row of keys[0]
+// probes the keys of range p; row0 = global row of keys[0].
+// A table much larger than L2 makes every probe a random DRAM access, and the
+// rate of random 32-byte sectors, not bandwidth or latency, bounds the kernel.
+// So a probe reads its home bucket (two slots, one aligned sector) in one
+// access, and each thread keeps kRows rows in flight in lock-step rounds: all
+// unresolved rows issue their next bucket read together, so a row with a long
+// chain costs rounds, not a serial walk after the rows before it.
 template <int kRows>
-__global__ void __launch_bounds__(256) join_probe_kernel(const uint64_t *__restrict__ keys, uint64_t n, uint64_t row0,
-                                                         uint64_t lo, uint64_t hi, bool last,
-                                                         const JoinSlot *__restrict__ t, uint64_t cap, JoinAcc *acc) {
+__global__ void __launch_bounds__(256, 4) join_probe_kernel(const uint64_t *__restrict__ keys, uint64_t n,
+                                                            uint64_t row0, uint64_t lo, uint64_t hi, bool last,
+                                                            const JoinSlot *__restrict__ t, uint64_t cap,
+                                                            JoinAcc *acc) {
   unsigned long long c = 0, s = 0, f = 0;
   const bool sp = acc->sentinel_present != 0;
   const uint64_t spay = acc->sentinel_payload;
-  const uint64_t max_disp = acc->max_disp;  // every key sits within this many slots of its home
+  const uint64_t nbk = cap / kJoinBucket;
+  // every key sits within max_disp slots of its (bucket-aligned) home
+  const uint64_t max_rounds = acc->max_disp / kJoinBucket + 1;
+  const ulonglong2 *tv = reinterpret_cast<const ulonglong2 *>(t);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kRows;
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x * kRows + threadIdx.x; base < n; base += stride) {
-    uint64_t k[kRows], h[kRows];
-    bool act[kRows];
-    JoinSlot sl[kRows];
+    uint64_t k[kRows], b[kRows];
+    unsigned live = 0;
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       const uint64_t i = base + (uint64_t)j * blockDim.x;
-      act[j] = false;
-      if (i < n) {
-        k[j] = keys[i];
-        act[j] = in_range(k[j], lo, hi, last);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kRows; ++j) {
-      h[j] = act[j] ? slot_of(k[j], cap) : 0;
-      if (act[j] && k[j] != kJoinEmpty) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(t) + h[j]);
-        sl[j].key = v.x;
-        sl[j].payload = v.y;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kRows; ++j) {
-      if (!act[j]) continue;
-      const uint64_t i = base + (uint64_t)j * blockDim.x;
-      bool hit = false;
-      uint64_t pay = 0;
-      if (k[j] == kJoinEmpty) {
-        hit = sp;
-        pay = spay;
-      } else {
-        JoinSlot cur = sl[j];
-        uint64_t hh = h[j];
-        for (uint64_t step = 0; step <= max_disp; ++step) {
-          if (cur.key == kJoinEmpty) break;
-          if (cur.key == k[j]) {
-            hit = true;
-            pay = cur.payload;
-            break;
-          }
-          hh = hh + 1 == cap ? 0 : hh + 1;
-          const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(t) + hh);
-          cur.key = v.x;
-          cur.payload = v.y;
+      k[j] = i < n ? keys[i] : kJoinEmpty;
+      if (i < n && in_range(k[j], lo, hi, last)) {
+        if (k[j] != kJoinEmpty) {
+          live |= 1u << j;
+        } else if (sp) {  // the empty-slot key matches only the build row kept aside
+          c += 1;
+          s += spay;
+          f += fmix64((row0 + i) ^ ((spay << 17) | (spay >> 47)));
         }
       }
-      if (hit) {
-        c += 1;
-        s += pay;
-        f += fmix64((row0 + i) ^ ((pay << 17) | (pay >> 47)));
+      b[j] = home_bucket(k[j], nbk);
+    }
+    for (uint64_t round = 0; live && round < max_rounds; ++round) {
+      ulonglong2 v[kRows][kJoinBucket];
+#pragma unroll
+      for (int j = 0; j < kRows; ++j)
+        if (live >> j & 1)
+#pragma unroll
+          for (int q = 0; q < kJoinBucket; ++q) v[j][q] = __ldg(tv + b[j] * kJoinBucket + q);
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        if (!(live >> j & 1)) continue;
+        bool hit = false, empty = false;
+        uint64_t pay = 0;
+#pragma unroll
+        for (int q = 0; q < kJoinBucket; ++q) {
+          if (v[j][q].x == k[j]) {
+            hit = true;
+            pay = v[j][q].y;
+          }
+          empty |= v[j][q].x == kJoinEmpty;
+        }
+        if (hit) {
+          c += 1;
+          s += pay;
+          f += fmix64((row0 + base + (uint64_t)j * blockDim.x) ^ ((pay << 17) | (pay >> 47)));
+        }
+        // no deletions and bucket-aligned homes: a key lies before the first
+        // empty slot of its walk, so an empty slot in the bucket ends it
+        if (hit || empty) live &= ~(1u << j);
+        else b[j] = b[j] + 1 == nbk ? 0 : b[j] + 1;
       }
     }
   }
@@ -269,7 +282,10 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
   }
   vx_join_opts o{};
   if (opts) o = *opts;
-  if (o.load_factor <= 0) o.load_factor = 0.8;
+  // load factor 0 = automatic: partitions are counted at load 0.8, then each
+  // table spreads over the free budget down to load 0.5 (fewer sectors per probe)
+  const bool auto_load = o.load_factor <= 0;
+  if (auto_load) o.load_factor = kJoinMaxAutoLoad;
   if (o.load_factor > 0.95 || o.n_partitions < 0 || o.n_partitions > 256 || o.partitioner < VX_PART_SAMPLE ||
       o.partitioner > VX_PART_LEARNED_MLP) {
     set_error("vx_join: bad options");
@@ -300,7 +316,7 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
     return VX_E_NOMEM;
   }
   const uint64_t table_bytes_max = (uint64_t)((avail - staging) * 0.98);
-  const uint64_t slots_max = table_bytes_max / sizeof(JoinSlot);
+  const uint64_t slots_max = table_bytes_max / sizeof(JoinSlot) / kJoinBucket * kJoinBucket;
   // ---- partitions: P such that each table (at the load factor) fits
   uint32_t P = o.n_partitions > 0 ? (uint32_t)o.n_partitions
                                   : (uint32_t)std::max<double>(1.0, std::ceil(nb / (o.load_factor * slots_max) * 1.05));
@@ -359,6 +375,9 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
     const bool last = p + 1 == P;
     if (p > 0 && p + 1 < P && hi <= lo) continue;  // empty range
     uint64_t cap = std::max<uint64_t>((uint64_t)std::ceil(part_n[p] / o.load_factor), 1024);
+    if (auto_load)
+      cap = std::max(cap, std::min<uint64_t>((uint64_t)std::ceil(part_n[p] / kJoinMinAutoLoad), slots_max));
+    cap = (cap + kJoinBucket - 1) / kJoinBucket * kJoinBucket;
     for (int attempt = 0;; ++attempt) {
       if (cap > slots_max) {
         set_error("vx_join: partition %u needs %llu slots; %llu fit", p, (unsigned long long)cap,
@@ -404,7 +423,7 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
       if ((h.err & ERR_HT_FULL) || h.inserted > (uint64_t)(0.95 * cap)) {
         // the table overflowed its load limit: rebuild larger (learned sizing's retry)
         res.overflow_retries += 1;
-        cap = (uint64_t)std::ceil(h.inserted / o.load_factor) + 4096;
+        cap = ((uint64_t)std::ceil(h.inserted / o.load_factor) + 4096) / kJoinBucket * kJoinBucket;
         if (attempt >= 3) {
           set_error("vx_join: table sizing did not converge");
           return VX_E_NOMEM;
@@ -420,7 +439,7 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
       ppass.n = np;
       ppass.R = 2 * R;
       ppass.fn = [&](const uint64_t *k, const uint64_t *, uint64_t n, uint64_t row0, cudaStream_t st) -> vx_status {
-        join_probe_kernel<8><<<grid_of(ctx, (n + 7) / 8, 256, 8), 256, 0, st>>>(k, n, row0, lo, hi, last, t, cap,
+        join_probe_kernel<4><<<grid_of(ctx, (n + 3) / 4, 256, 4), 256, 0, st>>>(k, n, row0, lo, hi, last, t, cap,
                                                                                acc);
         VX_CUDA_TRY(cudaGetLastError());
         return VX_OK;
