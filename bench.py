@@ -413,13 +413,14 @@ def run_ours(args):
     hbm_peak, peak_kind = measured_peaks()
     ach = staged_bytes / (kern_ms * 1e6) if kern_ms > 0 else None
     tpr = traffic_per_row()
-    avg_launch_rows = sum(s["rows"] for s in stats_all) / max(1, launches)
+    fused_launches = int(sum(s["chunks"] for s in stats_all))  # one fused-kernel launch per chunk
+    avg_launch_rows = sum(s["rows"] for s in stats_all) / max(1, fused_launches)
     roofline = {"bound": "hbm", "kernel": "star_chunk_kernel", "achieved": round(ach, 1) if ach else None,
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4) if ach else None,
                 "peak_kind": peak_kind,
                 "traffic": round(tpr * avg_launch_rows) if tpr else None,
-                "algorithmic_bytes_per_launch": round(staged_bytes / max(1, launches)),
-                "avg_launch_us": round(1000 * kern_ms / max(1, launches), 2)}
+                "algorithmic_bytes_per_launch": round(staged_bytes / max(1, fused_launches)),
+                "avg_launch_us": round(1000 * kern_ms / max(1, fused_launches), 2), "launches": fused_launches}
 
     # ---- learned / batched form: regressor trained on the plain form's log,
     # per-chunk late/early decisions, autotuned chunking, captured graphs

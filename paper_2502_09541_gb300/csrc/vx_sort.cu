@@ -65,9 +65,7 @@ __global__ void __launch_bounds__(kRxThreads) rx_upsweep(RadixBufs b, const Radi
   for (int r = 0; r < kRxItems; ++r) {
     const uint64_t i = wbase + (uint64_t)r * 32 + lane;
     const uint32_t d = i < n ? key_digit<kRange>(keys[i], shift, s_spl, n_spl) : kRxInvalid;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d != kRxInvalid && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][d] += __popc(peers);
-    __syncwarp();
+    if (d != kRxInvalid) atomicAdd(&wcnt[w][d], 1u);  // counting needs no order
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kRxDigits; d += blockDim.x) {
@@ -171,73 +169,117 @@ __global__ void rx_init_state(RadixState *st, const unsigned long long *bh, uint
   }
 }
 
+// dynamic shared memory of the scatter: the tile's pairs regrouped by digit
+// (keys, values, digits), per-warp digit counters, per-digit offsets
+struct RxScatterSmem {
+  uint64_t k[kRxTile];
+  uint32_t v[kRxTile];
+  uint32_t wcnt[kRxWarps][kRxDigits];
+  uint64_t off[kRxDigits];  // global position of local position 0 of each digit
+  uint32_t tstart[kRxDigits];
+  uint32_t wsum[kRxWarps];
+  uint8_t d[kRxTile];
+};
+
+// Stable scatter of one tile: rank every pair inside its warp (match_any over
+// 16 rounds of 32 consecutive pairs), regroup the tile by digit in shared
+// memory, then write each digit's run with consecutive threads on consecutive
+// output positions, so stores leave the SM as contiguous runs.
 template <bool kRange>
-__global__ void __launch_bounds__(kRxThreads) rx_downsweep(RadixBufs b, const RadixState *st, int pass, uint64_t n,
-                                                           int shift, const uint64_t *spl, int n_spl,
-                                                           const uint32_t *hist, uint32_t ntiles) {
+__global__ void __launch_bounds__(kRxThreads, 2) rx_downsweep(RadixBufs b, const RadixState *st, int pass, uint64_t n,
+                                                              int shift, const uint64_t *spl, int n_spl,
+                                                              const uint32_t *hist, uint32_t ntiles) {
   if (!kRange && st->skip[pass]) return;
-  __shared__ uint32_t wcnt[kRxWarps][kRxDigits];
-  __shared__ uint64_t s_off[kRxDigits];
+  extern __shared__ __align__(16) unsigned char rx_smem[];
+  RxScatterSmem &sm = *reinterpret_cast<RxScatterSmem *>(rx_smem);
   __shared__ uint64_t s_spl[kRxDigits];
   const int c = kRange ? 0 : st->cur[pass];
   const uint64_t *kin = b.keys[c];
   const uint32_t *vin = b.vals[c];
   uint64_t *kout = b.keys[1 - c];
   uint32_t *vout = b.vals[1 - c];
-  for (int i = threadIdx.x; i < kRxWarps * kRxDigits; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kRxWarps * kRxDigits; i += blockDim.x) (&sm.wcnt[0][0])[i] = 0;
   if (kRange)
     for (int i = threadIdx.x; i < n_spl; i += blockDim.x) s_spl[i] = spl[i];
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint64_t wbase = (uint64_t)blockIdx.x * kRxTile + (uint64_t)w * (32 * kRxItems);
+  const uint64_t tbase = (uint64_t)blockIdx.x * kRxTile;
+  const uint64_t wbase = tbase + (uint64_t)w * (32 * kRxItems);
   uint64_t k[kRxItems];
-  uint32_t v[kRxItems], dg[kRxItems], rk[kRxItems];
+  uint32_t v[kRxItems], dr[kRxItems];  // dr = rank inside the warp << 9 | digit
 #pragma unroll
   for (int r = 0; r < kRxItems; ++r) {
     const uint64_t i = wbase + (uint64_t)r * 32 + lane;
-    if (i < n) {
-      k[r] = kin[i];
-      v[r] = vin[i];
-    } else {
-      k[r] = 0;
-      v[r] = 0;
-    }
+    k[r] = i < n ? kin[i] : 0;
+    v[r] = i < n ? vin[i] : 0;
   }
 #pragma unroll
   for (int r = 0; r < kRxItems; ++r) {
     const uint64_t i = wbase + (uint64_t)r * 32 + lane;
-    dg[r] = i < n ? key_digit<kRange>(k[r], shift, s_spl, n_spl) : kRxInvalid;
-  }
-#pragma unroll
-  for (int r = 0; r < kRxItems; ++r) {
-    const uint32_t d = dg[r];
+    const uint32_t d = i < n ? key_digit<kRange>(k[r], shift, s_spl, n_spl) : kRxInvalid;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
-    if (d != kRxInvalid) before = wcnt[w][d];
+    if (d != kRxInvalid) before = sm.wcnt[w][d];
     __syncwarp();
-    rk[r] = before + __popc(peers & lanemask_lt());
-    if (d != kRxInvalid && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][d] = before + __popc(peers);
+    dr[r] = (before + __popc(peers & lanemask_lt())) << 9 | d;
+    if (d != kRxInvalid && lane == (uint32_t)(__ffs(peers) - 1)) sm.wcnt[w][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRxDigits; d += blockDim.x) {
+  {  // thread d: warp offsets within digit d, then the tile's digit starts (exclusive scan over digits)
+    const int d = threadIdx.x;
     uint32_t run = 0;
+#pragma unroll
     for (int q = 0; q < kRxWarps; ++q) {
-      const uint32_t cq = wcnt[q][d];
-      wcnt[q][d] = run;
+      const uint32_t cq = sm.wcnt[q][d];
+      sm.wcnt[q][d] = run;
       run += cq;
     }
-    s_off[d] = st->base[d] + hist[(uint64_t)d * ntiles + blockIdx.x];
+    uint32_t x = run;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= (uint32_t)off) x += y;
+    }
+    if (lane == 31) sm.wsum[w] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+#pragma unroll
+    for (int q = 0; q < kRxWarps; ++q) wpre += q < (int)w ? sm.wsum[q] : 0u;
+    const uint32_t excl = wpre + x - run;
+    sm.tstart[d] = excl;
+    sm.off[d] = st->base[d] + hist[(uint64_t)d * ntiles + blockIdx.x] - excl;  // wraps back when added to a position
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kRxItems; ++r) {
-    const uint32_t d = dg[r];
+    const uint32_t d = dr[r] & 0x1FFu;
     if (d == kRxInvalid) continue;
-    const uint64_t pos = s_off[d] + wcnt[w][d] + rk[r];
-    kout[pos] = k[r];
-    vout[pos] = v[r];
+    const uint32_t lp = sm.tstart[d] + sm.wcnt[w][d] + (dr[r] >> 9);
+    sm.k[lp] = k[r];
+    sm.v[lp] = v[r];
+    sm.d[lp] = (uint8_t)d;
   }
+  __syncthreads();
+  const uint32_t valid = n - tbase < (uint64_t)kRxTile ? (uint32_t)(n - tbase) : (uint32_t)kRxTile;
+  for (uint32_t t = threadIdx.x; t < valid; t += blockDim.x) {
+    const uint64_t pos = sm.off[sm.d[t]] + t;
+    kout[pos] = sm.k[t];
+    vout[pos] = sm.v[t];
+  }
+}
+
+constexpr size_t kRxScatterSmem = sizeof(RxScatterSmem);
+
+// the scatter's shared memory is above the 48 KB default: raise the limit once
+static vx_status rx_scatter_attr() {
+  static bool done = false;
+  if (!done) {
+    VX_CUDA_TRY(cudaFuncSetAttribute(rx_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRxScatterSmem));
+    VX_CUDA_TRY(cudaFuncSetAttribute(rx_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRxScatterSmem));
+    done = true;
+  }
+  return VX_OK;
 }
 
 __global__ void rx_publish(const RadixState *st, int pass, uint64_t *host_word) { *host_word = (uint64_t)st->cur[pass]; }
@@ -349,6 +391,7 @@ vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s
     VX_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(RadixState), s));
     return VX_OK;
   }
+  VX_TRY(rx_scatter_attr());
   int g = (int)std::min<uint64_t>((n + kRxThreads - 1) / kRxThreads, (uint64_t)num_sms * 4);
   rx_byte_hist<<<g, kRxThreads, 0, s>>>(b, n, bh);
   rx_init_state<<<1, 32, 0, s>>>(st, bh, n);
@@ -357,7 +400,7 @@ vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s
     rx_upsweep<false><<<nt, kRxThreads, 0, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, hist, nt);
     rx_scan_rows<<<kRxDigits, 1024, 0, s>>>(hist, nt, st, pass, true);
     rx_scan_totals<<<1, kRxDigits, 0, s>>>(st, pass, n, true);
-    rx_downsweep<false><<<nt, kRxThreads, 0, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, hist, nt);
+    rx_downsweep<false><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, hist, nt);
   }
   VX_CUDA_TRY(cudaGetLastError());
   return VX_OK;
@@ -371,13 +414,14 @@ vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, 
   uint32_t nt = std::max<uint32_t>(ntiles_of(n), 1);
   RadixState *st = radix_state_of(temp);
   uint32_t *hist = (uint32_t *)(temp + kStateBytes + kByteHistBytes);
+  VX_TRY(rx_scatter_attr());
   VX_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(RadixState), s));
   if (n) {
     rx_upsweep<true><<<nt, kRxThreads, 0, s>>>(b, st, 0, n, 0, spl, (int)P - 1, hist, nt);
     rx_scan_rows<<<kRxDigits, 1024, 0, s>>>(hist, nt, st, 0, false);
   }
   rx_scan_totals<<<1, kRxDigits, 0, s>>>(st, 0, n, false);
-  if (n) rx_downsweep<true><<<nt, kRxThreads, 0, s>>>(b, st, 0, n, 0, spl, (int)P - 1, hist, nt);
+  if (n) rx_downsweep<true><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, 0, n, 0, spl, (int)P - 1, hist, nt);
   VX_CUDA_TRY(cudaGetLastError());
   return VX_OK;
 }

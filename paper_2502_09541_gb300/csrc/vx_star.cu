@@ -261,6 +261,13 @@ __device__ __forceinline__ void star_rows(const ChunkParams &p, uint64_t base, u
   }
 }
 
+constexpr uint32_t kVecTileRows = 1024;  // one group of 4 rows per thread of 256
+
+// row j of a vector-path thread whose first row is r0 (group j / 4, lane j % 4)
+__device__ __forceinline__ uint64_t row_of(uint64_t r0, int j) {
+  return r0 + (uint64_t)(j >> 2) * kVecTileRows + (uint64_t)(j & 3);
+}
+
 __device__ __forceinline__ int32_t lane4(const int4 &v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
 
 // value of row j from the row-logic slot `slot` (compile-time select over the
@@ -274,56 +281,62 @@ __device__ __forceinline__ int32_t slot_val(const int4 (&vals)[kR], int slot, in
   return x;
 }
 
-// Vector path: 4 consecutive rows r0..r0+3 (r0 a multiple of 4, staged
-// columns 16-byte aligned).  Every row-logic column is loaded with one 16-byte
-// load before any row is evaluated, so the rows' memory latency overlaps;
+// Vector path: kV groups of 4 consecutive rows, r0 + v * kVecTileRows + 0..3
+// (r0 a multiple of 4, staged columns 16-byte aligned).  Every row-logic
+// column is loaded with one 16-byte load per group before any row is
+// evaluated, so the rows' memory latency overlaps;
 // then predicates, probes (direct map or hash, all 4 rows' lookups in flight)
 // and the group id are computed from registers.  Survivors are aggregated
 // (kSplit = false) or appended to the block's survivor list.
-template <bool kSmem, bool kSplit, int kR>
+template <bool kSmem, bool kSplit, int kR, int kV>
 __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, unsigned long long *ssum,
                                            unsigned long long *scnt, unsigned long long &surv, SurvTile *st) {
-  int4 vals[kR];
-  const bool full = r0 + 3 < p.n;
+  constexpr int kN = 4 * kV;  // rows of this thread
+  int4 vals[kV][kR];
 #pragma unroll
-  for (int k = 0; k < kR; ++k) {
-    const int32_t *col = p.staged[k < p.n_rowroles ? p.rowrole[k] : p.rowrole[0]];
-    if (full) {
-      vals[k] = __ldg(reinterpret_cast<const int4 *>(col + r0));
-    } else {
-      vals[k].x = r0 < p.n ? __ldg(col + r0) : 0;
-      vals[k].y = r0 + 1 < p.n ? __ldg(col + r0 + 1) : 0;
-      vals[k].z = r0 + 2 < p.n ? __ldg(col + r0 + 2) : 0;
-      vals[k].w = 0;
+  for (int v = 0; v < kV; ++v) {
+    const uint64_t rv = r0 + (uint64_t)v * kVecTileRows;
+    const bool full = rv + 3 < p.n;
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+      const int32_t *col = p.staged[k < p.n_rowroles ? p.rowrole[k] : p.rowrole[0]];
+      if (full) {
+        vals[v][k] = __ldg(reinterpret_cast<const int4 *>(col + rv));
+      } else {
+        vals[v][k].x = rv < p.n ? __ldg(col + rv) : 0;
+        vals[v][k].y = rv + 1 < p.n ? __ldg(col + rv + 1) : 0;
+        vals[v][k].z = rv + 2 < p.n ? __ldg(col + rv + 2) : 0;
+        vals[v][k].w = 0;
+      }
     }
   }
-  bool alive[4];
-  uint32_t g[4];
+  bool alive[kN];
+  uint32_t g[kN];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    alive[j] = r0 + j < p.n;
+  for (int j = 0; j < kN; ++j) {
+    alive[j] = row_of(r0, j) < p.n;
     g[j] = 0;
   }
   for (int q = 0; q < p.n_fact_preds; ++q) {
     const int s = p.fp_slot[q];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) alive[j] = alive[j] && pred_ok(slot_val(vals, s, j), p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+    for (int j = 0; j < kN; ++j) alive[j] = alive[j] && pred_ok(slot_val(vals[j >> 2], s, j & 3), p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
   }
   for (int d = 0; d < p.n_dims; ++d) {
     const int s = p.dim_slot[d];
-    int32_t key[4];
+    int32_t key[kN];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) key[j] = slot_val(vals, s, j);
+    for (int j = 0; j < kN; ++j) key[j] = slot_val(vals[j >> 2], s, j & 3);
     if (p.dspan[d]) {
       const uint32_t *__restrict__ map = reinterpret_cast<const uint32_t *>(p.ht[d]);
-      uint32_t v[4];
+      uint32_t v[kN];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kN; ++j) {
         const uint32_t idx = (uint32_t)(key[j] - p.dmin[d]);
         v[j] = (alive[j] && idx < p.dspan[d]) ? __ldg(&map[idx]) : HT_EMPTY_VAL;
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kN; ++j) {
         const bool hit = alive[j] && v[j] < HT_FILTERED;
         g[j] += hit ? v[j] : 0u;
         alive[j] = hit;
@@ -331,15 +344,15 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, un
     } else {
       const uint64_t *__restrict__ slots = p.ht[d];
       const uint32_t l2c = p.ht_log2[d], mask = (1u << l2c) - 1u;
-      uint32_t h[4];
-      uint64_t sl[4];
+      uint32_t h[kN];
+      uint64_t sl[kN];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kN; ++j) {
         h[j] = ht_hash32(key[j], l2c);
         sl[j] = alive[j] ? __ldg(&slots[h[j]]) : HT_EMPTY;
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kN; ++j) {
         if (!alive[j]) continue;
         uint64_t sv = sl[j];
         uint32_t hh = h[j];
@@ -362,9 +375,9 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, un
   for (int k = 0; k < p.n_fgk; ++k) {
     const int s = p.fgk_slot[k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kN; ++j) {
       if (!alive[j]) continue;
-      const int32_t code = slot_val(vals, s, j);
+      const int32_t code = slot_val(vals[j >> 2], s, j & 3);
       if (code < 0 || code >= p.fgk_card[k]) {
         atomicOr(p.err, ERR_RANGE);
         alive[j] = false;
@@ -375,19 +388,23 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, un
   }
   if (p.chunk_surv) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) surv += alive[j];
+    for (int j = 0; j < kN; ++j) surv += alive[j];
   }
   if (kSplit) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (alive[j]) st->e[atomicAdd(&st->n, 1u)] = make_uint2((uint32_t)(r0 + j), g[j]);
+    for (int j = 0; j < kN; ++j)
+      if (alive[j]) st->e[atomicAdd(&st->n, 1u)] = make_uint2((uint32_t)row_of(r0, j), g[j]);
     return;
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < kN; ++j) {
     if (!alive[j]) continue;
-    const int64_t a = p.agg_a_role >= 0 ? load_role(p, p.agg_a_role, r0 + j) : 0;
-    const int64_t b = p.agg_b_role >= 0 ? load_role(p, p.agg_b_role, r0 + j) : 0;
+    const int64_t a = p.agg_a_role < 0    ? 0
+                      : p.agg_slot[0] >= 0 ? slot_val(vals[j >> 2], p.agg_slot[0], j & 3)
+                                           : load_role(p, p.agg_a_role, row_of(r0, j));
+    const int64_t b = p.agg_b_role < 0    ? 0
+                      : p.agg_slot[1] >= 0 ? slot_val(vals[j >> 2], p.agg_slot[1], j & 3)
+                                           : load_role(p, p.agg_b_role, row_of(r0, j));
     const int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
     if (kSmem) {
       atomicAdd(&ssum[g[j]], (unsigned long long)v);
@@ -399,9 +416,12 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, un
   }
 }
 
-constexpr uint32_t kVecTileRows = 1024;  // 256 threads x 4 rows
 
-// Vector path kernel over whole block tiles of kVecTileRows rows.
+// groups of 4 rows per thread: a block tile is kVecGroups x kVecTileRows rows
+constexpr int kVecGroups = 1;  // 2 raises registers to 62-128 and measured slower
+static_assert(kVecGroups * kVecTileRows <= kStarTileRows, "a block tile's survivors must fit its list");
+
+// Vector path kernel over whole block tiles of kVecGroups x kVecTileRows rows.
 template <bool kSmem, bool kSplit, int kR>
 __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   extern __shared__ unsigned long long sacc[];  // [2 * n_groups] when kSmem
@@ -413,8 +433,9 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   if (threadIdx.x == 0) st.n = 0;
   __syncthreads();
   unsigned long long surv = 0;
-  for (uint64_t t0 = (uint64_t)blockIdx.x * kVecTileRows; t0 < p.n; t0 += (uint64_t)gridDim.x * kVecTileRows) {
-    star_rows4<kSmem, kSplit, kR>(p, t0 + 4ull * threadIdx.x, ssum, scnt, surv, &st);
+  constexpr uint64_t kTile = (uint64_t)kVecGroups * kVecTileRows;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * kTile; t0 < p.n; t0 += (uint64_t)gridDim.x * kTile) {
+    star_rows4<kSmem, kSplit, kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, ssum, scnt, surv, &st);
     if (kSplit) {
       __syncthreads();
       const unsigned int n = st.n;
@@ -469,7 +490,7 @@ static vx_status vec_attr(size_t smem) {
 // one block per tile: the hardware keeps as many resident as registers allow
 // and starts the next as soon as one finishes
 static int vec_grid(uint64_t n) {
-  const uint64_t t = (n + kVecTileRows - 1) / kVecTileRows;
+  const uint64_t t = (n + kVecGroups * kVecTileRows - 1) / (kVecGroups * kVecTileRows);
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(t, 1u << 30));
 }
 
@@ -1017,11 +1038,11 @@ struct StarExKernel : ExKernel {
     int g = grid_for(ctx, (p.n + 7) / 8, threads);
     const size_t ek = ev_a.empty() ? 0 : it % ev_a.size();
     const bool timed = !ev_a.empty() && ctx->cfg.sched == VX_SCHED_IMMEDIATE;
-    if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
     if (chunk_has_late(it)) {  // filter/probe pass, then the late-column gather
       p.surv_list = (uint2 *)(slot + cols_bytes());
       p.surv_cnt = (unsigned int *)(slot + cols_bytes() + chunk_rows * 8);
       VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
+      if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
       const int kr = vec_width(p);
       if (kr) {
         launch_vec<false, true>(p, kr, vec_grid(p.n), 0, s);
@@ -1048,10 +1069,14 @@ struct StarExKernel : ExKernel {
       return VX_OK;
     }
     launches += 1;
+    if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
     const int kr = vec_width(p);
     if (kr) {  // vector path
-      const int gv = vec_grid(p.n);
+      int gv = vec_grid(p.n);
       if (smem) {
+        // group accumulators in shared memory: a resident grid, so that each
+        // block merges its groups into global memory once per chunk, not once per tile
+        gv = std::min<int>(gv, ctx->num_sms * ctx->cfg.blocks_per_sm);
         VX_TRY((vec_attr<true, false>(smem_bytes)));
         launch_vec<true, false>(p, kr, gv, smem_bytes, s);
       } else {
@@ -1398,6 +1423,19 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
     for (int q = 0; q < P.n_fact_preds; ++q) P.fp_slot[q] = slot(P.fp_role[q]);
     for (int d = 0; d < P.n_dims; ++d) P.dim_slot[d] = slot(P.dim_role[d]);
     for (int k = 0; k < P.n_fgk; ++k) P.fgk_slot[k] = slot(P.fgk_role[k]);
+    // an aggregate column staged in every chunk joins the up-front loads, so a
+    // survivor's values need no load after its probe chain
+    // (only while the vector path's eight columns suffice)
+    const int agg_role[2] = {P.agg_a_role, P.agg_b_role};
+    const size_t n_logic = rr.size();
+    size_t n_new = 0;
+    for (int j = 0; j < 2; ++j)
+      if (agg_role[j] >= 0 && std::find(rr.begin(), rr.end(), agg_role[j]) == rr.end()) ++n_new;
+    for (int j = 0; j < 2; ++j)
+      P.agg_slot[j] = agg_role[j] >= 0 && !((late_mask | switch_mask) >> j & 1u) && n_logic >= 1 &&
+                              n_logic + n_new <= 8
+                          ? slot(agg_role[j])
+                          : (int8_t)-1;
     P.n_rowroles = rr.size() <= 8 ? (int)rr.size() : 0;  // 0: scalar path
     for (size_t k = 0; k < rr.size() && k < 8; ++k) P.rowrole[k] = (int8_t)rr[k];
   }

@@ -114,6 +114,9 @@ struct ChunkParams {
   int n_rowroles;
   int8_t rowrole[8];
   int8_t fp_slot[VX_MAX_PREDS], dim_slot[VX_MAX_DIMS], fgk_slot[VX_MAX_GKEYS];
+  // slot of each aggregate column among them when it is staged in every chunk
+  // (loaded with the row logic's columns), else -1 (loaded per survivor)
+  int8_t agg_slot[2];
 };
 
 constexpr uint32_t kStarTileRows = 2048;  // rows of one block tile (256 threads x 8 rows)
