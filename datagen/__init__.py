@@ -315,12 +315,22 @@ def probe_side(n_probe, n_build, match=1.0, zipf_s=0.0, seed=0, row0=0, out=None
     return o
 
 
-def probe_truth(n_probe, n_build, match=1.0, zipf_s=0.0, seed=0, row0=0):
-    """(match count, wrapping payload sum) recorded while drawing the probes."""
-    c, s = ctypes.c_uint64(), ctypes.c_uint64()
-    lib().vxg_probe_truth(n_probe, row0, n_build, int(round(match * 1e6)), zipf_s, seed,
-                          SALT["probe"], ctypes.byref(c), ctypes.byref(s))
-    return c.value, s.value
+def probe_truth(n_probe, n_build, match=1.0, zipf_s=0.0, seed=0, row0=0, nthreads=None):
+    """(match count, wrapping payload sum) recorded while drawing the probes;
+    row ranges are redrawn on nthreads threads (the C call releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def part(lo, hi):
+        c, s = ctypes.c_uint64(), ctypes.c_uint64()
+        lib().vxg_probe_truth(hi - lo, row0 + lo, n_build, int(round(match * 1e6)), zipf_s, seed,
+                              SALT["probe"], ctypes.byref(c), ctypes.byref(s))
+        return c.value, s.value
+
+    k = max(1, min(nthreads or NTHREADS, n_probe // (1 << 20) or 1))
+    cuts = [n_probe * i // k for i in range(k + 1)]
+    with ThreadPoolExecutor(k) as ex:
+        parts = list(ex.map(part, cuts[:-1], cuts[1:]))
+    return sum(c for c, _ in parts), sum(s for _, s in parts) % (1 << 64)
 
 
 def join_inputs(n_build, n_probe, match=1.0, zipf_s=0.0, seed=0):

@@ -228,6 +228,8 @@ typedef struct {
   double ms_kernel;        /* summed device time of the chunk kernels (CUDA events) */
   uint64_t kernel_launches;/* kernels launched by the call */
   uint64_t late_chunks;    /* VX_LATE_PER_CHUNK: chunks whose aggregate columns were read by zero-copy */
+  double ms_gather;        /* summed device time of the zero-copy gathers of late chunks (CUDA events;
+                              0 when not timed: graphs, DAG schedule, serving) */
 } vx_query_stats;
 
 /* Result of vx_run_plan / vx_groupby: groups with count > 0 in ascending group

@@ -76,7 +76,7 @@ class vx_query_stats(ctypes.Structure):
                 ("bytes_logical", ctypes.c_uint64), ("late_mask", ctypes.c_uint32),
                 ("overflow_retries", ctypes.c_uint32), ("est_selectivity", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
-                ("late_chunks", ctypes.c_uint64)]
+                ("late_chunks", ctypes.c_uint64), ("ms_gather", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

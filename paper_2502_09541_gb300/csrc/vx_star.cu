@@ -988,13 +988,14 @@ struct StarExKernel : ExKernel {
   // split mode (late roles): survivor list region after the staged columns
   bool any_late = false;
   // per-slot events around the fused kernel (its own duration, immediate schedule)
-  std::vector<cudaEvent_t> ev_a, ev_b;
+  std::vector<cudaEvent_t> ev_a, ev_b, ev_c;  // fused kernel [a, b), gather [b, c)
   std::vector<uint8_t> ev_used;
-  double ms_main = 0;
+  double ms_main = 0, ms_gather = 0;
   uint64_t main_launches = 0, launches = 0;
   ~StarExKernel() override {
     for (auto e : ev_a) cudaEventDestroy(e);
     for (auto e : ev_b) cudaEventDestroy(e);
+    for (auto e : ev_c) cudaEventDestroy(e);
   }
 
   uint64_t size() override { return (n_rows + chunk_rows - 1) / chunk_rows; }
@@ -1014,6 +1015,7 @@ struct StarExKernel : ExKernel {
       ms_main += ms;
       main_launches += 1;
     }
+    if (ev_used[k] == 2 && cudaEventElapsedTime(&ms, ev_b[k], ev_c[k]) == cudaSuccess) ms_gather += ms;
     cudaGetLastError();
     ev_used[k] = 0;
   }
@@ -1065,7 +1067,10 @@ struct StarExKernel : ExKernel {
       }
       VX_CUDA_TRY(cudaGetLastError());
       launches += 2;
-      if (timed) ev_used[ek] = 1;
+      if (timed) {
+        VX_CUDA_TRY(cudaEventRecord(ev_c[ek], s));
+        ev_used[ek] = 2;
+      }
       return VX_OK;
     }
     launches += 1;
@@ -1488,10 +1493,12 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
     const int S = std::max(2, ctx->cfg.n_slots);
     ek.ev_a.resize(S);
     ek.ev_b.resize(S);
+    ek.ev_c.resize(S);
     ek.ev_used.assign(S, 0);
     for (int i = 0; i < S; ++i) {
       VX_CUDA_TRY(cudaEventCreate(&ek.ev_a[i]));
       VX_CUDA_TRY(cudaEventCreate(&ek.ev_b[i]));
+      VX_CUDA_TRY(cudaEventCreate(&ek.ev_c[i]));
     }
   }
   const uint64_t n_chunks = n_rows ? (n_rows + cr - 1) / cr : 0;
@@ -1628,6 +1635,7 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   qs.late_chunks = late_chunks;
   qs.bytes_logical = n_rows * 4ull * role_col.size();
   qs.ms_kernel = ek.main_launches ? ek.ms_main : es.ms_kernel;  // the fused kernel's own time when timed
+  qs.ms_gather = ek.ms_gather;
   qs.kernel_launches = ge ? es.kernel_launches : ek.launches;
   qs.ms_total = now_ms() - t_start;
   out->stats = qs;
