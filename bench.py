@@ -325,6 +325,16 @@ def run_sort_extra(vx, G, args):
                          "ms_train": round(st["ms_train"], 1),
                          "link_gbs": round((st["bytes_h2d"] + st["bytes_d2h"]) / st["ms_total"] / 1e6, 1)}
         out["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
+        # per-partition radix sorts against HBM: 32 algorithmic bytes per pair
+        # and executed pass (8-byte key read by the histogram pass, 12-byte pair
+        # read and written by the scatter), from the last form's device time
+        if st["ms_sort_kernel"] > 0:
+            hbm_peak, peak_kind = measured_peaks()
+            ach = 32 * st["radix_pass_pairs"] / (st["ms_sort_kernel"] * 1e6)
+            out["radix_roofline"] = {"kernel": "rx_upsweep + rx_downsweep", "bound": "hbm", "unit": "GB/s",
+                                     "achieved": round(ach, 1), "peak": hbm_peak, "frac": round(ach / hbm_peak, 4),
+                                     "peak_kind": peak_kind, "pass_pairs": int(st["radix_pass_pairs"]),
+                                     "ms_sort_kernel": round(st["ms_sort_kernel"], 1)}
     finally:
         vx.vx_close(ctx)
     return out
@@ -360,6 +370,18 @@ def run_join_extra(vx, G, args):
                          "overflow_retries": r["overflow_retries"], "ms_build": round(r["ms_build"], 1),
                          "ms_probe": round(r["ms_probe"], 1), "ms_kernel": round(r["ms_kernel"], 1)}
         out["count_ok"] = out["planner"]["count"] == npr
+        # probe kernel against HBM's random-access ceiling, measured in this run
+        # on a table of the planner's size (one random 32-byte bucket read per
+        # probe is the algorithmic minimum; longer walks read more)
+        budget_slots = int(0.98 * ((24 << 30) - (256 << 20)) / 16)
+        table_bytes = 16 * min(budget_slots, 2 * nb)
+        ceiling = vx.vx_probe_hbm_random(ctx, table_bytes, 64 << 20)
+        pr = vx.vx_join(ctx, a, b, p, vx.vx_join_opts())
+        ach = npr / (pr["ms_probe_kernel"] * 1e6)
+        out["probe_roofline"] = {"kernel": "join_probe_kernel", "bound": "hbm_random", "unit": "G reads/s",
+                                 "achieved": round(ach, 2), "peak": round(ceiling, 2), "frac": round(ach / ceiling, 4),
+                                 "table_gb": round(table_bytes / 1e9, 2), "ms_probe_kernel": round(pr["ms_probe_kernel"], 1),
+                                 "peak_kind": "vx_probe_hbm_random in this run"}
         # the other probe distributions of the workload (planner form): match
         # rate 50 % and Zipf(1.0) foreign keys, drawn into the same pinned buffer;
         # count and wrapping payload sum against the truth recorded while drawing

@@ -321,6 +321,8 @@ typedef struct {
   double imbalance;                /* largest partition / mean partition */
   double ms_sample, ms_train, ms_partition, ms_sort, ms_total;
   uint64_t bytes_h2d, bytes_d2h, kernel_launches;
+  double ms_sort_kernel;           /* device time of the per-partition radix sorts (CUDA events) */
+  uint64_t radix_pass_pairs;       /* pairs x executed LSD passes in those sorts (skipped digits excluded) */
 } vx_sort_stats;
 
 /* Out-of-core sort of (uint64 key, uint32 row id) pairs held in two registered
@@ -384,6 +386,8 @@ typedef struct {
   uint32_t n_partitions, overflow_retries;
   uint64_t max_partition, bytes_h2d, kernel_launches;
   double ms_sample, ms_train, ms_build, ms_probe, ms_kernel, ms_total;
+  double ms_probe_kernel;  /* device time of the probe kernels alone (CUDA events); every probe key
+                              is looked up in exactly one partition */
 } vx_join_result;
 
 /* Equi-join of a build table (unique 64-bit keys, 64-bit payload) with a
@@ -468,6 +472,19 @@ vx_status vx_probe_zero_copy(vx_ctx *ctx, uint64_t n, const int32_t *sels, int32
  * context's copy streams and arena, and reports GB/s (1e9 B/s). */
 vx_status vx_probe_link(vx_ctx *ctx, uint64_t bytes, uint64_t chunk, double *h2d_gbs, double *d2h_gbs,
                         double *bidir_gbs);
+
+/* ---------------------------------------------------------------- random-read probe */
+
+/* Random-access ceiling of HBM, the roofline of a hash probe into a table far
+ * larger than L2 (every probe is a random DRAM access; Section 6.2's join
+ * probes such tables).  The paper has no counterpart: it is this library's
+ * denominator for the join probe kernel.  Reads n_reads 16-byte values, one
+ * from each of n_reads pseudo-random 32-byte-aligned buckets of a table of
+ * table_bytes (allocated from the arena, zero-filled), eight independent reads
+ * in flight per thread, and reports the best of three timed runs in 1e9 reads
+ * per second.  VX_E_NOMEM if the table does not fit the arena; VX_E_INVAL for
+ * table_bytes < 32 or n_reads == 0. */
+vx_status vx_probe_hbm_random(vx_ctx *ctx, uint64_t table_bytes, uint64_t n_reads, double *g_reads_per_s);
 
 #ifdef __cplusplus
 }

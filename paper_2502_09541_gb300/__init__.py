@@ -104,7 +104,8 @@ class vx_sort_stats(ctypes.Structure):
                 ("slot_pairs", ctypes.c_uint64), ("imbalance", ctypes.c_double), ("ms_sample", ctypes.c_double),
                 ("ms_train", ctypes.c_double), ("ms_partition", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("bytes_h2d", ctypes.c_uint64), ("bytes_d2h", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64), ("ms_sort_kernel", ctypes.c_double),
+                ("radix_pass_pairs", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -122,7 +123,7 @@ class vx_join_result(ctypes.Structure):
                 ("max_partition", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("ms_sample", ctypes.c_double), ("ms_train", ctypes.c_double),
                 ("ms_build", ctypes.c_double), ("ms_probe", ctypes.c_double), ("ms_kernel", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("ms_probe_kernel", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -160,6 +161,7 @@ SIGNATURES = {
     "vx_last_stats": ([_vp, _P(vx_query_stats)], _i32),
     "vx_drop_resident": ([_vp], _i32),
     "vx_probe_link": ([_vp, _u64, _u64, _P(_dbl), _P(_dbl), _P(_dbl)], _i32),
+    "vx_probe_hbm_random": ([_vp, _u64, _u64, _P(_dbl)], _i32),
     "vx_probe_zero_copy": ([_vp, _u64, _vp, _i32, _vp, _vp, _vp], _i32),
     "vx_sort": ([_vp, _i32, _i32, _vp, _vp, _P(vx_sort_opts), _P(vx_sort_stats)], _i32),
     "vx_radix_sort_pairs": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
@@ -405,6 +407,13 @@ def vx_probe_zero_copy(ctx, n: int, sels):
     ck = np.zeros(len(s), np.uint64)
     _check(load().vx_probe_zero_copy(ctx, n, s.ctypes.data, len(s), zc.ctypes.data, ce.ctypes.data, ck.ctypes.data))
     return zc, ce, ck
+
+
+def vx_probe_hbm_random(ctx, table_bytes: int, n_reads: int) -> float:
+    """1e9 random 16-byte reads per second from 32-byte buckets of a table."""
+    r = _dbl()
+    _check(load().vx_probe_hbm_random(ctx, table_bytes, n_reads, ctypes.byref(r)))
+    return r.value
 
 
 def vx_probe_link(ctx, nbytes: int, chunk: int):

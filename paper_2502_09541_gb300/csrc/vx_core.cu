@@ -431,6 +431,77 @@ VX_API vx_status vx_probe_zero_copy(vx_ctx *ctx, uint64_t n, const int32_t *sels
   return VX_OK;
 }
 
+// ------------------------------------------------------------------ random-read probe
+namespace {
+__device__ __forceinline__ uint64_t rr_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// read i goes to bucket mix(i) mapped onto [0, nbk) by multiply-shift
+__global__ void __launch_bounds__(256) rand_read_kernel(const ulonglong2 *__restrict__ t, uint64_t nbk, uint64_t n,
+                                                        unsigned long long *sink) {
+  constexpr int kR = 8;
+  unsigned long long x = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kR;
+  for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * kR; i < n; i += stride) {
+    ulonglong2 v[kR];
+#pragma unroll
+    for (int j = 0; j < kR; ++j) v[j] = i + j < n ? __ldg(t + 2 * __umul64hi(rr_mix(i + j), nbk)) : make_ulonglong2(0, 0);
+#pragma unroll
+    for (int j = 0; j < kR; ++j) x ^= v[j].x;
+  }
+  if (x == 0x5EEDull) atomicAdd(sink, 1ull);  // keeps the reads live
+}
+}  // namespace
+
+VX_API vx_status vx_probe_hbm_random(vx_ctx *ctx, uint64_t table_bytes, uint64_t n_reads, double *g_reads_per_s) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (table_bytes < 32 || !n_reads || !g_reads_per_s) {
+    set_error("vx_probe_hbm_random: need table_bytes >= 32, n_reads > 0 and an output");
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const uint64_t nbk = table_bytes / 32;
+  DevBuf tb;
+  tb.arena = &ctx->arena;
+  tb.p = ctx->arena.alloc(nbk * 32 + 256);
+  if (!tb.p) {
+    set_error("vx_probe_hbm_random: %llu bytes do not fit the arena", (unsigned long long)table_bytes);
+    return VX_E_NOMEM;
+  }
+  unsigned long long *sink = (unsigned long long *)(tb.as<char>() + nbk * 32);
+  cudaStream_t s = ctx->s_compute;
+  VX_CUDA_TRY(cudaMemsetAsync(tb.p, 0, nbk * 32 + 256, s));
+  int occ = 0;
+  VX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rand_read_kernel, 256, 0));
+  const int grid = std::max(1, occ) * ctx->num_sms;
+  cudaEvent_t e0, e1;
+  VX_CUDA_TRY(cudaEventCreate(&e0));
+  VX_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 0;
+  for (int it = 0; it < 4; ++it) {  // the first run warms up
+    cudaEventRecord(e0, s);
+    rand_read_kernel<<<grid, 256, 0, s>>>(tb.as<ulonglong2>(), nbk, n_reads, sink);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (it && (best == 0 || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) {
+    set_error("vx_probe_hbm_random: %s", cudaGetErrorString(le));
+    return VX_E_CUDA;
+  }
+  *g_reads_per_s = best > 0 ? (double)n_reads / (best * 1e6) : 0.0;
+  return VX_OK;
+}
+
 // ------------------------------------------------------------------ link probe
 VX_API vx_status vx_probe_link(vx_ctx *ctx, uint64_t bytes, uint64_t chunk, double *h2d, double *d2h,
                                double *bidir) {

@@ -451,6 +451,7 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
       res.kernel_launches += ep.kernel_launches;
       res.ms_probe += now_ms() - tp0;
       res.ms_kernel += es.ms_kernel + ep.ms_kernel;
+      res.ms_probe_kernel += ep.ms_kernel;
       break;
     }
   }

@@ -282,7 +282,13 @@ static vx_status rx_scatter_attr() {
   return VX_OK;
 }
 
-__global__ void rx_publish(const RadixState *st, int pass, uint64_t *host_word) { *host_word = (uint64_t)st->cur[pass]; }
+// publishes the buffer holding the result (low byte) and the number of
+// executed (not skipped) passes (next byte) to a mapped host word
+__global__ void rx_publish(const RadixState *st, int pass, uint64_t *host_word) {
+  uint64_t executed = 0;
+  for (int p = 0; p < pass; ++p) executed += st->skip[p] ? 0u : 1u;
+  *host_word = (uint64_t)st->cur[pass] | executed << 8;
+}
 
 // ---- sampling and splitters -----------------------------------------------
 
@@ -603,6 +609,7 @@ struct SortPass : ExKernel {
   uint64_t *out_keys;
   uint32_t *out_vals;
   int S;
+  uint64_t pass_pairs = 0;  // pairs x executed passes
 
   uint64_t size() override { return job_n.size(); }
   uint64_t kb() const { return (8 * cap + 255) & ~255ull; }
@@ -636,7 +643,9 @@ struct SortPass : ExKernel {
   bool has_outputs() override { return true; }
   vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
     RadixBufs b = bufs(slot);
-    int c = (int)((volatile uint64_t *)ctx->h_scalars)[64 + (it % S)];
+    const uint64_t word = ((volatile uint64_t *)ctx->h_scalars)[64 + (it % S)];
+    const int c = (int)(word & 0xFF);
+    pass_pairs += job_n[it] * ((word >> 8) & 0xFF);
     if (job_n[it] == 0) return VX_OK;
     d2h.push_back({b.keys[c], out_keys + job_off[it], 8 * job_n[it]});
     d2h.push_back({b.vals[c], out_vals + job_off[it], 4 * job_n[it]});
@@ -680,6 +689,8 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     ss.bytes_h2d += es.bytes_h2d;
     ss.bytes_d2h += es.bytes_d2h;
     ss.kernel_launches += es.kernel_launches;
+    ss.ms_sort_kernel += es.ms_kernel;
+    ss.radix_pass_pairs += sp.pass_pairs;
     ss.n_partitions = std::max<uint32_t>(ss.n_partitions, 1);
     ss.max_partition = std::max(ss.max_partition, n);
     ss.ms_sort += now_ms() - t0;
@@ -818,6 +829,8 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     ss.bytes_h2d += es.bytes_h2d;
     ss.bytes_d2h += es.bytes_d2h;
     ss.kernel_launches += es.kernel_launches * 35;  // byte histogram, state, 8 x 4 passes, publish
+    ss.ms_sort_kernel += es.ms_kernel;
+    ss.radix_pass_pairs += sp.pass_pairs;
   }
   for (uint32_t p : big) {
     const uint64_t lo = p == 0 ? 0 : spl[p - 1];

@@ -37,3 +37,13 @@ def test_zero_copy_crossover(ctx):
     # granule; neighbours sharing granules move the measured crossover lower.
     cross = next(s for s, a, b in zip(sels, zc, ce) if a < 0.9 * b)
     assert 2 <= cross <= 32, (cross, zc.tolist(), ce.tolist())
+
+
+def test_hbm_random_read_probe(ctx):
+    # a 256 MiB table (twice L2): random 32-byte buckets, then the arena limit
+    g = vx.vx_probe_hbm_random(ctx, 256 << 20, 16 << 20)
+    assert 1.0 < g < 500.0
+    with pytest.raises(vx.VxError):
+        vx.vx_probe_hbm_random(ctx, 4 << 30, 1 << 20)
+    with pytest.raises(vx.VxError):
+        vx.vx_probe_hbm_random(ctx, 16, 1 << 20)
