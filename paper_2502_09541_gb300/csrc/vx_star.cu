@@ -288,11 +288,8 @@ __device__ __forceinline__ int32_t slot_val(const int4 (&vals)[kR], int slot, in
 // then predicates, probes (direct map or hash, all 4 rows' lookups in flight)
 // and the group id are computed from registers.  Survivors are aggregated
 // (kSplit = false) or appended to the block's survivor list.
-template <bool kSmem, bool kSplit, int kR, int kV>
-__device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, unsigned long long *ssum,
-                                           unsigned long long *scnt, unsigned long long &surv, SurvTile *st) {
-  constexpr int kN = 4 * kV;  // rows of this thread
-  int4 vals[kV][kR];
+template <int kR, int kV>
+__device__ __forceinline__ void star_load4(const ChunkParams &p, uint64_t r0, int4 (&vals)[kV][kR]) {
 #pragma unroll
   for (int v = 0; v < kV; ++v) {
     const uint64_t rv = r0 + (uint64_t)v * kVecTileRows;
@@ -310,6 +307,13 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, un
       }
     }
   }
+}
+
+template <bool kSmem, bool kSplit, int kR, int kV>
+__device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, const int4 (&vals)[kV][kR],
+                                           unsigned long long *ssum, unsigned long long *scnt,
+                                           unsigned long long &surv, SurvTile *st) {
+  constexpr int kN = 4 * kV;  // rows of this thread
   bool alive[kN];
   uint32_t g[kN];
 #pragma unroll
@@ -417,12 +421,19 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, un
 }
 
 
+// prefetching resident grid (see star_vec_kernel); measured slower (64-116
+// registers, fewer resident blocks), so one block per tile
+constexpr bool kVecPrefetch = false;
+
 // groups of 4 rows per thread: a block tile is kVecGroups x kVecTileRows rows
 constexpr int kVecGroups = 1;  // 2 raises registers to 62-128 and measured slower
 static_assert(kVecGroups * kVecTileRows <= kStarTileRows, "a block tile's survivors must fit its list");
 
 // Vector path kernel over whole block tiles of kVecGroups x kVecTileRows rows.
-template <bool kSmem, bool kSplit, int kR>
+// kPrefetch = false: one block per tile (the hardware keeps as many resident as
+// registers allow); true: a resident grid whose threads load the next tile's
+// columns before evaluating the current one
+template <bool kSmem, bool kSplit, int kR, bool kPrefetch>
 __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   extern __shared__ unsigned long long sacc[];  // [2 * n_groups] when kSmem
   __shared__ SurvTile st;
@@ -434,8 +445,23 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   __syncthreads();
   unsigned long long surv = 0;
   constexpr uint64_t kTile = (uint64_t)kVecGroups * kVecTileRows;
-  for (uint64_t t0 = (uint64_t)blockIdx.x * kTile; t0 < p.n; t0 += (uint64_t)gridDim.x * kTile) {
-    star_rows4<kSmem, kSplit, kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, ssum, scnt, surv, &st);
+  const uint64_t stride = (uint64_t)gridDim.x * kTile;
+  uint64_t t0 = (uint64_t)blockIdx.x * kTile;
+  int4 cur[kVecGroups][kR], nxt[kVecGroups][kR];
+  if (kPrefetch && t0 < p.n) star_load4<kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, cur);
+  for (; t0 < p.n; t0 += stride) {
+    if (kPrefetch) {  // the next tile's columns are in flight while this one is evaluated
+      if (t0 + stride < p.n) star_load4<kR, kVecGroups>(p, t0 + stride + 4ull * threadIdx.x, nxt);
+    } else {
+      star_load4<kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, cur);
+    }
+    star_rows4<kSmem, kSplit, kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, cur, ssum, scnt, surv, &st);
+    if (kPrefetch) {
+#pragma unroll
+      for (int v = 0; v < kVecGroups; ++v)
+#pragma unroll
+        for (int k = 0; k < kR; ++k) cur[v][k] = nxt[v][k];
+    }
     if (kSplit) {
       __syncthreads();
       const unsigned int n = st.n;
@@ -464,13 +490,42 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   }
 }
 
+template <bool kSmem, bool kSplit, int kR>
+static int vec_resident(size_t smem) {
+  // resident blocks per SM of one instantiation at a dynamic shared-memory size
+  static std::mutex mu;
+  static std::map<size_t, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(smem);
+  if (it != cache.end()) return it->second;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, star_vec_kernel<kSmem, kSplit, kR, kVecPrefetch>, 256,
+                                                    smem) != cudaSuccess || occ < 1)
+    occ = 1;
+  cudaGetLastError();
+  cache[smem] = occ;
+  return occ;
+}
+
+// tiles of n rows; a resident grid when the blocks prefetch their next tile
+template <bool kSmem, bool kSplit, int kR>
+static void launch_vec_w(const vx_ctx *ctx, const ChunkParams &p, uint64_t n, size_t smem, cudaStream_t s) {
+  uint64_t grid = (n + kVecGroups * kVecTileRows - 1) / (kVecGroups * kVecTileRows);
+  // group accumulators in shared memory also want a resident grid: each block
+  // then merges its groups into global memory once per chunk, not once per tile
+  if (kVecPrefetch || kSmem)
+    grid = std::min<uint64_t>(grid, (uint64_t)ctx->num_sms * vec_resident<kSmem, kSplit, kR>(smem));
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, 1u << 30));
+  star_vec_kernel<kSmem, kSplit, kR, kVecPrefetch><<<(unsigned)grid, 256, smem, s>>>(p);
+}
+
 template <bool kSmem, bool kSplit>
-static void launch_vec(const ChunkParams &p, int kr, int grid, size_t smem, cudaStream_t s) {
+static void launch_vec(const vx_ctx *ctx, const ChunkParams &p, int kr, size_t smem, cudaStream_t s) {
   switch (kr) {
-    case 2: star_vec_kernel<kSmem, kSplit, 2><<<grid, 256, smem, s>>>(p); break;
-    case 4: star_vec_kernel<kSmem, kSplit, 4><<<grid, 256, smem, s>>>(p); break;
-    case 6: star_vec_kernel<kSmem, kSplit, 6><<<grid, 256, smem, s>>>(p); break;
-    default: star_vec_kernel<kSmem, kSplit, 8><<<grid, 256, smem, s>>>(p); break;
+    case 2: launch_vec_w<kSmem, kSplit, 2>(ctx, p, p.n, smem, s); break;
+    case 4: launch_vec_w<kSmem, kSplit, 4>(ctx, p, p.n, smem, s); break;
+    case 6: launch_vec_w<kSmem, kSplit, 6>(ctx, p, p.n, smem, s); break;
+    default: launch_vec_w<kSmem, kSplit, 8>(ctx, p, p.n, smem, s); break;
   }
 }
 
@@ -478,20 +533,13 @@ template <bool kSmem, bool kSplit>
 static vx_status vec_attr(size_t smem) {
   static bool done = false;
   if (!done && smem > 0) {
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 2, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 4, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 6, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 8, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
     done = true;
   }
   return VX_OK;
-}
-
-// one block per tile: the hardware keeps as many resident as registers allow
-// and starts the next as soon as one finishes
-static int vec_grid(uint64_t n) {
-  const uint64_t t = (n + kVecGroups * kVecTileRows - 1) / (kVecGroups * kVecTileRows);
-  return (int)std::max<uint64_t>(1, std::min<uint64_t>(t, 1u << 30));
 }
 
 // width (2, 4, 6 or 8 loaded columns) of the vector path for a chunk, or 0
@@ -1047,7 +1095,7 @@ struct StarExKernel : ExKernel {
       if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
       const int kr = vec_width(p);
       if (kr) {
-        launch_vec<false, true>(p, kr, vec_grid(p.n), 0, s);
+        launch_vec<false, true>(ctx, p, kr, 0, s);
       } else {
         const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
         star_split_kernel<<<gs, 256, 0, s>>>(p);
@@ -1077,15 +1125,11 @@ struct StarExKernel : ExKernel {
     if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
     const int kr = vec_width(p);
     if (kr) {  // vector path
-      int gv = vec_grid(p.n);
       if (smem) {
-        // group accumulators in shared memory: a resident grid, so that each
-        // block merges its groups into global memory once per chunk, not once per tile
-        gv = std::min<int>(gv, ctx->num_sms * ctx->cfg.blocks_per_sm);
         VX_TRY((vec_attr<true, false>(smem_bytes)));
-        launch_vec<true, false>(p, kr, gv, smem_bytes, s);
+        launch_vec<true, false>(ctx, p, kr, smem_bytes, s);
       } else {
-        launch_vec<false, false>(p, kr, gv, 0, s);
+        launch_vec<false, false>(ctx, p, kr, 0, s);
       }
     } else if (smem) {
       static bool attr_set = false;
