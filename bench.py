@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--workload", default="star", choices=["star", "sort", "join", "serve"],
                     help="star: the full benchmark line; sort / join / serve: that part alone")
     ap.add_argument("--serve-plain-queries", type=int, default=100)
+    ap.add_argument("--clustered-rows", type=int, default=300_000_000,
+                    help="date-clustered fact table of the per-chunk materialization comparison (0: skip)")
     return ap.parse_args()
 
 
@@ -274,6 +276,51 @@ def run_serving(vx, G, ctx, fid, did, args):
                         "p99_ms": round(float(np_.percentile(lat, 99)), 3), "mean_ms": round(float(np_.mean(lat)), 3),
                         "qps": round(k / wall, 2), "host_gbs": round(sum(logical_of[:k]) / wall / 1e9, 3),
                         "form": "one query at a time, first come first served (same arrivals)"}
+    return out
+
+
+# a star query whose qualifying years sit in the last chunks of a table
+# appended in date order (fact rows' date_fk ascends with the row)
+CLUSTER_T = {
+    "dims": [{"dim": "cust", "fk": "fk_cust", "preds": [("nation", 0, 11)]},
+             {"dim": "date", "fk": "date_fk", "preds": [("year", 5, 6)]}],
+    "fact_preds": [("discount", 0, 2)],
+    "group": [("date", "year"), ("cust", "nation")],
+    "agg": ("sub", "price", "cost"),
+}
+
+
+def run_clustered(vx, G, ctx, did, args):
+    """Late/early materialization decided per chunk by the regressor (learned)
+    against one decision per plan (plain) on a date-clustered fact table: the
+    survivors crowd into the last chunks, where staging the payload columns
+    beats reading them by zero-copy.  Same executor configuration for both;
+    results compared equal."""
+    import numpy as np
+    n = args.clustered_rows
+    clu = G.star_fact(n, seed=6, clustered_date=True,
+                      out={c: pinned_array(n, np.int32) for c in G.STAR_FACT_COLS})
+    fc = {k: vx.vx_register_host_column(ctx, "clustered." + k, clu[k]) for k in clu}
+    plans = {"plain": vx.make_plan(CLUSTER_T, fc, did, G.STAR_ATTR_CARD, vx.VX_LATE_AUTO),
+             "learned": vx.make_plan(CLUSTER_T, fc, did, G.STAR_ATTR_CARD, vx.VX_LATE_PER_CHUNK)}
+    res, out = {}, {"rows": n, "template": "cust.nation<=11, date.year in [5,6], discount in [0,2]"}
+    for _ in range(2):  # warm-up: dimension tables resident, host pages touched
+        for pl in plans.values():
+            vx.vx_run_plan(ctx, pl)
+    times = {k: [] for k in plans}
+    for _ in range(3):
+        for k, pl in plans.items():
+            st, gid, sm, cnt, stats = vx.vx_run_plan(ctx, pl)
+            assert st == vx.VX_OK
+            times[k].append(stats)
+            res[k] = (gid, sm, cnt)
+    for k, ss in times.items():
+        ms = statistics.median(x["ms_total"] for x in ss)
+        x = ss[-1]
+        out[k] = {"gbs": round(x["bytes_logical"] / (ms * 1e6), 1), "ms": round(ms, 2),
+                  "link_bytes": int(x["bytes_h2d"] + x["bytes_zero_copy"]), "late_chunks": int(x["late_chunks"]),
+                  "chunks": int(x["chunks"]), "late_mask": int(x["late_mask"])}
+    out["equal"] = all(np.array_equal(a, b) for a, b in zip(res["plain"], res["learned"]))
     return out
 
 
@@ -560,6 +607,7 @@ def run_ours(args):
     e2e_gbs = logical * world / (e2e_s * 1e9)
 
     serving = run_serving(vx, G, ctx, fid, did, args) if not args.no_extras else None
+    clustered = run_clustered(vx, G, ctx, did, args) if not args.no_extras and args.clustered_rows else None
 
     line = {
         "metric": METRIC, "value": round(host_gbs, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -586,6 +634,8 @@ def run_ours(args):
     }
     if serving:
         line["serving"] = serving
+    if clustered:
+        line["clustered"] = clustered
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = args.cpu_sample_rows or min(args.rows, 20_000_000)
         v, cores, dt = cpu_baseline(fact, dims, sample)
