@@ -4,12 +4,17 @@
 // partition (digit = one key byte; Section 6.1 sorts chunks with a radix sort
 // over a double buffer).
 //
-// One pass = upsweep (per-tile digit histograms) -> row scan (per digit,
-// exclusive over tiles) -> totals scan (exclusive over digits: the boundary
-// array of Section 6.2.1) -> downsweep (stable scatter).  Ranking inside a tile
-// is warp-contiguous: warp w owns 512 consecutive pairs and processes them in
-// 16 rounds of 32; __match_any_sync groups equal digits of a round, so pairs
-// keep their input order (stability).  No pass waits on another block.
+// Range partition = upsweep (per-tile digit histograms) -> row scan (per
+// digit, exclusive over tiles) -> totals scan (exclusive over digits: the
+// boundary array of Section 6.2.1) -> downsweep (stable scatter).  An LSD sort
+// pass is one scatter kernel: the global digit offsets of all eight passes
+// come from one histogram read of the keys, and each tile finds the count of
+// its digits in the tiles before it by decoupled look-back (tiles take
+// tickets in launch order, publish their counts, then their inclusive
+// prefixes; every wait is bounded and sets the error word when it gives up).
+// Ranking inside a tile is warp-contiguous: warp w owns 512 consecutive pairs
+// and processes them in 16 rounds of 32; __match_any_sync groups equal digits
+// of a round, so pairs keep their input order (stability).
 //
 // Double buffer: `cur[pass]` (device) says which of (A, B) holds the input of
 // LSD pass `pass`; a pass whose digit is constant over all pairs is skipped on
@@ -32,10 +37,12 @@ struct RadixBufs {
   uint32_t *vals[2];
 };
 
-// per-pass device state: cur[0..8], skip[0..7], totals[256], base[257]
+// per-pass device state: cur[0..8], skip[0..7], an error word (a look-back
+// wait that gave up), totals[256], base[257]
 struct RadixState {
   int32_t cur[12];
   int32_t skip[12];
+  uint32_t err, pad;
   uint64_t totals[kRxDigits];
   uint64_t base[kRxDigits + 1];
 };

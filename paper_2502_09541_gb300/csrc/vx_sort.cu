@@ -16,6 +16,7 @@
 // are already in input order and are copied through; a multi-key partition
 // above the slot capacity is sorted recursively.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <thread>
 
@@ -161,7 +162,10 @@ __global__ void __launch_bounds__(kRxThreads) rx_byte_hist(const RadixBufs b, ui
 
 __global__ void rx_init_state(RadixState *st, const unsigned long long *bh, uint64_t n) {
   const int p = threadIdx.x;  // 8 threads
-  if (p == 0) st->cur[0] = 0;
+  if (p == 0) {
+    st->cur[0] = 0;
+    st->err = 0;
+  }
   if (p < 8) {
     int full = 0;
     for (int d = 0; d < kRxDigits; ++d) full |= bh[p * kRxDigits + d] == n;
@@ -181,29 +185,70 @@ struct RxScatterSmem {
   uint8_t d[kRxTile];
 };
 
+// One-sweep LSD passes: per-(tile, digit) status words carry a flag (0 not
+// ready, 1 the tile's own count, 2 the inclusive prefix over tiles 0..t), the
+// pass number (so one clearing serves all eight passes) and the value.
+constexpr uint64_t kRxFlagAgg = 1ull << 62, kRxFlagIncl = 2ull << 62;
+constexpr uint64_t kRxValueMask = (1ull << 59) - 1;
+constexpr uint32_t kRxSpinLimit = 1u << 20;  // polls of one predecessor word before giving up
+
+__device__ __forceinline__ uint64_t rx_status_word(uint64_t flag, int pass, uint64_t value) {
+  return flag | (uint64_t)pass << 59 | value;
+}
+
+// 8 blocks x 256 threads: exclusive scan of each digit histogram = the global
+// position of each digit's first pair in every LSD pass
+__global__ void __launch_bounds__(kRxDigits) rx_init_bases(const unsigned long long *bh, uint64_t *bases) {
+  __shared__ uint64_t s[kRxDigits];
+  const int p = blockIdx.x, d = threadIdx.x;
+  const uint64_t t = bh[p * kRxDigits + d];
+  s[d] = t;
+  __syncthreads();
+  for (int off = 1; off < kRxDigits; off <<= 1) {
+    const uint64_t y = d >= off ? s[d - off] : 0;
+    __syncthreads();
+    s[d] += y;
+    __syncthreads();
+  }
+  bases[p * kRxDigits + d] = s[d] - t;
+}
+
 // Stable scatter of one tile: rank every pair inside its warp (match_any over
 // 16 rounds of 32 consecutive pairs), regroup the tile by digit in shared
 // memory, then write each digit's run with consecutive threads on consecutive
 // output positions, so stores leave the SM as contiguous runs.
-template <bool kRange>
-__global__ void __launch_bounds__(kRxThreads, 2) rx_downsweep(RadixBufs b, const RadixState *st, int pass, uint64_t n,
+// kOneSweep (LSD passes): the tile is the block's ticket, and its digit offsets
+// come from the one-read histogram (bases) plus a look-back over the status
+// words of the tiles before it; otherwise the tile is blockIdx.x and its
+// offsets come from the scanned per-tile histograms.
+template <bool kRange, bool kOneSweep>
+__global__ void __launch_bounds__(kRxThreads, 2) rx_downsweep(RadixBufs b, RadixState *st, int pass, uint64_t n,
                                                               int shift, const uint64_t *spl, int n_spl,
-                                                              const uint32_t *hist, uint32_t ntiles) {
-  if (!kRange && st->skip[pass]) return;
+                                                              const uint32_t *hist, uint32_t ntiles,
+                                                              const uint64_t *bases, unsigned int *tickets,
+                                                              unsigned long long *status) {
+  if (!kRange && st->skip[pass]) {
+    if (kOneSweep && blockIdx.x == 0 && threadIdx.x == 0) st->cur[pass + 1] = st->cur[pass];
+    return;
+  }
   extern __shared__ __align__(16) unsigned char rx_smem[];
   RxScatterSmem &sm = *reinterpret_cast<RxScatterSmem *>(rx_smem);
   __shared__ uint64_t s_spl[kRxDigits];
+  __shared__ uint32_t s_tile;
   const int c = kRange ? 0 : st->cur[pass];
   const uint64_t *kin = b.keys[c];
   const uint32_t *vin = b.vals[c];
   uint64_t *kout = b.keys[1 - c];
   uint32_t *vout = b.vals[1 - c];
+  if (kOneSweep && threadIdx.x == 0) s_tile = atomicAdd(&tickets[pass], 1u);
   for (int i = threadIdx.x; i < kRxWarps * kRxDigits; i += blockDim.x) (&sm.wcnt[0][0])[i] = 0;
   if (kRange)
     for (int i = threadIdx.x; i < n_spl; i += blockDim.x) s_spl[i] = spl[i];
   __syncthreads();
+  const uint32_t tile = kOneSweep ? s_tile : blockIdx.x;
+  if (kOneSweep && tile == 0 && threadIdx.x == 0) st->cur[pass + 1] = 1 - c;  // read by the next pass only
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint64_t tbase = (uint64_t)blockIdx.x * kRxTile;
+  const uint64_t tbase = (uint64_t)tile * kRxTile;
   const uint64_t wbase = tbase + (uint64_t)w * (32 * kRxItems);
   uint64_t k[kRxItems];
   uint32_t v[kRxItems], dr[kRxItems];  // dr = rank inside the warp << 9 | digit
@@ -235,6 +280,37 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_downsweep(RadixBufs b, const
       sm.wcnt[q][d] = run;
       run += cq;
     }
+    uint64_t before_tile;  // position of the tile's first pair of digit d
+    if (kOneSweep) {
+      volatile unsigned long long *sw = status + (uint64_t)tile * kRxDigits + d;
+      *sw = rx_status_word(tile == 0 ? kRxFlagIncl : kRxFlagAgg, pass, run);
+      uint64_t prefix = 0;  // pairs of digit d in the tiles before this one
+      for (uint32_t t = tile; t > 0;) {  // look back over the predecessors' words
+        --t;
+        const volatile unsigned long long *pw = status + (uint64_t)t * kRxDigits + d;
+        uint64_t word = *pw;
+        uint32_t spins = 0;
+        while ((word >> 62) == 0 || (int)((word >> 59) & 7u) != pass) {
+          // give up after the limit, or at once when another tile already gave up
+          if (++spins > kRxSpinLimit || ((spins & 1023u) == 0 && *(volatile uint32_t *)&st->err)) {
+            spins = kRxSpinLimit + 1;
+            break;
+          }
+          __nanosleep(32);
+          word = *pw;
+        }
+        if (spins > kRxSpinLimit) {  // a predecessor never published: report, keep going
+          atomicOr(&st->err, 1u);
+          break;
+        }
+        prefix += word & kRxValueMask;
+        if ((word >> 62) == 2) break;
+      }
+      if (tile > 0) *sw = rx_status_word(kRxFlagIncl, pass, prefix + run);
+      before_tile = bases[pass * kRxDigits + d] + prefix;
+    } else {
+      before_tile = st->base[d] + hist[(uint64_t)d * ntiles + tile];
+    }
     uint32_t x = run;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -248,7 +324,7 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_downsweep(RadixBufs b, const
     for (int q = 0; q < kRxWarps; ++q) wpre += q < (int)w ? sm.wsum[q] : 0u;
     const uint32_t excl = wpre + x - run;
     sm.tstart[d] = excl;
-    sm.off[d] = st->base[d] + hist[(uint64_t)d * ntiles + blockIdx.x] - excl;  // wraps back when added to a position
+    sm.off[d] = before_tile - excl;  // wraps back when added to a position
   }
   __syncthreads();
 #pragma unroll
@@ -275,19 +351,22 @@ constexpr size_t kRxScatterSmem = sizeof(RxScatterSmem);
 static vx_status rx_scatter_attr() {
   static bool done = false;
   if (!done) {
-    VX_CUDA_TRY(cudaFuncSetAttribute(rx_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRxScatterSmem));
-    VX_CUDA_TRY(cudaFuncSetAttribute(rx_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRxScatterSmem));
+    VX_CUDA_TRY(cudaFuncSetAttribute(rx_downsweep<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRxScatterSmem));
+    VX_CUDA_TRY(cudaFuncSetAttribute(rx_downsweep<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRxScatterSmem));
     done = true;
   }
   return VX_OK;
 }
 
-// publishes the buffer holding the result (low byte) and the number of
-// executed (not skipped) passes (next byte) to a mapped host word
+// publishes the buffer holding the result (low byte), the number of
+// executed (not skipped) passes (next byte) and the error word (bit 16) to a
+// mapped host word
 __global__ void rx_publish(const RadixState *st, int pass, uint64_t *host_word) {
   uint64_t executed = 0;
   for (int p = 0; p < pass; ++p) executed += st->skip[p] ? 0u : 1u;
-  *host_word = (uint64_t)st->cur[pass] | executed << 8;
+  *host_word = (uint64_t)st->cur[pass] | executed << 8 | (uint64_t)(st->err != 0) << 16;
 }
 
 // ---- sampling and splitters -----------------------------------------------
@@ -375,15 +454,35 @@ __global__ void isolate_splitters_kernel(const uint64_t *raw, uint32_t n_raw, co
 
 static uint32_t ntiles_of(uint64_t n) { return (uint32_t)((n + kRxTile - 1) / kRxTile); }
 
-// temp layout: [RadixState | 8 byte histograms (u64) | per-tile histograms]
+// temp layout: [RadixState | 8 byte histograms (u64) | per-tile region]; the
+// per-tile region holds the range partition's per-tile histograms (u32), or
+// for an LSD sort the 8 digit bases (u64), 8 tickets and the look-back status
+// words (u64 per tile and digit)
 constexpr uint64_t kStateBytes = (sizeof(RadixState) + 255) & ~255ull;
 constexpr uint64_t kByteHistBytes = 8ull * kRxDigits * 8;
+constexpr uint64_t kBasesBytes = 8ull * kRxDigits * 8;
+constexpr uint64_t kTicketBytes = 256;
 
 uint64_t radix_temp_bytes(uint64_t cap) {
-  return kStateBytes + kByteHistBytes + (uint64_t)kRxDigits * std::max<uint32_t>(ntiles_of(cap), 1) * 4 + 256;
+  const uint64_t nt = std::max<uint32_t>(ntiles_of(cap), 1);
+  return kStateBytes + kByteHistBytes + kBasesBytes + kTicketBytes + (uint64_t)kRxDigits * nt * 8 + 256;
 }
 
 RadixState *radix_state_of(char *temp) { return (RadixState *)temp; }
+
+// after a radix sort on s: the buffer holding the result, or VX_E_TIMEOUT when
+// a look-back wait gave up
+static vx_status radix_result(char *temp, cudaStream_t s, int *cur) {
+  RadixState h;
+  VX_CUDA_TRY(cudaMemcpyAsync(&h, radix_state_of(temp), offsetof(RadixState, totals), cudaMemcpyDeviceToHost, s));
+  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.err) {
+    set_error("radix sort: a look-back wait gave up");
+    return VX_E_TIMEOUT;
+  }
+  *cur = h.cur[8];
+  return VX_OK;
+}
 
 // Enqueues a stable LSD radix sort of b.keys[0]/b.vals[0] (n pairs) on s.
 // The sorted pairs end in buffer st->cur[8] (0 or 1).
@@ -398,16 +497,18 @@ vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s
     return VX_OK;
   }
   VX_TRY(rx_scatter_attr());
+  uint64_t *bases = (uint64_t *)hist;
+  unsigned int *tickets = (unsigned int *)((char *)hist + kBasesBytes);
+  unsigned long long *status = (unsigned long long *)((char *)hist + kBasesBytes + kTicketBytes);
+  // tickets and status words: cleared once, the words carry their pass number
+  VX_CUDA_TRY(cudaMemsetAsync(tickets, 0, kTicketBytes + (uint64_t)kRxDigits * nt * 8, s));
   int g = (int)std::min<uint64_t>((n + kRxThreads - 1) / kRxThreads, (uint64_t)num_sms * 4);
   rx_byte_hist<<<g, kRxThreads, 0, s>>>(b, n, bh);
   rx_init_state<<<1, 32, 0, s>>>(st, bh, n);
-  for (int pass = 0; pass < 8; ++pass) {
-    // skipped passes return at once in every kernel
-    rx_upsweep<false><<<nt, kRxThreads, 0, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, hist, nt);
-    rx_scan_rows<<<kRxDigits, 1024, 0, s>>>(hist, nt, st, pass, true);
-    rx_scan_totals<<<1, kRxDigits, 0, s>>>(st, pass, n, true);
-    rx_downsweep<false><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, hist, nt);
-  }
+  rx_init_bases<<<8, kRxDigits, 0, s>>>(bh, bases);
+  for (int pass = 0; pass < 8; ++pass)  // a skipped pass returns at once and keeps the buffer
+    rx_downsweep<false, true><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, nullptr, nt,
+                                                                      bases, tickets, status);
   VX_CUDA_TRY(cudaGetLastError());
   return VX_OK;
 }
@@ -427,7 +528,9 @@ vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, 
     rx_scan_rows<<<kRxDigits, 1024, 0, s>>>(hist, nt, st, 0, false);
   }
   rx_scan_totals<<<1, kRxDigits, 0, s>>>(st, 0, n, false);
-  if (n) rx_downsweep<true><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, 0, n, 0, spl, (int)P - 1, hist, nt);
+  if (n)
+    rx_downsweep<true, false><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, 0, n, 0, spl, (int)P - 1, hist, nt,
+                                                                      nullptr, nullptr, nullptr);
   VX_CUDA_TRY(cudaGetLastError());
   return VX_OK;
 }
@@ -496,9 +599,7 @@ vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uin
   VX_CUDA_TRY(cudaGetLastError());
   VX_TRY(radix_sort_enqueue(b, m, temp, s, ctx->num_sms));
   int cur = 0;
-  RadixState *st = radix_state_of(temp);
-  VX_CUDA_TRY(cudaMemcpyAsync(&cur, &st->cur[8], 4, cudaMemcpyDeviceToHost, s));
-  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  VX_TRY(radix_result(temp, s, &cur));
   *sorted_ptr = b.keys[cur];
   return VX_OK;
 }
@@ -644,6 +745,10 @@ struct SortPass : ExKernel {
   vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
     RadixBufs b = bufs(slot);
     const uint64_t word = ((volatile uint64_t *)ctx->h_scalars)[64 + (it % S)];
+    if (word >> 16 & 1) {
+      set_error("radix sort of partition job %llu: a look-back wait gave up", (unsigned long long)it);
+      return VX_E_TIMEOUT;
+    }
     const int c = (int)(word & 0xFF);
     pass_pairs += job_n[it] * ((word >> 8) & 0xFF);
     if (job_n[it] == 0) return VX_OK;
@@ -661,7 +766,7 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
   const int S = std::max(2, ctx->cfg.n_slots);
   const uint64_t avail = ctx->arena.largest_free();
   // pairs per slot: (2 x 12 B + histograms) per pair, S slots
-  uint64_t cap = (uint64_t)((double)avail / (S * (24.0 + 256.0 * 4 / kRxTile)) * 0.97);
+  uint64_t cap = (uint64_t)((double)avail / (S * (24.0 + 256.0 * 8 / kRxTile)) * 0.97);
   cap = cap / kRxTile * kRxTile;
   if (o.max_slot_pairs) cap = std::min<uint64_t>(cap, o.max_slot_pairs / kRxTile * kRxTile);
   if (cap < kRxTile) {
@@ -941,8 +1046,7 @@ VX_API vx_status vx_radix_sort_pairs(vx_ctx *ctx, const uint64_t *keys, const ui
   VX_CUDA_TRY(cudaMemcpyAsync(b.vals[0], vals, 4 * n, cudaMemcpyHostToDevice, s));
   VX_TRY(radix_sort_enqueue(b, n, temp, s, ctx->num_sms));
   int cur = 0;
-  VX_CUDA_TRY(cudaMemcpyAsync(&cur, &radix_state_of(temp)->cur[8], 4, cudaMemcpyDeviceToHost, s));
-  VX_CUDA_TRY(cudaStreamSynchronize(s));
+  VX_TRY(radix_result(temp, s, &cur));
   VX_CUDA_TRY(cudaMemcpyAsync(out_keys, b.keys[cur], 8 * n, cudaMemcpyDeviceToHost, s));
   VX_CUDA_TRY(cudaMemcpyAsync(out_vals, b.vals[cur], 4 * n, cudaMemcpyDeviceToHost, s));
   VX_CUDA_TRY(cudaStreamSynchronize(s));
