@@ -364,8 +364,12 @@ def run_sort_extra(vx, G, args):
             o.host_scratch = scratch.ctypes.data
             o.host_scratch_bytes = scratch.nbytes
             o.sample_size = 1 << 20
-            st = vx.vx_sort(ctx, kc, rc, ok, orr, o)
+            # two runs per form, the faster reported (single runs of a form
+            # have come out up to 35 % slow on some boxes, whichever form ran)
+            runs = [vx.vx_sort(ctx, kc, rc, ok, orr, o) for _ in range(2)]
+            st = min(runs, key=lambda r: r["ms_total"])
             out[name] = {"gpairs_s": round(n / st["ms_total"] / 1e6, 3), "ms": round(st["ms_total"], 1),
+                         "ms_runs": [round(r["ms_total"], 1) for r in runs],
                          "partitions": st["n_partitions"], "imbalance": round(st["imbalance"], 3),
                          "passthrough": st["passthrough_partitions"], "overflow_retries": st["overflow_retries"],
                          "ms_partition": round(st["ms_partition"], 1), "ms_sort": round(st["ms_sort"], 1),
