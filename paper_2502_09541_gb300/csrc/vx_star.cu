@@ -130,10 +130,12 @@ __device__ __forceinline__ int32_t load_role(const ChunkParams &p, int r, uint64
 // mixed-radix group id, aggregate.  Accumulators live in shared memory when
 // the groups fit (kSmem), else in global memory.
 // survivors of one block tile, collected in shared memory (split mode)
-struct SurvTile {
+template <uint32_t kCap>
+struct SurvTileT {
   unsigned int n, base;
-  uint2 e[kStarTileRows];  // (chunk row, group id)
+  uint2 e[kCap];  // (chunk row, group id)
 };
+using SurvTile = SurvTileT<kStarTileRows>;
 
 // rows base + j * blockDim.x (j < kRows) of one chunk.  kSplit: surviving
 // rows are appended to the block's survivor list instead of being aggregated
@@ -281,6 +283,21 @@ __device__ __forceinline__ int32_t slot_val(const int4 (&vals)[kR], int slot, in
   return x;
 }
 
+// where the vector path reads row j's value of a row-logic slot: the loaded
+// vectors in registers, or the thread's own 16-byte slots in shared memory
+// (slot k of thread t at sv[k * 256 + t])
+template <int kR, int kV>
+struct RegVals {
+  const int4 (&v)[kV][kR];
+  __device__ __forceinline__ int32_t operator()(int slot, int j) const { return slot_val(v[j >> 2], slot, j & 3); }
+};
+struct SmemVals {
+  const int4 *sv;
+  __device__ __forceinline__ int32_t operator()(int slot, int j) const {
+    return lane4(sv[slot * 256 + threadIdx.x], j & 3);
+  }
+};
+
 // Vector path: kV groups of 4 consecutive rows, r0 + v * kVecTileRows + 0..3
 // (r0 a multiple of 4, staged columns 16-byte aligned).  Every row-logic
 // column is loaded with one 16-byte load per group before any row is
@@ -309,10 +326,10 @@ __device__ __forceinline__ void star_load4(const ChunkParams &p, uint64_t r0, in
   }
 }
 
-template <bool kSmem, bool kSplit, int kR, int kV>
-__device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, const int4 (&vals)[kV][kR],
+template <bool kSmem, bool kSplit, int kV, class Vals, class Tile>
+__device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, const Vals &vals,
                                            unsigned long long *ssum, unsigned long long *scnt,
-                                           unsigned long long &surv, SurvTile *st) {
+                                           unsigned long long &surv, Tile *st) {
   constexpr int kN = 4 * kV;  // rows of this thread
   bool alive[kN];
   uint32_t g[kN];
@@ -324,13 +341,13 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
   for (int q = 0; q < p.n_fact_preds; ++q) {
     const int s = p.fp_slot[q];
 #pragma unroll
-    for (int j = 0; j < kN; ++j) alive[j] = alive[j] && pred_ok(slot_val(vals[j >> 2], s, j & 3), p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+    for (int j = 0; j < kN; ++j) alive[j] = alive[j] && pred_ok(vals(s, j), p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
   }
   for (int d = 0; d < p.n_dims; ++d) {
     const int s = p.dim_slot[d];
     int32_t key[kN];
 #pragma unroll
-    for (int j = 0; j < kN; ++j) key[j] = slot_val(vals[j >> 2], s, j & 3);
+    for (int j = 0; j < kN; ++j) key[j] = vals(s, j);
     if (p.dspan[d]) {
       const uint32_t *__restrict__ map = reinterpret_cast<const uint32_t *>(p.ht[d]);
       uint32_t v[kN];
@@ -381,7 +398,7 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
 #pragma unroll
     for (int j = 0; j < kN; ++j) {
       if (!alive[j]) continue;
-      const int32_t code = slot_val(vals[j >> 2], s, j & 3);
+      const int32_t code = vals(s, j);
       if (code < 0 || code >= p.fgk_card[k]) {
         atomicOr(p.err, ERR_RANGE);
         alive[j] = false;
@@ -404,10 +421,10 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
   for (int j = 0; j < kN; ++j) {
     if (!alive[j]) continue;
     const int64_t a = p.agg_a_role < 0    ? 0
-                      : p.agg_slot[0] >= 0 ? slot_val(vals[j >> 2], p.agg_slot[0], j & 3)
+                      : p.agg_slot[0] >= 0 ? vals(p.agg_slot[0], j)
                                            : load_role(p, p.agg_a_role, row_of(r0, j));
     const int64_t b = p.agg_b_role < 0    ? 0
-                      : p.agg_slot[1] >= 0 ? slot_val(vals[j >> 2], p.agg_slot[1], j & 3)
+                      : p.agg_slot[1] >= 0 ? vals(p.agg_slot[1], j)
                                            : load_role(p, p.agg_b_role, row_of(r0, j));
     const int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
     if (kSmem) {
@@ -421,22 +438,48 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
 }
 
 
-// prefetching resident grid (see star_vec_kernel); measured slower (64-116
-// registers, fewer resident blocks), so one block per tile
-constexpr bool kVecPrefetch = false;
+// column values of the vector path: in registers, or staged by each thread into
+// its own shared-memory slots with cp.async and read back per access (no
+// column vectors in registers: 32-40 instead of 48-116 registers).  Measured
+// per 2.8M-row chunk, shared-memory slots won in split mode (28.0 vs 30.1 µs
+// with 4 columns, 31.4 vs 35.0 with 6) and with 8 columns (37.7 vs 48.0), and
+// lost with 6 columns and shared-memory group accumulators (47.2 vs 40.5).
+constexpr bool vec_cols(bool split, int kr) { return split || kr >= 8; }
 
 // groups of 4 rows per thread: a block tile is kVecGroups x kVecTileRows rows
 constexpr int kVecGroups = 1;  // 2 raises registers to 62-128 and measured slower
 static_assert(kVecGroups * kVecTileRows <= kStarTileRows, "a block tile's survivors must fit its list");
+static_assert(kVecGroups == 1, "shared-memory column slots hold one group of 4 rows");
 
-// Vector path kernel over whole block tiles of kVecGroups x kVecTileRows rows.
-// kPrefetch = false: one block per tile (the hardware keeps as many resident as
-// registers allow); true: a resident grid whose threads load the next tile's
-// columns before evaluating the current one
-template <bool kSmem, bool kSplit, int kR, bool kPrefetch>
+// thread t's 4 rows r0..r0+3 of every row-logic column into scol[k * 256 + t]
+template <int kR>
+__device__ __forceinline__ void star_stage4(const ChunkParams &p, uint64_t r0, int4 *scol) {
+  const bool full = r0 + 3 < p.n;
+#pragma unroll
+  for (int k = 0; k < kR; ++k) {
+    const int32_t *col = p.staged[k < p.n_rowroles ? p.rowrole[k] : p.rowrole[0]];
+    int4 *dst = &scol[k * 256 + threadIdx.x];
+    if (full) {  // 16-byte aligned: staged columns are, and r0 is a multiple of 4
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(col + r0) : "memory");
+    } else {
+      *dst = make_int4(r0 < p.n ? __ldg(col + r0) : 0, r0 + 1 < p.n ? __ldg(col + r0 + 1) : 0,
+                       r0 + 2 < p.n ? __ldg(col + r0 + 2) : 0, 0);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the thread reads only its own slots
+}
+
+// Vector path kernel over whole block tiles of kVecGroups x kVecTileRows rows,
+// one block per tile (the hardware keeps as many resident as registers and
+// shared memory allow).
+template <bool kSmem, bool kSplit, int kR>
 __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
+  constexpr bool kCols = vec_cols(kSplit, kR);
   extern __shared__ unsigned long long sacc[];  // [2 * n_groups] when kSmem
-  __shared__ SurvTile st;
+  __shared__ SurvTileT<kVecGroups * kVecTileRows> st;
+  __shared__ int4 scol[kCols ? kR * 256 : 1];
   unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
   if (kSmem) {
     for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
@@ -445,22 +488,15 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   __syncthreads();
   unsigned long long surv = 0;
   constexpr uint64_t kTile = (uint64_t)kVecGroups * kVecTileRows;
-  const uint64_t stride = (uint64_t)gridDim.x * kTile;
-  uint64_t t0 = (uint64_t)blockIdx.x * kTile;
-  int4 cur[kVecGroups][kR], nxt[kVecGroups][kR];
-  if (kPrefetch && t0 < p.n) star_load4<kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, cur);
-  for (; t0 < p.n; t0 += stride) {
-    if (kPrefetch) {  // the next tile's columns are in flight while this one is evaluated
-      if (t0 + stride < p.n) star_load4<kR, kVecGroups>(p, t0 + stride + 4ull * threadIdx.x, nxt);
+  for (uint64_t t0 = (uint64_t)blockIdx.x * kTile; t0 < p.n; t0 += (uint64_t)gridDim.x * kTile) {
+    const uint64_t r0 = t0 + 4ull * threadIdx.x;
+    if (kCols) {
+      star_stage4<kR>(p, r0, scol);
+      star_rows4<kSmem, kSplit, 1>(p, r0, SmemVals{scol}, ssum, scnt, surv, &st);
     } else {
-      star_load4<kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, cur);
-    }
-    star_rows4<kSmem, kSplit, kR, kVecGroups>(p, t0 + 4ull * threadIdx.x, cur, ssum, scnt, surv, &st);
-    if (kPrefetch) {
-#pragma unroll
-      for (int v = 0; v < kVecGroups; ++v)
-#pragma unroll
-        for (int k = 0; k < kR; ++k) cur[v][k] = nxt[v][k];
+      int4 cur[kVecGroups][kR];
+      star_load4<kR, kVecGroups>(p, r0, cur);
+      star_rows4<kSmem, kSplit, kVecGroups>(p, r0, RegVals<kR, kVecGroups>{cur}, ssum, scnt, surv, &st);
     }
     if (kSplit) {
       __syncthreads();
@@ -499,7 +535,7 @@ static int vec_resident(size_t smem) {
   auto it = cache.find(smem);
   if (it != cache.end()) return it->second;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, star_vec_kernel<kSmem, kSplit, kR, kVecPrefetch>, 256,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, star_vec_kernel<kSmem, kSplit, kR>, 256,
                                                     smem) != cudaSuccess || occ < 1)
     occ = 1;
   cudaGetLastError();
@@ -507,16 +543,16 @@ static int vec_resident(size_t smem) {
   return occ;
 }
 
-// tiles of n rows; a resident grid when the blocks prefetch their next tile
+// tiles of n rows; a resident grid when groups accumulate in shared memory
 template <bool kSmem, bool kSplit, int kR>
 static void launch_vec_w(const vx_ctx *ctx, const ChunkParams &p, uint64_t n, size_t smem, cudaStream_t s) {
   uint64_t grid = (n + kVecGroups * kVecTileRows - 1) / (kVecGroups * kVecTileRows);
-  // group accumulators in shared memory also want a resident grid: each block
+  // group accumulators in shared memory want a resident grid: each block
   // then merges its groups into global memory once per chunk, not once per tile
-  if (kVecPrefetch || kSmem)
+  if (kSmem)
     grid = std::min<uint64_t>(grid, (uint64_t)ctx->num_sms * vec_resident<kSmem, kSplit, kR>(smem));
   grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, 1u << 30));
-  star_vec_kernel<kSmem, kSplit, kR, kVecPrefetch><<<(unsigned)grid, 256, smem, s>>>(p);
+  star_vec_kernel<kSmem, kSplit, kR><<<(unsigned)grid, 256, smem, s>>>(p);
 }
 
 template <bool kSmem, bool kSplit>
@@ -533,10 +569,10 @@ template <bool kSmem, bool kSplit>
 static vx_status vec_attr(size_t smem) {
   static bool done = false;
   if (!done && smem > 0) {
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 2, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 4, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 6, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 8, kVecPrefetch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
     done = true;
   }
   return VX_OK;
