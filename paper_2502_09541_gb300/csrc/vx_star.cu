@@ -232,32 +232,32 @@ __device__ __forceinline__ void star_rows(const ChunkParams &p, uint64_t base, u
 #pragma unroll
       for (int j = 0; j < kRows; ++j) surv += alive[j];
     }
-    if (kSplit) {
+    if constexpr (kSplit) {
 #pragma unroll
       for (int j = 0; j < kRows; ++j) {
         if (!alive[j]) continue;
         const unsigned int k = atomicAdd(&st->n, 1u);
         st->e[k] = make_uint2((uint32_t)row[j], g[j]);
       }
-      return;
-    }
-    int32_t av[kRows], bv[kRows];
+    } else {
+      int32_t av[kRows], bv[kRows];
 #pragma unroll
-    for (int j = 0; j < kRows; ++j) {  // aggregate inputs of all rows in flight together
-      av[j] = (alive[j] && p.agg_a_role >= 0) ? load_role(p, p.agg_a_role, row[j]) : 0;
-      bv[j] = (alive[j] && p.agg_b_role >= 0) ? load_role(p, p.agg_b_role, row[j]) : 0;
-    }
+      for (int j = 0; j < kRows; ++j) {  // aggregate inputs of all rows in flight together
+        av[j] = (alive[j] && p.agg_a_role >= 0) ? load_role(p, p.agg_a_role, row[j]) : 0;
+        bv[j] = (alive[j] && p.agg_b_role >= 0) ? load_role(p, p.agg_b_role, row[j]) : 0;
+      }
 #pragma unroll
-    for (int j = 0; j < kRows; ++j) {
-      if (!alive[j]) continue;
-      const int64_t a = av[j], b = bv[j];
-      int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
-      if (kSmem) {
-        atomicAdd(&ssum[g[j]], (unsigned long long)v);
-        atomicAdd(&scnt[g[j]], 1ull);
-      } else {
-        atomicAdd(&p.g_sum[g[j]], (unsigned long long)v);
-        atomicAdd(&p.g_cnt[g[j]], 1ull);
+      for (int j = 0; j < kRows; ++j) {
+        if (!alive[j]) continue;
+        const int64_t a = av[j], b = bv[j];
+        int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
+        if (kSmem) {
+          atomicAdd(&ssum[g[j]], (unsigned long long)v);
+          atomicAdd(&scnt[g[j]], 1ull);
+        } else {
+          atomicAdd(&p.g_sum[g[j]], (unsigned long long)v);
+          atomicAdd(&p.g_cnt[g[j]], 1ull);
+        }
       }
     }
   }
@@ -291,10 +291,11 @@ struct RegVals {
   const int4 (&v)[kV][kR];
   __device__ __forceinline__ int32_t operator()(int slot, int j) const { return slot_val(v[j >> 2], slot, j & 3); }
 };
-struct SmemVals {
+template <int kV>
+struct SmemVals {  // slot k, group v of thread t at sv[(k * kV + v) * 256 + t]
   const int4 *sv;
   __device__ __forceinline__ int32_t operator()(int slot, int j) const {
-    return lane4(sv[slot * 256 + threadIdx.x], j & 3);
+    return lane4(sv[(slot * kV + (j >> 2)) * 256 + threadIdx.x], j & 3);
   }
 };
 
@@ -411,28 +412,28 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
 #pragma unroll
     for (int j = 0; j < kN; ++j) surv += alive[j];
   }
-  if (kSplit) {
+  if constexpr (kSplit) {
 #pragma unroll
     for (int j = 0; j < kN; ++j)
       if (alive[j]) st->e[atomicAdd(&st->n, 1u)] = make_uint2((uint32_t)row_of(r0, j), g[j]);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int j = 0; j < kN; ++j) {
-    if (!alive[j]) continue;
-    const int64_t a = p.agg_a_role < 0    ? 0
-                      : p.agg_slot[0] >= 0 ? vals(p.agg_slot[0], j)
-                                           : load_role(p, p.agg_a_role, row_of(r0, j));
-    const int64_t b = p.agg_b_role < 0    ? 0
-                      : p.agg_slot[1] >= 0 ? vals(p.agg_slot[1], j)
-                                           : load_role(p, p.agg_b_role, row_of(r0, j));
-    const int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
-    if (kSmem) {
-      atomicAdd(&ssum[g[j]], (unsigned long long)v);
-      atomicAdd(&scnt[g[j]], 1ull);
-    } else {
-      atomicAdd(&p.g_sum[g[j]], (unsigned long long)v);
-      atomicAdd(&p.g_cnt[g[j]], 1ull);
+    for (int j = 0; j < kN; ++j) {
+      if (!alive[j]) continue;
+      const int64_t a = p.agg_a_role < 0    ? 0
+                        : p.agg_slot[0] >= 0 ? vals(p.agg_slot[0], j)
+                                             : load_role(p, p.agg_a_role, row_of(r0, j));
+      const int64_t b = p.agg_b_role < 0    ? 0
+                        : p.agg_slot[1] >= 0 ? vals(p.agg_slot[1], j)
+                                             : load_role(p, p.agg_b_role, row_of(r0, j));
+      const int64_t v = p.agg_op == VX_AGG_SUM ? a : p.agg_op == VX_AGG_MUL ? a * b : p.agg_op == VX_AGG_SUB ? a - b : 0;
+      if (kSmem) {
+        atomicAdd(&ssum[g[j]], (unsigned long long)v);
+        atomicAdd(&scnt[g[j]], 1ull);
+      } else {
+        atomicAdd(&p.g_sum[g[j]], (unsigned long long)v);
+        atomicAdd(&p.g_cnt[g[j]], 1ull);
+      }
     }
   }
 }
@@ -446,25 +447,37 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
 // lost with 6 columns and shared-memory group accumulators (47.2 vs 40.5).
 constexpr bool vec_cols(bool split, int kr) { return split || kr >= 8; }
 
-// groups of 4 rows per thread: a block tile is kVecGroups x kVecTileRows rows
-constexpr int kVecGroups = 1;  // 2 raises registers to 62-128 and measured slower
-static_assert(kVecGroups * kVecTileRows <= kStarTileRows, "a block tile's survivors must fit its list");
-static_assert(kVecGroups == 1, "shared-memory column slots hold one group of 4 rows");
+// groups of 4 rows per thread (a block tile is groups x kVecTileRows rows):
+// one.  Two raised registers to 62-128 with register-held columns, and with
+// shared-memory slots of 4 columns (48 registers, 4 resident blocks) measured
+// 29.5 / 34.3 µs against 29.0 / 29.2 µs per chunk for T2 at 0.1 / 1 %.
+constexpr int kVecGroups = 1;
+constexpr int vec_groups(bool split, int kr) { return (void)split, (void)kr, kVecGroups; }
+static_assert(2 * kVecTileRows <= kStarTileRows, "a block tile's survivors must fit its list");
+// dynamic shared memory of the column slots, after the group accumulators
+constexpr size_t vec_col_bytes(bool split, int kr) {
+  return vec_cols(split, kr) ? (size_t)kr * vec_groups(split, kr) * 256 * sizeof(int4) : 0;
+}
 
-// thread t's 4 rows r0..r0+3 of every row-logic column into scol[k * 256 + t]
-template <int kR>
+// thread t's rows r0 + v * kVecTileRows + 0..3 of every row-logic column into
+// scol[(k * kV + v) * 256 + t]
+template <int kR, int kV>
 __device__ __forceinline__ void star_stage4(const ChunkParams &p, uint64_t r0, int4 *scol) {
-  const bool full = r0 + 3 < p.n;
 #pragma unroll
-  for (int k = 0; k < kR; ++k) {
-    const int32_t *col = p.staged[k < p.n_rowroles ? p.rowrole[k] : p.rowrole[0]];
-    int4 *dst = &scol[k * 256 + threadIdx.x];
-    if (full) {  // 16-byte aligned: staged columns are, and r0 is a multiple of 4
-      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(col + r0) : "memory");
-    } else {
-      *dst = make_int4(r0 < p.n ? __ldg(col + r0) : 0, r0 + 1 < p.n ? __ldg(col + r0 + 1) : 0,
-                       r0 + 2 < p.n ? __ldg(col + r0 + 2) : 0, 0);
+  for (int v = 0; v < kV; ++v) {
+    const uint64_t rv = r0 + (uint64_t)v * kVecTileRows;
+    const bool full = rv + 3 < p.n;
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+      const int32_t *col = p.staged[k < p.n_rowroles ? p.rowrole[k] : p.rowrole[0]];
+      int4 *dst = &scol[(k * kV + v) * 256 + threadIdx.x];
+      if (full) {  // 16-byte aligned: staged columns are, and rv is a multiple of 4
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(col + rv) : "memory");
+      } else {
+        *dst = make_int4(rv < p.n ? __ldg(col + rv) : 0, rv + 1 < p.n ? __ldg(col + rv + 1) : 0,
+                         rv + 2 < p.n ? __ldg(col + rv + 2) : 0, 0);
+      }
     }
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -477,9 +490,10 @@ __device__ __forceinline__ void star_stage4(const ChunkParams &p, uint64_t r0, i
 template <bool kSmem, bool kSplit, int kR>
 __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   constexpr bool kCols = vec_cols(kSplit, kR);
-  extern __shared__ unsigned long long sacc[];  // [2 * n_groups] when kSmem
-  __shared__ SurvTileT<kVecGroups * kVecTileRows> st;
-  __shared__ int4 scol[kCols ? kR * 256 : 1];
+  constexpr int kG = vec_groups(kSplit, kR);
+  extern __shared__ __align__(16) unsigned long long sacc[];  // [2 * n_groups] when kSmem, then column slots
+  __shared__ SurvTileT<kG * kVecTileRows> st;
+  int4 *scol = reinterpret_cast<int4 *>(sacc + (kSmem ? 2 * p.n_groups : 0));  // 16-byte aligned: even count
   unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
   if (kSmem) {
     for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
@@ -487,12 +501,12 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   if (threadIdx.x == 0) st.n = 0;
   __syncthreads();
   unsigned long long surv = 0;
-  constexpr uint64_t kTile = (uint64_t)kVecGroups * kVecTileRows;
+  constexpr uint64_t kTile = (uint64_t)kG * kVecTileRows;
   for (uint64_t t0 = (uint64_t)blockIdx.x * kTile; t0 < p.n; t0 += (uint64_t)gridDim.x * kTile) {
     const uint64_t r0 = t0 + 4ull * threadIdx.x;
     if (kCols) {
-      star_stage4<kR>(p, r0, scol);
-      star_rows4<kSmem, kSplit, 1>(p, r0, SmemVals{scol}, ssum, scnt, surv, &st);
+      star_stage4<kR, kG>(p, r0, scol);
+      star_rows4<kSmem, kSplit, kG>(p, r0, SmemVals<kG>{scol}, ssum, scnt, surv, &st);
     } else {
       int4 cur[kVecGroups][kR];
       star_load4<kR, kVecGroups>(p, r0, cur);
@@ -543,40 +557,40 @@ static int vec_resident(size_t smem) {
   return occ;
 }
 
-// tiles of n rows; a resident grid when groups accumulate in shared memory
+// tiles of n rows; a resident grid when groups accumulate in shared memory.
+// acc_smem = the group accumulators' bytes (0 unless kSmem).
 template <bool kSmem, bool kSplit, int kR>
-static void launch_vec_w(const vx_ctx *ctx, const ChunkParams &p, uint64_t n, size_t smem, cudaStream_t s) {
-  uint64_t grid = (n + kVecGroups * kVecTileRows - 1) / (kVecGroups * kVecTileRows);
+static vx_status launch_vec_w(const vx_ctx *ctx, const ChunkParams &p, uint64_t n, size_t acc_smem,
+                              cudaStream_t s) {
+  static bool attr = false;  // the largest dynamic size this instantiation takes
+  if (!attr) {
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, kR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)((kSmem ? 16 * kSmemGroups : 0) + vec_col_bytes(kSplit, kR))));
+    attr = true;
+  }
+  const size_t smem = acc_smem + vec_col_bytes(kSplit, kR);
+  constexpr uint64_t kTile = (uint64_t)vec_groups(kSplit, kR) * kVecTileRows;
+  uint64_t grid = (n + kTile - 1) / kTile;
   // group accumulators in shared memory want a resident grid: each block
   // then merges its groups into global memory once per chunk, not once per tile
   if (kSmem)
     grid = std::min<uint64_t>(grid, (uint64_t)ctx->num_sms * vec_resident<kSmem, kSplit, kR>(smem));
   grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, 1u << 30));
   star_vec_kernel<kSmem, kSplit, kR><<<(unsigned)grid, 256, smem, s>>>(p);
-}
-
-template <bool kSmem, bool kSplit>
-static void launch_vec(const vx_ctx *ctx, const ChunkParams &p, int kr, size_t smem, cudaStream_t s) {
-  switch (kr) {
-    case 2: launch_vec_w<kSmem, kSplit, 2>(ctx, p, p.n, smem, s); break;
-    case 4: launch_vec_w<kSmem, kSplit, 4>(ctx, p, p.n, smem, s); break;
-    case 6: launch_vec_w<kSmem, kSplit, 6>(ctx, p, p.n, smem, s); break;
-    default: launch_vec_w<kSmem, kSplit, 8>(ctx, p, p.n, smem, s); break;
-  }
-}
-
-template <bool kSmem, bool kSplit>
-static vx_status vec_attr(size_t smem) {
-  static bool done = false;
-  if (!done && smem > 0) {
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    VX_CUDA_TRY(cudaFuncSetAttribute(star_vec_kernel<kSmem, kSplit, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(16 * kSmemGroups)));
-    done = true;
-  }
   return VX_OK;
 }
+
+template <bool kSmem, bool kSplit>
+static vx_status launch_vec(const vx_ctx *ctx, const ChunkParams &p, int kr, size_t acc_smem, cudaStream_t s) {
+  switch (kr) {
+    case 2: return launch_vec_w<kSmem, kSplit, 2>(ctx, p, p.n, acc_smem, s);
+    case 4: return launch_vec_w<kSmem, kSplit, 4>(ctx, p, p.n, acc_smem, s);
+    case 6: return launch_vec_w<kSmem, kSplit, 6>(ctx, p, p.n, acc_smem, s);
+    default: return launch_vec_w<kSmem, kSplit, 8>(ctx, p, p.n, acc_smem, s);
+  }
+}
+
 
 // width (2, 4, 6 or 8 loaded columns) of the vector path for a chunk, or 0
 // for the scalar path (no row-logic column, more than 8, or a staged column
@@ -1131,7 +1145,7 @@ struct StarExKernel : ExKernel {
       if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
       const int kr = vec_width(p);
       if (kr) {
-        launch_vec<false, true>(ctx, p, kr, 0, s);
+        VX_TRY((launch_vec<false, true>(ctx, p, kr, 0, s)));
       } else {
         const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
         star_split_kernel<<<gs, 256, 0, s>>>(p);
@@ -1162,10 +1176,9 @@ struct StarExKernel : ExKernel {
     const int kr = vec_width(p);
     if (kr) {  // vector path
       if (smem) {
-        VX_TRY((vec_attr<true, false>(smem_bytes)));
-        launch_vec<true, false>(ctx, p, kr, smem_bytes, s);
+        VX_TRY((launch_vec<true, false>(ctx, p, kr, smem_bytes, s)));
       } else {
-        launch_vec<false, false>(ctx, p, kr, 0, s);
+        VX_TRY((launch_vec<false, false>(ctx, p, kr, 0, s)));
       }
     } else if (smem) {
       static bool attr_set = false;
