@@ -194,4 +194,31 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st);
 // and joined back into the compute stream, nothing is synchronised.
 vx_status enqueue_pipeline_for_capture(vx_ctx *ctx, ExKernel &k, char *ring, int n_slots, ExecStats *st);
 
+// Registers caller host memory for the duration of a call unless it is
+// already page-locked: copies to or from pageable memory hold the issuing
+// thread until the stream's earlier work is done.
+struct HostReg {
+  void *p = nullptr;
+  bool reg = false;
+  vx_status add(void *ptr, uint64_t bytes) {
+    if (!ptr || !bytes) return VX_OK;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    cudaGetLastError();
+    if (e == cudaSuccess && at.type == cudaMemoryTypeHost) return VX_OK;
+    e = cudaHostRegister(ptr, bytes, cudaHostRegisterMapped);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaHostRegister(%llu) failed: %s", (unsigned long long)bytes, cudaGetErrorString(e));
+      return VX_E_CUDA;
+    }
+    p = ptr;
+    reg = true;
+    return VX_OK;
+  }
+  ~HostReg() {
+    if (reg) cudaHostUnregister(p);
+  }
+};
+
 }  // namespace vx

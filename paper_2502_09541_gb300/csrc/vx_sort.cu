@@ -608,30 +608,6 @@ vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uin
 
 namespace {
 
-struct HostReg {  // registers host memory for the duration of a call if not pinned
-  void *p = nullptr;
-  bool reg = false;
-  vx_status add(void *ptr, uint64_t bytes) {
-    if (!ptr || !bytes) return VX_OK;
-    cudaPointerAttributes at{};
-    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
-    cudaGetLastError();
-    if (e == cudaSuccess && at.type == cudaMemoryTypeHost) return VX_OK;
-    e = cudaHostRegister(ptr, bytes, cudaHostRegisterMapped);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      set_error("cudaHostRegister(%llu) failed: %s", (unsigned long long)bytes, cudaGetErrorString(e));
-      return VX_E_CUDA;
-    }
-    p = ptr;
-    reg = true;
-    return VX_OK;
-  }
-  ~HostReg() {
-    if (reg) cudaHostUnregister(p);
-  }
-};
-
 void parallel_copy(void *dst, const void *src, uint64_t bytes) {
   const uint64_t kMin = 64ull << 20;
   unsigned nt = std::max(1u, std::min(16u, (unsigned)(bytes / kMin)));
@@ -657,7 +633,7 @@ struct PartitionPass : ExKernel {
   const uint64_t *d_spl;
   uint64_t *mid_keys;
   uint32_t *mid_vals;
-  std::vector<uint64_t> *bnd;  // chunks x (P+1)
+  uint64_t *d_bnd;  // device, chunks x (P+1): read back once after the pass
   int S;
 
   uint64_t size() override { return (n + R - 1) / R; }
@@ -681,7 +657,12 @@ struct PartitionPass : ExKernel {
     h2d.push_back({vals + r0, b.vals[0], 4 * m});
   }
   vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
-    return range_partition_enqueue(bufs(slot), rows(it), d_spl, P, temp(slot), s);
+    VX_TRY(range_partition_enqueue(bufs(slot), rows(it), d_spl, P, temp(slot), s));
+    // the chunk's boundary array stays on the device: a copy into pageable
+    // host memory would hold the issuing thread until the store queue drains
+    VX_CUDA_TRY(cudaMemcpyAsync(d_bnd + it * (P + 1), radix_state_of(temp(slot))->base, 8ull * (P + 1),
+                                cudaMemcpyDeviceToDevice, s));
+    return VX_OK;
   }
   bool has_outputs() override { return true; }
   vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
@@ -689,8 +670,6 @@ struct PartitionPass : ExKernel {
     uint64_t r0 = it * R, m = rows(it);
     d2h.push_back({b.keys[1], mid_keys + r0, 8 * m});
     d2h.push_back({b.vals[1], mid_vals + r0, 4 * m});
-    RadixState *st = radix_state_of(temp(slot));
-    d2h.push_back({st->base, bnd->data() + it * (P + 1), 8ull * (P + 1)});
     return VX_OK;
   }
 };
@@ -861,6 +840,13 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
   const uint64_t n_chunks = (n + R - 1) / R;
   std::vector<uint64_t> bnd(n_chunks * (P + 1));
   {
+    DevBuf dbnd;
+    dbnd.arena = &ctx->arena;
+    dbnd.p = ctx->arena.alloc(8 * bnd.size());
+    if (!dbnd.p) {
+      set_error("vx_sort: boundary arrays do not fit the arena");
+      return VX_E_NOMEM;
+    }
     PartitionPass pp;
     pp.ctx = ctx;
     pp.keys = keys;
@@ -871,10 +857,12 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     pp.d_spl = d_spl;
     pp.mid_keys = mid_keys;
     pp.mid_vals = mid_vals;
-    pp.bnd = &bnd;
+    pp.d_bnd = dbnd.as<uint64_t>();
     pp.S = S;
     ExecStats es;
     VX_TRY(run_pipeline(ctx, pp, &es));
+    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+    VX_CUDA_TRY(cudaMemcpy(bnd.data(), dbnd.p, 8 * bnd.size(), cudaMemcpyDeviceToHost));
     ss.bytes_h2d += es.bytes_h2d;
     ss.bytes_d2h += es.bytes_d2h;
     ss.kernel_launches += es.kernel_launches * 4;  // upsweep, row scan, totals, downsweep

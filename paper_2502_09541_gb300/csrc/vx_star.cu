@@ -2030,6 +2030,8 @@ VX_API vx_status vx_filter(vx_ctx *ctx, const vx_pred *preds, int32_t n_preds, u
   fk.out_rows = out_rows;
   fk.cap = out_rows ? cap : 0;
   fk.S = ctx->cfg.n_slots;
+  HostReg out_reg;  // the per-chunk stores of row ids then run asynchronously
+  if (out_rows && cap) VX_TRY(out_reg.add(out_rows, 8 * cap));
   ExecStats es;
   if (fk.n_rows) VX_TRY(run_pipeline(ctx, fk, &es));
   *out_count = fk.total;
