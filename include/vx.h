@@ -427,6 +427,9 @@ typedef struct {
   uint64_t submitted, completed, failed, cycles, bytes_h2d, active_peak;
   double p50_ms, p99_ms, mean_ms, max_ms; /* latency from vx_submit to completion */
   double wall_ms;                         /* since vx_serve_start */
+  uint64_t work_rows;                     /* query rows evaluated by the multi-query kernels */
+  double ms_kernel;                       /* their device time (CUDA events) */
+  double ms_admit;                        /* host time spent admitting (planning) queries */
 } vx_serve_stats;
 
 /* Starts the serving engine of a context: a thread that runs one shared

@@ -52,6 +52,8 @@ struct ServeEngine {
   std::map<uint64_t, std::unique_ptr<ServeQuery>> all;
   uint64_t next_id = 1;
   uint64_t n_chunks = 0, cursor = 0, cycles = 0, bytes_h2d = 0, active_peak = 0, failed = 0;
+  uint64_t work_rows = 0;           // query rows the multi-query kernels evaluated
+  double ms_kernel = 0, ms_admit = 0;  // their device time; host time spent admitting
   double t_start = 0;
   std::vector<double> latencies;
   // staging ring
@@ -60,7 +62,7 @@ struct ServeEngine {
   DevBuf ring;
   uint64_t slot_bytes = 0;
   struct Slot {
-    cudaEvent_t ev_in = nullptr, ev_k = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_k0 = nullptr, ev_k = nullptr;  // ev_k0..ev_k: the multi-query kernel
     bool busy = false;
     char *host = nullptr;  // pinned staging for params and items
   };
@@ -118,6 +120,7 @@ static void admit(ServeEngine &e) {
   while (!e.pending.empty() && e.active.size() < e.opts.max_active && !e.rfree.empty()) {
     ServeQuery *q = e.pending.front();
     vx_status st;
+    const double t_adm = now_ms();
     {
       std::lock_guard<std::recursive_mutex> g(e.ctx->mu);
       st = run_star(e.ctx, &q->plan, nullptr, true, &q->prep);
@@ -126,6 +129,7 @@ static void admit(ServeEngine &e) {
         st = run_star(e.ctx, &q->plan, nullptr, true, &q->prep);
       }
     }
+    e.ms_admit += now_ms() - t_adm;
     if (st == VX_E_NOMEM && !e.active.empty()) return;  // wait for memory to free up
     e.pending.pop_front();
     if (st == VX_OK && q->prep.G > kServeMaxGroups) {
@@ -184,7 +188,12 @@ static vx_status cycle(ServeEngine &e, bool *did) {
     const double dl = now_ms() + ctx->cfg.wait_timeout_ms;
     for (;;) {
       cudaError_t qe = cudaEventQuery(sl.ev_k);
-      if (qe == cudaSuccess) break;
+      if (qe == cudaSuccess) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k) == cudaSuccess) e.ms_kernel += ms;
+        cudaGetLastError();
+        break;
+      }
       if (qe != cudaErrorNotReady) VX_CUDA_TRY(qe);
       if (now_ms() > dl) {
         set_error("serving: wait limit expired");
@@ -235,6 +244,7 @@ static vx_status cycle(ServeEngine &e, bool *did) {
       p.staged[q->prep.staged_role[i]] = (const int32_t *)(dcols + (uint64_t)bufs[i] * col_bytes(e)) + lo;
     p.row0 = c0 + lo;
     p.n = hi - lo;
+    e.work_rows += hi - lo;
     p.chunk_surv = nullptr;
     const uint32_t qi = (uint32_t)qs.size();
     hparams[qi] = p;
@@ -255,6 +265,7 @@ static vx_status cycle(ServeEngine &e, bool *did) {
   VX_CUDA_TRY(cudaMemcpyAsync(ditems, hitems, sizeof(MultiItem) * n_items, cudaMemcpyHostToDevice, ctx->s_h2d));
   VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
   VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
+  VX_CUDA_TRY(cudaEventRecord(sl.ev_k0, ctx->s_compute));
   VX_TRY(launch_star_multi(ctx, dparams, ditems, n_items, dnext, ctx->s_compute));
   VX_CUDA_TRY(cudaEventRecord(sl.ev_k, ctx->s_compute));
   sl.busy = true;
@@ -337,6 +348,7 @@ void serve_shutdown(vx_ctx *ctx) {
   for (auto &s : e->slots) {
     if (s.ev_in) cudaEventDestroy(s.ev_in);
     if (s.ev_k) cudaEventDestroy(s.ev_k);
+    if (s.ev_k0) cudaEventDestroy(s.ev_k0);
     if (s.host) cudaFreeHost(s.host);
   }
   for (uint64_t *p : e->rbuf) cudaFreeHost(p);
@@ -379,7 +391,8 @@ VX_API vx_status vx_serve_start(vx_ctx *ctx, const vx_serve_opts *opts) {
   e->slots.resize(e->S);
   for (auto &s : e->slots) {
     VX_CUDA_TRY(cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming));
-    VX_CUDA_TRY(cudaEventCreateWithFlags(&s.ev_k, cudaEventDisableTiming));
+    VX_CUDA_TRY(cudaEventCreate(&s.ev_k0));
+    VX_CUDA_TRY(cudaEventCreate(&s.ev_k));
     VX_CUDA_TRY(cudaHostAlloc((void **)&s.host, params_bytes(*e) + items_bytes(*e), cudaHostAllocDefault));
   }
   for (uint32_t i = 0; i < e->opts.max_active; ++i) {
@@ -481,6 +494,9 @@ VX_API vx_status vx_serve_stats_get(vx_ctx *ctx, vx_serve_stats *out) {
   s.completed = e->latencies.size();
   s.failed = e->failed;
   s.cycles = e->cycles;
+  s.work_rows = e->work_rows;
+  s.ms_kernel = e->ms_kernel;
+  s.ms_admit = e->ms_admit;
   s.bytes_h2d = e->bytes_h2d;
   s.active_peak = e->active_peak;
   s.wall_ms = now_ms() - e->t_start;
