@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--serve-plain-queries", type=int, default=100)
     ap.add_argument("--serve-chunk-rows", type=int, default=1 << 21, help="rows per shared-scan chunk")
     ap.add_argument("--serve-max-active", type=int, default=32, help="queries attached to the scan at once")
+    ap.add_argument("--serve-slots", type=int, default=0, help="staging slots of the shared scan (0: library default)")
     ap.add_argument("--clustered-rows", type=int, default=300_000_000,
                     help="date-clustered fact table of the per-chunk materialization comparison (0: skip)")
     return ap.parse_args()
@@ -243,7 +244,8 @@ def run_serving(vx, G, ctx, fid, did, args):
     plans = [vx.make_plan(tmpls[name], fid, did, G.STAR_ATTR_CARD, vx.VX_LATE_AUTO, rb, re) for name, rb, re in qs]
     logical_of = [(q[2] - q[1]) * 4 * (len(tmpls[q[0]]["dims"]) + len(tmpls[q[0]]["fact_preds"]) + 2) for q in qs]
 
-    vx.vx_serve_start(ctx, chunk_rows=args.serve_chunk_rows, max_active=args.serve_max_active)
+    vx.vx_serve_start(ctx, chunk_rows=args.serve_chunk_rows, max_active=args.serve_max_active,
+                      n_slots=args.serve_slots)
     t0 = time.perf_counter()
     tickets = []
     for plan, ta in zip(plans, arrivals):
@@ -262,6 +264,8 @@ def run_serving(vx, G, ctx, fid, did, args):
            "qps": round(len(qs) / wall, 2), "host_gbs": round(sum(logical_of) / wall / 1e9, 3),
            "scan_h2d_gbs": round(s["bytes_h2d"] / wall / 1e9, 3), "active_peak": int(s["active_peak"]),
            "kernel_busy": round(s["ms_kernel"] / (wall * 1e3), 3), "admit_busy": round(s["ms_admit"] / (wall * 1e3), 3),
+           "cycle_host_busy": round(s["ms_cycle"] / (wall * 1e3), 3), "slot_wait_busy": round(s["ms_wait"] / (wall * 1e3), 3),
+           "cycles": int(s["cycles"]),
            "kernel_grows_s": round(s["work_rows"] / (s["ms_kernel"] * 1e6), 2) if s["ms_kernel"] else None,
            "mean_interarrival_ms": round(gap_s * 1e3, 3), "form": "shared circular scan"}
 

@@ -430,6 +430,8 @@ typedef struct {
   uint64_t work_rows;                     /* query rows evaluated by the multi-query kernels */
   double ms_kernel;                       /* their device time (CUDA events) */
   double ms_admit;                        /* host time spent admitting (planning) queries */
+  double ms_cycle;                        /* host time spent issuing scan cycles */
+  double ms_wait;                         /* of which waiting for a staging slot's previous kernel */
 } vx_serve_stats;
 
 /* Starts the serving engine of a context: a thread that runs one shared

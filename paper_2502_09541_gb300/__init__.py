@@ -138,7 +138,8 @@ class vx_serve_stats(ctypes.Structure):
                 ("cycles", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64), ("active_peak", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("wall_ms", ctypes.c_double), ("work_rows", ctypes.c_uint64),
-                ("ms_kernel", ctypes.c_double), ("ms_admit", ctypes.c_double)]
+                ("ms_kernel", ctypes.c_double), ("ms_admit", ctypes.c_double), ("ms_cycle", ctypes.c_double),
+                ("ms_wait", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -54,6 +54,8 @@ struct ServeEngine {
   uint64_t n_chunks = 0, cursor = 0, cycles = 0, bytes_h2d = 0, active_peak = 0, failed = 0;
   uint64_t work_rows = 0;           // query rows the multi-query kernels evaluated
   double ms_kernel = 0, ms_admit = 0;  // their device time; host time spent admitting
+  double ms_cycle = 0;                 // host time spent in scan cycles (issuing chunks)
+  double ms_wait = 0;                  // of which waiting for a slot's previous kernel
   double t_start = 0;
   std::vector<double> latencies;
   // staging ring
@@ -67,6 +69,7 @@ struct ServeEngine {
     char *host = nullptr;  // pinned staging for params and items
   };
   std::vector<Slot> slots;
+  cudaStream_t s_plan = nullptr;  // admission's planning work, apart from the scan's kernels
   // pinned result slots
   std::vector<uint64_t *> rbuf;
   std::vector<int> rfree;
@@ -123,11 +126,18 @@ static void admit(ServeEngine &e) {
     const double t_adm = now_ms();
     {
       std::lock_guard<std::recursive_mutex> g(e.ctx->mu);
+      // planning (sampling, dimension builds, accumulator set-up) runs and
+      // synchronises on its own stream, so it does not wait for the scan
+      // kernels queued on the compute stream; it ends synchronised, before
+      // the query attaches
+      std::swap(e.ctx->s_compute, e.s_plan);
       st = run_star(e.ctx, &q->plan, nullptr, true, &q->prep);
       if (st == VX_E_NOMEM && evict_unused_resident(e.ctx)) {  // tables of finished queries make room
         q->prep = PreparedStar();
         st = run_star(e.ctx, &q->plan, nullptr, true, &q->prep);
       }
+      cudaStreamSynchronize(e.ctx->s_compute);
+      std::swap(e.ctx->s_compute, e.s_plan);
     }
     e.ms_admit += now_ms() - t_adm;
     if (st == VX_E_NOMEM && !e.active.empty()) return;  // wait for memory to free up
@@ -185,13 +195,15 @@ static vx_status cycle(ServeEngine &e, bool *did) {
   const int k = (int)(e.cycles % e.S);
   ServeEngine::Slot &sl = e.slots[k];
   if (sl.busy) {  // slot reuse waits for its previous kernel (bounded)
-    const double dl = now_ms() + ctx->cfg.wait_timeout_ms;
+    const double t_w = now_ms();
+    const double dl = t_w + ctx->cfg.wait_timeout_ms;
     for (;;) {
       cudaError_t qe = cudaEventQuery(sl.ev_k);
       if (qe == cudaSuccess) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k) == cudaSuccess) e.ms_kernel += ms;
         cudaGetLastError();
+        e.ms_wait += now_ms() - t_w;
         break;
       }
       if (qe != cudaErrorNotReady) VX_CUDA_TRY(qe);
@@ -222,6 +234,7 @@ static vx_status cycle(ServeEngine &e, bool *did) {
   };
   std::vector<ServeQuery *> qs;
   uint32_t n_items = 0;
+  uint64_t n_scan_rows = 0;  // chunk rows the shared-scan queries reach
   for (ServeQuery *q : e.active) {
     if (q->state != 1 || c < q->c_first || c >= q->c_last || q->seen[c - q->c_first]) continue;
     const uint64_t lo = std::max(c0, q->prep.row_begin) - c0;
@@ -234,22 +247,51 @@ static vx_status cycle(ServeEngine &e, bool *did) {
       if (b < 0) fits = false;
       bufs.push_back(b);
     }
-    const uint32_t tiles = (uint32_t)((hi - lo + kMultiTile - 1) / kMultiTile);
-    if (!fits || n_items + tiles > e.max_items) {  // this query waits for a later cycle over the chunk
+    if (!fits) {  // this query waits for a later cycle over the chunk
       cols.resize(saved);
       continue;
     }
     ChunkParams p = q->prep.P;
-    for (size_t i = 0; i < q->prep.staged_cols.size(); ++i)
-      p.staged[q->prep.staged_role[i]] = (const int32_t *)(dcols + (uint64_t)bufs[i] * col_bytes(e)) + lo;
-    p.row0 = c0 + lo;
-    p.n = hi - lo;
-    e.work_rows += hi - lo;
     p.chunk_surv = nullptr;
+    // shared scan: row-logic slots read from the tile's union columns; staged
+    // pointers at the chunk's base; the query's rows are [lo, hi) of the chunk
+    int8_t ucol[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool scan = p.n_rowroles >= 1 && p.n_rowroles <= 8;
+    for (int k = 0; scan && k < p.n_rowroles; ++k) {
+      int b = -1;
+      for (size_t i = 0; i < q->prep.staged_role.size(); ++i)
+        if (q->prep.staged_role[i] == p.rowrole[k]) b = bufs[i];
+      if (b < 0) scan = false;
+      ucol[k] = (int8_t)b;
+    }
+    uint32_t tiles = 0;
+    if (scan) {
+      for (size_t i = 0; i < q->prep.staged_cols.size(); ++i)
+        p.staged[q->prep.staged_role[i]] = (const int32_t *)(dcols + (uint64_t)bufs[i] * col_bytes(e));
+      for (int k = 0; k < 8; ++k) p.ucol[k] = k < p.n_rowroles ? ucol[k] : ucol[0];
+      p.scan_kr = (int8_t)(p.n_rowroles <= 2 ? 2 : p.n_rowroles <= 4 ? 4 : p.n_rowroles <= 6 ? 6 : 8);
+      p.row0 = c0;
+      p.row_lo = lo;
+      p.n = hi;
+    } else {  // the (query, tile) kernel over the query's part of the chunk
+      tiles = (uint32_t)((hi - lo + kMultiTile - 1) / kMultiTile);
+      if (n_items + tiles > e.max_items) {
+        cols.resize(saved);
+        continue;
+      }
+      for (size_t i = 0; i < q->prep.staged_cols.size(); ++i)
+        p.staged[q->prep.staged_role[i]] = (const int32_t *)(dcols + (uint64_t)bufs[i] * col_bytes(e)) + lo;
+      p.scan_kr = 0;
+      p.row0 = c0 + lo;
+      p.row_lo = 0;
+      p.n = hi - lo;
+    }
+    e.work_rows += hi - lo;
     const uint32_t qi = (uint32_t)qs.size();
     hparams[qi] = p;
     for (uint32_t t = 0; t < tiles; ++t) hitems[n_items + t] = MultiItem{qi, t};
     n_items += tiles;
+    n_scan_rows = std::max<uint64_t>(n_scan_rows, scan ? hi : 0);
     qs.push_back(q);
   }
   if (qs.empty()) return VX_OK;
@@ -262,10 +304,13 @@ static vx_status cycle(ServeEngine &e, bool *did) {
     e.bytes_h2d += 4 * len;
   }
   VX_CUDA_TRY(cudaMemcpyAsync(dparams, hparams, sizeof(ChunkParams) * qs.size(), cudaMemcpyHostToDevice, ctx->s_h2d));
-  VX_CUDA_TRY(cudaMemcpyAsync(ditems, hitems, sizeof(MultiItem) * n_items, cudaMemcpyHostToDevice, ctx->s_h2d));
+  if (n_items)
+    VX_CUDA_TRY(cudaMemcpyAsync(ditems, hitems, sizeof(MultiItem) * n_items, cudaMemcpyHostToDevice, ctx->s_h2d));
   VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
   VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
   VX_CUDA_TRY(cudaEventRecord(sl.ev_k0, ctx->s_compute));
+  VX_TRY(launch_star_scan(ctx, dparams, (uint32_t)qs.size(), dcols, col_bytes(e), (uint32_t)cols.size(), n_scan_rows,
+                          dnext + 1, ctx->s_compute));
   VX_TRY(launch_star_multi(ctx, dparams, ditems, n_items, dnext, ctx->s_compute));
   VX_CUDA_TRY(cudaEventRecord(sl.ev_k, ctx->s_compute));
   sl.busy = true;
@@ -308,7 +353,9 @@ static void engine_loop(ServeEngine *e) {
     vx_status st = VX_OK;
     if (e->fatal == VX_OK) {
       lk.unlock();
+      const double t_cyc = now_ms();
       st = cycle(*e, &did);
+      e->ms_cycle += now_ms() - t_cyc;
       lk.lock();
     }
     if (st != VX_OK && e->fatal == VX_OK) {
@@ -352,6 +399,10 @@ void serve_shutdown(vx_ctx *ctx) {
     if (s.host) cudaFreeHost(s.host);
   }
   for (uint64_t *p : e->rbuf) cudaFreeHost(p);
+  if (e->s_plan) {
+    cudaStreamSynchronize(e->s_plan);
+    cudaStreamDestroy(e->s_plan);
+  }
   delete e;
   ctx->serve = nullptr;
 }
@@ -388,6 +439,7 @@ VX_API vx_status vx_serve_start(vx_ctx *ctx, const vx_serve_opts *opts) {
               (unsigned long long)(e->slot_bytes * e->S));
     return VX_E_NOMEM;
   }
+  VX_CUDA_TRY(cudaStreamCreateWithFlags(&e->s_plan, cudaStreamNonBlocking));
   e->slots.resize(e->S);
   for (auto &s : e->slots) {
     VX_CUDA_TRY(cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming));
@@ -497,6 +549,8 @@ VX_API vx_status vx_serve_stats_get(vx_ctx *ctx, vx_serve_stats *out) {
   s.work_rows = e->work_rows;
   s.ms_kernel = e->ms_kernel;
   s.ms_admit = e->ms_admit;
+  s.ms_cycle = e->ms_cycle;
+  s.ms_wait = e->ms_wait;
   s.bytes_h2d = e->bytes_h2d;
   s.active_peak = e->active_peak;
   s.wall_ms = now_ms() - e->t_start;

@@ -336,7 +336,7 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
   uint32_t g[kN];
 #pragma unroll
   for (int j = 0; j < kN; ++j) {
-    alive[j] = row_of(r0, j) < p.n;
+    alive[j] = row_of(r0, j) >= p.row_lo && row_of(r0, j) < p.n;
     g[j] = 0;
   }
   for (int q = 0; q < p.n_fact_preds; ++q) {
@@ -719,6 +719,75 @@ __global__ void __launch_bounds__(256) star_multi_kernel(const ChunkParams *__re
     star_rows<false, 8>(sp, (uint64_t)m.tile * kMultiTile + threadIdx.x, nullptr, nullptr, surv);
     __syncthreads();  // sp and s_item are rewritten by the next item
   }
+}
+
+// union column slots of the shared-scan kernel: column u, thread t at sv[u * 256 + t]
+struct UnionVals {
+  const int4 *sv;
+  const int8_t *ucol;  // the query's slot -> union column
+  __device__ __forceinline__ int32_t operator()(int slot, int j) const {
+    return lane4(sv[ucol[slot] * 256 + threadIdx.x], j & 3);
+  }
+};
+
+__global__ void __launch_bounds__(256) star_scan_kernel(const ChunkParams *__restrict__ ps, uint32_t n_q,
+                                                         const char *__restrict__ dcols, uint64_t col_stride,
+                                                         uint32_t n_cols, uint64_t n_rows, unsigned int *next) {
+  extern __shared__ __align__(16) int4 ucols[];  // [n_cols][256] 16-byte slots
+  __shared__ unsigned int s_tile;
+  unsigned long long surv = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(next, 1u);
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)s_tile * kVecTileRows;
+    __syncthreads();  // s_tile is rewritten by the next tile
+    if (t0 >= n_rows) break;
+    const uint64_t r0 = t0 + 4ull * threadIdx.x;
+    const bool full = r0 + 3 < n_rows;
+    for (uint32_t u = 0; u < n_cols; ++u) {  // each thread stages and later reads only its own slots
+      const int32_t *col = reinterpret_cast<const int32_t *>(dcols + u * col_stride);
+      int4 *dst = &ucols[u * 256 + threadIdx.x];
+      if (full) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(col + r0) : "memory");
+      } else {
+        *dst = make_int4(r0 < n_rows ? col[r0] : 0, r0 + 1 < n_rows ? col[r0 + 1] : 0,
+                         r0 + 2 < n_rows ? col[r0 + 2] : 0, 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    for (uint32_t q = 0; q < n_q; ++q) {
+      const ChunkParams &p = ps[q];
+      if (!p.scan_kr || t0 >= p.n || t0 + kVecTileRows <= p.row_lo) continue;  // uniform over the block
+      const UnionVals vals{ucols, p.ucol};
+      star_rows4<false, false, 1>(p, r0, vals, nullptr, nullptr, surv, static_cast<SurvTile *>(nullptr));
+    }
+  }
+}
+
+vx_status launch_star_scan(vx_ctx *ctx, const ChunkParams *d_params, uint32_t n_q, const char *dcols,
+                           uint64_t col_stride, uint32_t n_cols, uint64_t n_rows, unsigned int *d_next,
+                           cudaStream_t s) {
+  if (!n_q || !n_rows || !n_cols) return VX_OK;
+  static int occ = 0;
+  const size_t smem = (size_t)n_cols * 256 * sizeof(int4);
+  if (!occ) {
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(12 * 256 * sizeof(int4))));
+    VX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, star_scan_kernel, 256, 12 * 256 * sizeof(int4)));
+    occ = std::max(occ, 1);
+  }
+  if (n_cols > 12) {
+    set_error("shared scan: %u union columns; at most 12", n_cols);
+    return VX_E_UNSUPPORTED;
+  }
+  VX_CUDA_TRY(cudaMemsetAsync(d_next, 0, 4, s));
+  const uint64_t tiles = (n_rows + kVecTileRows - 1) / kVecTileRows;
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)ctx->num_sms * occ);
+  star_scan_kernel<<<grid, 256, smem, s>>>(d_params, n_q, dcols, col_stride, n_cols, n_rows, d_next);
+  VX_CUDA_TRY(cudaGetLastError());
+  return VX_OK;
 }
 
 vx_status launch_star_multi(vx_ctx *ctx, const ChunkParams *d_params, const MultiItem *d_items, uint32_t n_items,

@@ -117,6 +117,12 @@ struct ChunkParams {
   // slot of each aggregate column among them when it is staged in every chunk
   // (loaded with the row logic's columns), else -1 (loaded per survivor)
   int8_t agg_slot[2];
+  // shared-scan kernel (serving): row-logic slot k of this query lives in
+  // union column ucol[k] of the staged chunk; the query's rows of the chunk
+  // are [row_lo, n); scan_kr = its vector width (0: the (query, tile) kernel)
+  int8_t ucol[8];
+  int8_t scan_kr;
+  uint64_t row_lo;
 };
 
 constexpr uint32_t kStarTileRows = 2048;  // rows of one block tile (256 threads x 8 rows)
@@ -127,6 +133,13 @@ struct MultiItem {
   uint32_t q, tile;
 };
 constexpr uint32_t kMultiTile = 256 * 8;
+// Shared-scan kernel of the serving engine: resident blocks pull 1024-row
+// tiles of the staged chunk (n_rows rows, n_cols union columns of col_stride
+// bytes from dcols), stage each tile's union columns in shared memory once
+// and evaluate every query with scan_kr != 0 against them.
+vx_status launch_star_scan(vx_ctx *ctx, const ChunkParams *d_params, uint32_t n_q, const char *dcols,
+                           uint64_t col_stride, uint32_t n_cols, uint64_t n_rows, unsigned int *d_next,
+                           cudaStream_t s);
 vx_status launch_star_multi(vx_ctx *ctx, const ChunkParams *d_params, const MultiItem *d_items, uint32_t n_items,
                             unsigned int *d_next, cudaStream_t s);
 
