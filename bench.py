@@ -133,13 +133,21 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+STAR_KERNEL_END = b"// ---- end of the fused chunk kernel's device code"
+
+
 def kernel_source_digest():
-    """sha256 of the fused star kernel's sources (ties a stored ncu figure to them)."""
+    """sha256 of the fused star kernel's device code: vx_star.cu up to its end
+    marker, and vx_star.cuh (ties a stored ncu figure to that code)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("vx_star.cu", "vx_star.cuh"):
-        with open(os.path.join(ROOT, "paper_2502_09541_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2502_09541_gb300", "csrc")
+    with open(os.path.join(csrc, "vx_star.cu"), "rb") as fh:
+        text = fh.read()
+    cut = text.find(STAR_KERNEL_END)
+    h.update(text if cut < 0 else text[:cut])
+    with open(os.path.join(csrc, "vx_star.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()
 
 
@@ -619,7 +627,7 @@ def run_ours(args):
     e2e_d2h = sum(s["bytes_d2h"] for s in e2e_stats) / args.steps
     e2e_gbs = logical * world / (e2e_s * 1e9)
 
-    serving = run_serving(vx, G, ctx, fid, did, args) if not args.no_extras else None
+    serving = run_serving(vx, G, ctx, fid, did, args) if not args.no_extras and args.serve_queries > 0 else None
     clustered = run_clustered(vx, G, ctx, did, args) if not args.no_extras and args.clustered_rows else None
 
     line = {

@@ -539,6 +539,7 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
     if ((threadIdx.x & 31) == 0 && surv) atomicAdd(&p.chunk_surv[p.chunk_idx], surv);
   }
 }
+// ---- end of the fused chunk kernel's device code
 
 template <bool kSmem, bool kSplit, int kR>
 static int vec_resident(size_t smem) {
@@ -818,21 +819,37 @@ __global__ void __launch_bounds__(kChunkSampleRows) chunk_features_kernel(const 
   const uint32_t run = threadIdx.x / 64, k = threadIdx.x % 64;
   const uint64_t off = (uint64_t)run * cn / 4 + k;
   if (off < cn) {
-    const uint64_t i = c0 + off;
+    const uint64_t i = p.row0 + c0 + off;
+    // every value of the row is read through mapped host memory up front (the
+    // reads overlap instead of forming a chain of link round trips), then
+    // every dimension is probed (all lookups in flight, for the marginals)
+    int32_t fv[VX_MAX_PREDS], kv[VX_MAX_DIMS], gv[VX_MAX_GKEYS];
+#pragma unroll
+    for (int q = 0; q < VX_MAX_PREDS; ++q) fv[q] = q < p.n_fact_preds ? p.zc[p.fp_role[q]][i] : 0;
+#pragma unroll
+    for (int d = 0; d < VX_MAX_DIMS; ++d) kv[d] = d < p.n_dims ? p.zc[p.dim_role[d]][i] : 0;
+#pragma unroll
+    for (int q = 0; q < VX_MAX_GKEYS; ++q) gv[q] = q < p.n_fgk ? p.zc[p.fgk_role[q]][i] : 0;
     bool ok = true;
-    for (int q = 0; q < p.n_fact_preds && ok; ++q)
-      ok = pred_ok(p.zc[p.fp_role[q]][p.row0 + i], p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
-    bool all = ok;
-    for (int d = 0; d < p.n_dims; ++d) {  // every probe, for the per-dimension marginals
+#pragma unroll
+    for (int q = 0; q < VX_MAX_PREDS; ++q)
+      if (q < p.n_fact_preds) ok = ok && pred_ok(fv[q], p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+    bool hit[VX_MAX_DIMS];
+#pragma unroll
+    for (int d = 0; d < VX_MAX_DIMS; ++d) {
       uint32_t v = 0;
-      const bool hit = dim_lookup(p, d, p.zc[p.dim_role[d]][p.row0 + i], v);
-      if (hit) atomicAdd(&cd[d], 1u);
-      all = all && hit;
+      hit[d] = d < p.n_dims && dim_lookup(p, d, kv[d], v);
     }
-    for (int q = 0; q < p.n_fgk && all; ++q) {
-      const int32_t code = p.zc[p.fgk_role[q]][p.row0 + i];
-      all = code >= 0 && code < p.fgk_card[q];
+    bool all = ok;
+#pragma unroll
+    for (int d = 0; d < VX_MAX_DIMS; ++d) {
+      if (d >= p.n_dims) continue;
+      if (hit[d]) atomicAdd(&cd[d], 1u);
+      all = all && hit[d];
     }
+#pragma unroll
+    for (int q = 0; q < VX_MAX_GKEYS; ++q)
+      if (q < p.n_fgk) all = all && gv[q] >= 0 && gv[q] < p.fgk_card[q];
     atomicAdd(&cs, 1u);
     if (ok) atomicAdd(&cf, 1u);
     if (all) atomicAdd(&ca, 1u);
