@@ -570,6 +570,14 @@ def run_ours(args):
                 "traffic": round(tr * staged_bytes / max(1, fused_launches)) if tr else None,
                 "algorithmic_bytes_per_launch": round(staged_bytes / max(1, fused_launches)),
                 "avg_launch_us": round(1000 * kern_ms / max(1, fused_launches), 2), "launches": fused_launches}
+    # what any kernel reading each launch's bytes once reaches at this launch
+    # size (a plain coalesced read of them right after their copy-engine
+    # transfer, event-timed the same way): the fused kernel's practical ceiling
+    if ach and fused_launches:
+        ceil_gbs = vx.vx_probe_stream(ctx, roofline["algorithmic_bytes_per_launch"], 15)
+        roofline["launch_ceiling"] = {"kernel": "stream_read_kernel (vx_probe_stream)", "achieved": round(ceil_gbs, 1),
+                                      "frac": round(ceil_gbs / hbm_peak, 4),
+                                      "fused_of_ceiling": round(ach / ceil_gbs, 4)}
 
     # the late-materialization gather: link-bound zero-copy reads of the
     # survivors' payload columns from mapped host memory (64-byte granules)

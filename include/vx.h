@@ -230,6 +230,8 @@ typedef struct {
   uint64_t late_chunks;    /* VX_LATE_PER_CHUNK: chunks whose aggregate columns were read by zero-copy */
   double ms_gather;        /* summed device time of the zero-copy gathers of late chunks (CUDA events;
                               0 when not timed: graphs, DAG schedule, serving) */
+  double ms_features;      /* wall time of the per-chunk feature pass before the pipeline (sampling
+                              kernel, copy-back and the per-chunk decisions); 0 when it did not run */
 } vx_query_stats;
 
 /* Result of vx_run_plan / vx_groupby: groups with count > 0 in ascending group
@@ -490,6 +492,19 @@ vx_status vx_probe_link(vx_ctx *ctx, uint64_t bytes, uint64_t chunk, double *h2d
  * per second.  VX_E_NOMEM if the table does not fit the arena; VX_E_INVAL for
  * table_bytes < 32 or n_reads == 0. */
 vx_status vx_probe_hbm_random(vx_ctx *ctx, uint64_t table_bytes, uint64_t n_reads, double *g_reads_per_s);
+
+/* ---------------------------------------------------------------- streaming probe */
+
+/* What one kernel launch that reads `bytes` of HBM once can reach: the
+ * ceiling of a chunk kernel at the same launch size (the fused chunk kernel of
+ * Section 7.1 reads each staged chunk once).  The paper has no counterpart.
+ * Each of reps + 1 rounds copies `bytes` (rounded down to a multiple of 16)
+ * from a pinned host buffer into an arena buffer by copy engine, as the
+ * executor stages a chunk, then times one coalesced read of them with CUDA
+ * events on the context's compute stream; the first round warms up.  Reports
+ * the median in GB/s (1e9 B/s).  VX_E_NOMEM if the bytes do not fit the arena;
+ * VX_E_INVAL for bytes < 16, reps < 1 or a null output. */
+vx_status vx_probe_stream(vx_ctx *ctx, uint64_t bytes, int32_t reps, double *gbs);
 
 #ifdef __cplusplus
 }

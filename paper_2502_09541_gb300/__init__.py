@@ -76,7 +76,8 @@ class vx_query_stats(ctypes.Structure):
                 ("bytes_logical", ctypes.c_uint64), ("late_mask", ctypes.c_uint32),
                 ("overflow_retries", ctypes.c_uint32), ("est_selectivity", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
-                ("late_chunks", ctypes.c_uint64), ("ms_gather", ctypes.c_double)]
+                ("late_chunks", ctypes.c_uint64), ("ms_gather", ctypes.c_double),
+                ("ms_features", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -164,6 +165,7 @@ SIGNATURES = {
     "vx_drop_resident": ([_vp], _i32),
     "vx_probe_link": ([_vp, _u64, _u64, _P(_dbl), _P(_dbl), _P(_dbl)], _i32),
     "vx_probe_hbm_random": ([_vp, _u64, _u64, _P(_dbl)], _i32),
+    "vx_probe_stream": ([_vp, _u64, _i32, _P(_dbl)], _i32),
     "vx_probe_zero_copy": ([_vp, _u64, _vp, _i32, _vp, _vp, _vp], _i32),
     "vx_sort": ([_vp, _i32, _i32, _vp, _vp, _P(vx_sort_opts), _P(vx_sort_stats)], _i32),
     "vx_radix_sort_pairs": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
@@ -409,6 +411,14 @@ def vx_probe_zero_copy(ctx, n: int, sels):
     ck = np.zeros(len(s), np.uint64)
     _check(load().vx_probe_zero_copy(ctx, n, s.ctypes.data, len(s), zc.ctypes.data, ce.ctypes.data, ck.ctypes.data))
     return zc, ce, ck
+
+
+def vx_probe_stream(ctx, nbytes: int, reps: int) -> float:
+    """GB/s of one coalesced read of nbytes right after their host-to-device
+    copy (median of reps launches)."""
+    r = _dbl()
+    _check(load().vx_probe_stream(ctx, nbytes, reps, ctypes.byref(r)))
+    return r.value
 
 
 def vx_probe_hbm_random(ctx, table_bytes: int, n_reads: int) -> float:

@@ -19,17 +19,37 @@ namespace vx {
 
 // ================================================================== device code
 
-__device__ __forceinline__ bool pred_ok(int32_t v, int32_t op, int32_t lo, int32_t hi) {
+// Every comparison operator as one inclusive range [lo, hi] tested on uint32
+// offsets, v - lo <= hi - lo, optionally complemented: NE is the complement of
+// [lo, lo], and an empty range (BETWEEN with lo > hi, LT INT_MIN, GT INT_MAX,
+// an unknown operator) is the complement of the full range.  Built once per
+// predicate, so the per-row test is a subtract and a compare.
+struct PredRange {
+  uint32_t lo, span;
+  bool inv;
+};
+
+__device__ __forceinline__ PredRange pred_range(int32_t op, int32_t lo, int32_t hi) {
+  int32_t a = lo, b = hi;
+  bool inv = false, none = false;
   switch (op) {
-    case VX_BETWEEN: return lo <= v && v <= hi;
-    case VX_EQ: return v == lo;
-    case VX_NE: return v != lo;
-    case VX_LT: return v < lo;
-    case VX_LE: return v <= lo;
-    case VX_GT: return v > lo;
-    case VX_GE: return v >= lo;
+    case VX_BETWEEN: none = lo > hi; break;
+    case VX_EQ: b = lo; break;
+    case VX_NE: b = lo, inv = true; break;
+    case VX_LT: none = lo == INT_MIN, a = INT_MIN, b = lo - (lo != INT_MIN); break;
+    case VX_LE: a = INT_MIN, b = lo; break;
+    case VX_GT: none = lo == INT_MAX, a = lo + (lo != INT_MAX), b = INT_MAX; break;
+    case VX_GE: a = lo, b = INT_MAX; break;
+    default: none = true;
   }
-  return false;
+  if (none) a = INT_MIN, b = INT_MAX, inv = true;
+  return PredRange{(uint32_t)a, (uint32_t)b - (uint32_t)a, inv};
+}
+
+__device__ __forceinline__ bool pred_in(const PredRange &r, int32_t v) { return ((uint32_t)v - r.lo <= r.span) != r.inv; }
+
+__device__ __forceinline__ bool pred_ok(int32_t v, int32_t op, int32_t lo, int32_t hi) {
+  return pred_in(pred_range(op, lo, hi), v);
 }
 
 __device__ __forceinline__ uint32_t ht_hash32(int32_t k, uint32_t log2cap) {
@@ -158,8 +178,9 @@ __device__ __forceinline__ void star_rows(const ChunkParams &p, uint64_t base, u
       int32_t v[kRows];
 #pragma unroll
       for (int j = 0; j < kRows; ++j) v[j] = alive[j] ? load_role(p, p.fp_role[q], row[j]) : 0;
+      const PredRange r = pred_range(p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
 #pragma unroll
-      for (int j = 0; j < kRows; ++j) alive[j] = alive[j] && pred_ok(v[j], p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+      for (int j = 0; j < kRows; ++j) alive[j] = alive[j] && pred_in(r, v[j]);
     }
     for (int d = 0; d < p.n_dims; ++d) {
       const uint64_t *__restrict__ slots = p.ht[d];
@@ -341,8 +362,9 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
   }
   for (int q = 0; q < p.n_fact_preds; ++q) {
     const int s = p.fp_slot[q];
+    const PredRange r = pred_range(p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
 #pragma unroll
-    for (int j = 0; j < kN; ++j) alive[j] = alive[j] && pred_ok(vals(s, j), p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
+    for (int j = 0; j < kN; ++j) alive[j] = alive[j] && pred_in(r, vals(s, j));
   }
   for (int d = 0; d < p.n_dims; ++d) {
     const int s = p.dim_slot[d];
@@ -1703,7 +1725,9 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   std::vector<float> feats;
   DevBuf fbuf;
   uint32_t late_chunks = 0;
+  double ms_features = 0;
   if ((per_chunk || want_log) && n_chunks) {
+    const double tf0 = now_ms();
     fbuf.arena = &ctx->arena;
     fbuf.p = ctx->arena.alloc(n_chunks * (4 * kChunkFeatures + 8) + 512);
     if (!fbuf.p) {
@@ -1745,6 +1769,7 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
         late_chunks += ek.chunk_late[c];
       }
     }
+    ms_features = now_ms() - tf0;
   }
   ek.proto = P;
 
@@ -1815,6 +1840,7 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   qs.bytes_logical = n_rows * 4ull * role_col.size();
   qs.ms_kernel = ek.main_launches ? ek.ms_main : es.ms_kernel;  // the fused kernel's own time when timed
   qs.ms_gather = ek.ms_gather;
+  qs.ms_features = ms_features;
   qs.kernel_launches = ge ? es.kernel_launches : ek.launches;
   qs.ms_total = now_ms() - t_start;
   out->stats = qs;

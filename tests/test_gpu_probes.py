@@ -47,3 +47,16 @@ def test_hbm_random_read_probe(ctx):
         vx.vx_probe_hbm_random(ctx, 4 << 30, 1 << 20)
     with pytest.raises(vx.VxError):
         vx.vx_probe_hbm_random(ctx, 16, 1 << 20)
+
+
+def test_stream_probe(ctx):
+    # one launch over a 64 MiB chunk's staged bytes, and one eight times larger
+    a = vx.vx_probe_stream(ctx, 45 << 20, 5)
+    b = vx.vx_probe_stream(ctx, 360 << 20, 5)
+    assert 100.0 < a < 20000.0 and 100.0 < b < 20000.0
+    with pytest.raises(vx.VxError):
+        vx.vx_probe_stream(ctx, 4 << 30, 3)
+    with pytest.raises(vx.VxError):
+        vx.vx_probe_stream(ctx, 8, 3)
+    with pytest.raises(vx.VxError):
+        vx.vx_probe_stream(ctx, 1 << 20, 0)

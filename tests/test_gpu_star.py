@@ -189,6 +189,11 @@ def filt():
     [("price", vx.VX_GE, 9_990_000, 0), ("quantity", vx.VX_NE, 3, 0)],
     [("quantity", vx.VX_GT, 100, 0)],   # none pass
     [("quantity", vx.VX_GE, 1, 0)],     # all pass
+    [("quantity", vx.VX_LT, -2**31, 0)],          # empty: nothing is below INT_MIN
+    [("quantity", vx.VX_GT, 2**31 - 1, 0)],       # empty: nothing is above INT_MAX
+    [("quantity", vx.VX_LE, 2**31 - 1, 0), ("discount", vx.VX_GE, -2**31, 0)],  # full ranges
+    [("quantity", vx.VX_BETWEEN, 30, 20)],        # lo > hi: empty
+    [("discount", vx.VX_NE, -5, 0), ("quantity", vx.VX_BETWEEN, -2**31, 2**31 - 1)],
 ])
 def test_filter_rows_bit_exact(filt, preds):
     ctx, f, fid, n = filt
