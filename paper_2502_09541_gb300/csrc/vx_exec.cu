@@ -52,7 +52,7 @@ vx_status issue_copies(const std::vector<CopyOp> &ops, cudaMemcpyKind kind, cuda
 vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
   const uint64_t N = k.size();
   if (N == 0) return VX_OK;
-  const int S = ctx->cfg.n_slots < 2 ? 2 : ctx->cfg.n_slots;
+  const int S = k.n_slots() >= 2 ? k.n_slots() : ctx->cfg.n_slots < 2 ? 2 : ctx->cfg.n_slots;
   const uint64_t slot_bytes = (k.slot_bytes() + 255) & ~255ull;
   DevBuf ring;
   ring.arena = &ctx->arena;
@@ -100,7 +100,7 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
 
   const double deadline = now_ms() + ctx->cfg.wait_timeout_ms;
   uint64_t next_load = 0, next_retire = 0, loads_issued = 0, stores_issued = 0;
-  const int max_loading = 2;  // chunks whose loads may be queued on the copy engine at once
+  const uint64_t max_in_flight = (uint64_t)std::max(1, k.max_in_flight());
   while (next_retire < N) {
     bool progress = false;
     // retire in chunk order
@@ -141,8 +141,7 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
     // stores may not run ahead of loads (flow control)
     if (next_load < N && next_load - next_retire < (uint64_t)S && stores_issued <= loads_issued) {
       SlotState &sl = es.s[next_load % S];
-      uint64_t loading = next_load - next_retire;
-      if (sl.phase == 0 && loading < (uint64_t)max_loading + 1) {
+      if (sl.phase == 0 && next_load - next_retire < max_in_flight) {
         char *slot = base + (next_load % S) * slot_bytes;
         ops.clear();
         k.inputs(next_load, slot, ops);

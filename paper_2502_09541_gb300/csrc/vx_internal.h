@@ -178,6 +178,10 @@ struct ExKernel {
   virtual void on_retire(uint64_t it) {}
   // called after kernel(it) has completed on the device
   virtual vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) { return VX_OK; }
+  // slots of the ring (0: the context's n_slots) and chunks the immediate
+  // schedule keeps in flight at once (loaded, computing or storing)
+  virtual int n_slots() { return 0; }
+  virtual int max_in_flight() { return 3; }
 };
 
 struct ExecStats {

@@ -688,10 +688,12 @@ struct SortPass : ExKernel {
   std::vector<uint64_t> job_n, job_off;
   uint64_t *out_keys;
   uint32_t *out_vals;
-  int S;
+  int S;                    // slots of the ring (one published result word per slot)
   uint64_t pass_pairs = 0;  // pairs x executed passes
 
   uint64_t size() override { return job_n.size(); }
+  int n_slots() override { return S; }
+  int max_in_flight() override { return S; }
   uint64_t kb() const { return (8 * cap + 255) & ~255ull; }
   uint64_t vb() const { return (4 * cap + 255) & ~255ull; }
   uint64_t slot_bytes() override { return 2 * kb() + 2 * vb() + radix_temp_bytes(cap); }
@@ -918,6 +920,19 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     }
   }
   {
+    // Slots sized by the largest job, as many as fit (at most kMaxSortSlots):
+    // a job's load, sort and store take about the same time, so with three
+    // slots the next load waits for a store and every uneven partition leaves
+    // the device idle; more slots let loads run ahead.  Never fewer than the
+    // S slots of `cap` pairs the partition count was planned for.
+    uint64_t jcap = 0;
+    for (uint64_t x : sp.job_n) jcap = std::max(jcap, x);
+    jcap = (jcap + kRxTile - 1) / kRxTile * kRxTile;
+    if (jcap) {
+      sp.cap = jcap;
+      const uint64_t sb = (sp.slot_bytes() + 255) & ~255ull;
+      sp.S = std::max<int>(S, (int)std::min<uint64_t>(kMaxSortSlots, ctx->arena.largest_free() / sb));
+    }
     ExecStats es;
     VX_TRY(run_pipeline(ctx, sp, &es));
     ss.bytes_h2d += es.bytes_h2d;

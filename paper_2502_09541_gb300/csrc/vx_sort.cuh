@@ -17,6 +17,7 @@ vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s
 vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, uint32_t P, char *temp,
                                   cudaStream_t s);
 constexpr uint32_t kMaxRequestedPartitions = 128;  // isolation may add up to P-1 boundaries
+constexpr int kMaxSortSlots = 6;                   // staging slots of the partition sort pass, at most
 constexpr uint64_t kPipelineRows = 32ull << 20;    // pairs per partition-pass chunk (multiple of the radix tile; 16M / 64M measured slower / erratic)
 constexpr uint64_t kSplitterBufBytes = 8ull * (512 + kPLSegments + 1 + 8);
 
