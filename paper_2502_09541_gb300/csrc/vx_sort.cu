@@ -837,7 +837,7 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
   // ---- pass 1: partition
   double tp = now_ms();
   // partition-pass chunks of kPipelineRows pairs: long enough for efficient
-  // copies (384 MB) and few extents per partition, short enough that the pass
+  // copies (576 MB) and few extents per partition, short enough that the pass
   // pipelines over many chunks
   const uint64_t R = std::min<uint64_t>(cap, kPipelineRows);
   const uint64_t n_chunks = (n + R - 1) / R;

@@ -18,7 +18,14 @@ vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, 
                                   cudaStream_t s);
 constexpr uint32_t kMaxRequestedPartitions = 128;  // isolation may add up to P-1 boundaries
 constexpr int kMaxSortSlots = 6;                   // staging slots of the partition sort pass, at most
-constexpr uint64_t kPipelineRows = 32ull << 20;    // pairs per partition-pass chunk (multiple of the radix tile; 16M / 64M measured slower / erratic)
+// pairs per partition-pass chunk (a multiple of the radix tile).  A
+// partition's pairs sit in one extent per chunk of the intermediate buffer,
+// and the sort pass loads them extent by extent: larger chunks make fewer,
+// larger copies (combined H2D + D2H throughput falls from 340 GB/s at 64 MB
+// copies to 255 GB/s at 2-4 MB).  On 1e9 Zipf pairs the sort phase took
+// 97.5 / 95.0 / 94.1 ms with 32M / 48M / 64M and the partition phase 74 ms
+// with each.
+constexpr uint64_t kPipelineRows = 48ull << 20;
 constexpr uint64_t kSplitterBufBytes = 8ull * (512 + kPLSegments + 1 + 8);
 
 vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t &m, uint64_t seed,
