@@ -360,7 +360,7 @@ def run_sort_extra(vx, G, args):
     gen = time.perf_counter() - t0
     ok = pinned_array(n, np.uint64)
     orr = pinned_array(n, np.uint32)
-    scratch = pinned_array(12 * n, np.uint8)
+    scratch = pinned_array(12 * (n + n // 16), np.uint8)  # room for a region per partition
     ctx = vx.vx_open(16 << 30)
     out = {"pairs": n, "dist": "zipf(1.1)", "budget_gib": 16, "generate_s": round(gen, 1)}
     try:
@@ -390,6 +390,8 @@ def run_sort_extra(vx, G, args):
                          "passthrough": st["passthrough_partitions"], "overflow_retries": st["overflow_retries"],
                          "ms_partition": round(st["ms_partition"], 1), "ms_sort": round(st["ms_sort"], 1),
                          "ms_train": round(st["ms_train"], 1),
+                         "partition_regions": bool(st["contiguous_layout"]),
+                         "out_of_region_pairs": st["out_of_region_pairs"],
                          "link_gbs": round((st["bytes_h2d"] + st["bytes_d2h"]) / st["ms_total"] / 1e6, 1)}
         out["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
         # per-partition radix sorts against HBM: 24 algorithmic bytes per pair

@@ -306,9 +306,16 @@ typedef struct {
   uint64_t seed;              /* sample positions */
   uint64_t sample_size;       /* keys sampled for the splitters (0 = 1 Mi) */
   uint32_t mlp_steps;         /* Adam steps of the CDF MLP (0 = 300) */
-  uint32_t reserved;
+  uint32_t region_slack_pct;  /* headroom of each partition's host region over its sample
+                                 estimate, in percent (0 = 1 % plus four standard deviations of
+                                 the sample count); smaller regions only add extents */
   void *host_scratch;         /* optional host memory of >= 12 * n bytes for the partitioned
-                                 intermediate (else allocated for the call) */
+                                 intermediate (else allocated for the call).  With room for
+                                 the partitions' headroom (12 * (n + n / 16) bytes suffice at
+                                 1e9 pairs; smaller inputs need a larger share) every partition
+                                 gets a contiguous region, which the sort pass loads faster than
+                                 the per-chunk pieces of an intermediate of exactly 12 * n
+                                 bytes (stats: contiguous_layout) */
   uint64_t host_scratch_bytes;
   uint64_t max_slot_pairs;    /* optional cap on the pairs per staging slot (0 = from the arena) */
   uint64_t *splitters_out;    /* optional: receives the P-1 top-level splitters */
@@ -318,13 +325,17 @@ typedef struct {
   uint32_t n_partitions;
   uint32_t passthrough_partitions; /* single-key partitions copied through unsorted */
   uint32_t overflow_retries;       /* multi-key partitions above the slot, sorted recursively */
-  uint32_t reserved;
+  uint32_t contiguous_layout;      /* 1: the intermediate gave every partition its own region */
   uint64_t max_partition, min_partition, slot_pairs;
   double imbalance;                /* largest partition / mean partition */
   double ms_sample, ms_train, ms_partition, ms_sort, ms_total;
   uint64_t bytes_h2d, bytes_d2h, kernel_launches;
   double ms_sort_kernel;           /* device time of the per-partition radix sorts (CUDA events) */
   uint64_t radix_pass_pairs;       /* pairs x executed LSD passes in those sorts (skipped digits excluded) */
+  uint64_t out_of_region_pairs;    /* pairs stored past their partition's region (overflow area,
+                                      spill buffers) */
+  uint64_t spill_buffers;          /* host buffers registered for the call when the overflow area
+                                      ran out */
 } vx_sort_stats;
 
 /* Out-of-core sort of (uint64 key, uint32 row id) pairs held in two registered

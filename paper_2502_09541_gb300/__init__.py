@@ -93,20 +93,21 @@ VX_PART_SAMPLE, VX_PART_LEARNED_PL, VX_PART_LEARNED_MLP = 0, 1, 2
 
 class vx_sort_opts(ctypes.Structure):
     _fields_ = [("partitioner", ctypes.c_int32), ("n_partitions", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("sample_size", ctypes.c_uint64), ("mlp_steps", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("sample_size", ctypes.c_uint64), ("mlp_steps", ctypes.c_uint32), ("region_slack_pct", ctypes.c_uint32),
                 ("host_scratch", ctypes.c_void_p), ("host_scratch_bytes", ctypes.c_uint64),
                 ("max_slot_pairs", ctypes.c_uint64), ("splitters_out", ctypes.c_void_p)]
 
 
 class vx_sort_stats(ctypes.Structure):
     _fields_ = [("n_partitions", ctypes.c_uint32), ("passthrough_partitions", ctypes.c_uint32),
-                ("overflow_retries", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("overflow_retries", ctypes.c_uint32), ("contiguous_layout", ctypes.c_uint32),
                 ("max_partition", ctypes.c_uint64), ("min_partition", ctypes.c_uint64),
                 ("slot_pairs", ctypes.c_uint64), ("imbalance", ctypes.c_double), ("ms_sample", ctypes.c_double),
                 ("ms_train", ctypes.c_double), ("ms_partition", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("bytes_h2d", ctypes.c_uint64), ("bytes_d2h", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("ms_sort_kernel", ctypes.c_double),
-                ("radix_pass_pairs", ctypes.c_uint64)]
+                ("radix_pass_pairs", ctypes.c_uint64), ("out_of_region_pairs", ctypes.c_uint64),
+                ("spill_buffers", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -17,6 +17,7 @@
 // above the slot capacity is sorted recursively.
 #include <algorithm>
 #include <cstddef>
+#include <deque>
 #include <cmath>
 #include <thread>
 
@@ -388,6 +389,22 @@ __global__ void sample_keys_kernel(const uint64_t *keys, uint64_t n, uint64_t m,
   }
 }
 
+// rank[i] = number of sample keys below splitter i (lower bound in the sorted
+// sample): partition p (keys in [spl[p-1], spl[p])) holds rank[p] - rank[p-1]
+// of the m sample keys
+__global__ void sample_ranks_kernel(const uint64_t *sorted, uint64_t m, const uint64_t *spl, uint32_t n_spl,
+                                    uint64_t *rank) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_spl; i += gridDim.x * blockDim.x) {
+    uint64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (sorted[mid] < spl[i]) lo = mid + 1;
+      else hi = mid;
+    }
+    rank[i] = lo;
+  }
+}
+
 // splitters from the sorted sample: s_p = sample[p*m/P]
 __global__ void sample_splitters_kernel(const uint64_t *sorted, uint64_t m, uint32_t P, uint64_t *spl) {
   for (uint32_t p = 1 + blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
@@ -624,6 +641,28 @@ void parallel_copy(void *dst, const void *src, uint64_t bytes) {
 }
 
 // pass 1: per-chunk stable partition into the intermediate + boundary arrays
+// a run of one partition's pairs in host memory, in input order
+struct Extent {
+  const uint64_t *k;
+  const uint32_t *v;
+  uint64_t len;
+};
+
+// host memory registered for the call that holds spilled partition segments
+struct Spill {
+  std::unique_ptr<char[]> mem;
+  HostReg reg;
+  uint64_t cap = 0, used = 0;
+};
+
+// pass 1: range-partition each chunk on the device and store its partition
+// segments to the host intermediate.  Contiguous layout: partition p owns
+// [reg_off[p], reg_off[p] + reg_cap[p]) of the intermediate and each chunk's
+// segment of p is appended there, so the sort pass loads a partition with one
+// copy per column; what does not fit goes to the overflow area after the
+// regions, then to spill buffers.  Blocked layout (an intermediate without room
+// for the regions): chunk c keeps rows [c R, c R + R) and partition p is one
+// extent per chunk.
 struct PartitionPass : ExKernel {
   vx_ctx *ctx;
   const uint64_t *keys;
@@ -633,8 +672,15 @@ struct PartitionPass : ExKernel {
   const uint64_t *d_spl;
   uint64_t *mid_keys;
   uint32_t *mid_vals;
-  uint64_t *d_bnd;  // device, chunks x (P+1): read back once after the pass
+  uint64_t *h_bnd;  // page-locked host, chunks x (P+1): chunk-local partition starts
   int S;
+  bool contig = false;
+  uint64_t C = 0;                          // pairs of the intermediate
+  std::vector<uint64_t> reg_off, reg_cap;  // contiguous layout
+  std::vector<uint64_t> used;
+  uint64_t ovf = 0;                        // next free pair of the overflow area
+  std::deque<Spill> *spills = nullptr;
+  std::vector<std::vector<Extent>> ext;    // per partition, in input order
 
   uint64_t size() override { return (n + R - 1) / R; }
   uint64_t rows(uint64_t it) const { return std::min(R, n - it * R); }
@@ -658,31 +704,88 @@ struct PartitionPass : ExKernel {
   }
   vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
     VX_TRY(range_partition_enqueue(bufs(slot), rows(it), d_spl, P, temp(slot), s));
-    // the chunk's boundary array stays on the device: a copy into pageable
-    // host memory would hold the issuing thread until the store queue drains
-    VX_CUDA_TRY(cudaMemcpyAsync(d_bnd + it * (P + 1), radix_state_of(temp(slot))->base, 8ull * (P + 1),
-                                cudaMemcpyDeviceToDevice, s));
+    // the chunk's boundary array goes to page-locked host memory (a copy into
+    // pageable memory would hold the issuing thread until the store queue
+    // drains); outputs() reads it once the kernel has completed
+    VX_CUDA_TRY(cudaMemcpyAsync(h_bnd + it * (P + 1), radix_state_of(temp(slot))->base, 8ull * (P + 1),
+                                cudaMemcpyDeviceToHost, s));
     return VX_OK;
   }
   bool has_outputs() override { return true; }
-  vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
-    RadixBufs b = bufs(slot);
-    uint64_t r0 = it * R, m = rows(it);
-    d2h.push_back({b.keys[1], mid_keys + r0, 8 * m});
-    d2h.push_back({b.vals[1], mid_vals + r0, 4 * m});
+  void add_extent(uint32_t p, const uint64_t *k, const uint32_t *v, uint64_t len) {
+    std::vector<Extent> &e = ext[p];
+    if (!e.empty() && e.back().k + e.back().len == k && e.back().v + e.back().len == v)
+      e.back().len += len;  // right after the partition's previous segment
+    else
+      e.push_back({k, v, len});
+  }
+  // room for up to len pairs of partition p: its region, the overflow area,
+  // then a spill buffer; *take pairs of it are handed out
+  vx_status place(uint32_t p, uint64_t len, uint64_t **dk, uint32_t **dv, uint64_t *take) {
+    if (used[p] < reg_cap[p]) {
+      *take = std::min(len, reg_cap[p] - used[p]);
+      *dk = mid_keys + reg_off[p] + used[p];
+      *dv = mid_vals + reg_off[p] + used[p];
+      used[p] += *take;
+      return VX_OK;
+    }
+    if (ovf < C) {
+      *take = std::min(len, C - ovf);
+      *dk = mid_keys + ovf;
+      *dv = mid_vals + ovf;
+      ovf += *take;
+      return VX_OK;
+    }
+    if (spills->empty() || spills->back().used == spills->back().cap) {
+      spills->emplace_back();
+      Spill &sp = spills->back();
+      sp.cap = std::max(len, R);
+      sp.mem.reset(new (std::nothrow) char[12 * sp.cap]);
+      if (!sp.mem) {
+        set_error("vx_sort: no host memory for %llu spilled pairs", (unsigned long long)sp.cap);
+        return VX_E_NOMEM;
+      }
+      VX_TRY(sp.reg.add(sp.mem.get(), 12 * sp.cap));
+    }
+    Spill &sp = spills->back();
+    *take = std::min(len, sp.cap - sp.used);
+    *dk = (uint64_t *)sp.mem.get() + sp.used;
+    *dv = (uint32_t *)(sp.mem.get() + 8 * sp.cap) + sp.used;
+    sp.used += *take;
     return VX_OK;
   }
-};
-
-struct Extent {
-  uint64_t off, len;
+  vx_status outputs(uint64_t it, char *slot, std::vector<CopyOp> &d2h) override {
+    RadixBufs b = bufs(slot);
+    const uint64_t r0 = it * R, m = rows(it);
+    const uint64_t *bd = h_bnd + it * (P + 1);  // copied before the kernel's completion event
+    if (!contig) {
+      d2h.push_back({b.keys[1], mid_keys + r0, 8 * m});
+      d2h.push_back({b.vals[1], mid_vals + r0, 4 * m});
+      for (uint32_t p = 0; p < P; ++p)
+        if (bd[p + 1] > bd[p]) add_extent(p, mid_keys + r0 + bd[p], mid_vals + r0 + bd[p], bd[p + 1] - bd[p]);
+      return VX_OK;
+    }
+    for (uint32_t p = 0; p < P; ++p) {
+      uint64_t s0 = bd[p], len = bd[p + 1] - bd[p];
+      while (len) {
+        uint64_t *dk;
+        uint32_t *dv;
+        uint64_t take;
+        VX_TRY(place(p, len, &dk, &dv, &take));
+        d2h.push_back({b.keys[1] + s0, dk, 8 * take});
+        d2h.push_back({b.vals[1] + s0, dv, 4 * take});
+        add_extent(p, dk, dv, take);
+        s0 += take;
+        len -= take;
+      }
+    }
+    return VX_OK;
+  }
 };
 
 // pass 2: per-partition gather + radix sort + store
 struct SortPass : ExKernel {
   vx_ctx *ctx;
-  const uint64_t *mid_keys;
-  const uint32_t *mid_vals;
   uint64_t cap;
   std::vector<std::vector<Extent>> ext;  // per job
   std::vector<uint64_t> job_n, job_off;
@@ -711,8 +814,8 @@ struct SortPass : ExKernel {
     uint64_t at = 0;
     for (const Extent &e : ext[it]) {
       if (!e.len) continue;
-      h2d.push_back({mid_keys + e.off, b.keys[0] + at, 8 * e.len});
-      h2d.push_back({mid_vals + e.off, b.vals[0] + at, 4 * e.len});
+      h2d.push_back({e.k, b.keys[0] + at, 8 * e.len});
+      h2d.push_back({e.v, b.vals[0] + at, 4 * e.len});
       at += e.len;
     }
   }
@@ -761,10 +864,8 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
   if (n <= cap && o.n_partitions <= 1) {
     SortPass sp;
     sp.ctx = ctx;
-    sp.mid_keys = keys;
-    sp.mid_vals = vals;
     sp.cap = cap;
-    sp.ext.push_back({{0, n}});
+    sp.ext.push_back({{keys, vals, n}});
     sp.job_n.push_back(n);
     sp.job_off.push_back(0);
     sp.out_keys = out_keys;
@@ -809,48 +910,86 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
   uint32_t n_spl = 0;
   VX_TRY(splitters_from_sample(ctx, o.partitioner, sorted, m, P, d_spl, o.mlp_steps, &ms_train, &n_spl));
   P = n_spl + 1;  // partitions after heavy-key isolation
-  std::vector<uint64_t> spl(n_spl);
-  if (n_spl) VX_CUDA_TRY(cudaMemcpyAsync(spl.data(), d_spl, 8 * n_spl, cudaMemcpyDeviceToHost, ctx->s_compute));
+  std::vector<uint64_t> spl(n_spl), srank(n_spl);
+  if (n_spl) {
+    DevBuf rbuf;
+    rbuf.arena = &ctx->arena;
+    rbuf.p = ctx->arena.alloc(8 * n_spl);
+    if (!rbuf.p) return VX_E_NOMEM;
+    sample_ranks_kernel<<<1, 128, 0, ctx->s_compute>>>(sorted, m, d_spl, n_spl, rbuf.as<uint64_t>());
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_CUDA_TRY(cudaMemcpyAsync(spl.data(), d_spl, 8 * n_spl, cudaMemcpyDeviceToHost, ctx->s_compute));
+    VX_CUDA_TRY(cudaMemcpyAsync(srank.data(), rbuf.p, 8 * n_spl, cudaMemcpyDeviceToHost, ctx->s_compute));
+    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  }
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
   sbuf.release();
   ss.ms_sample += now_ms() - ts - ms_train;
   ss.ms_train += ms_train;
   if (depth == 0 && o.splitters_out) memcpy(o.splitters_out, spl.data(), 8 * n_spl);
 
-  // ---- host intermediate
+  // partition-pass chunks of kPipelineRows pairs: long enough for efficient
+  // copies (576 MB), short enough that the pass pipelines over many chunks
+  const uint64_t R = std::min<uint64_t>(cap, kPipelineRows);
+  const uint64_t n_chunks = (n + R - 1) / R;
+
+  // ---- host intermediate: one region per partition, sized from the sample's
+  // count c in it (estimate n c / m) plus 1 % and four binomial standard
+  // deviations, then an overflow area of what the intermediate has left (at
+  // least n / 256 pairs); the sort stays exact whatever the estimates, only the
+  // number of extents grows
+  std::vector<uint64_t> reg_off(P), reg_cap(P);
+  uint64_t regions = 0;
+  for (uint32_t p = 0; p < P; ++p) {
+    const uint64_t r1 = p < n_spl ? srank[p] : m, r0 = p ? srank[p - 1] : 0;
+    const double cnt = (double)(r1 - r0), scale = (double)n / (double)m;
+    const double slack = o.region_slack_pct ? o.region_slack_pct / 100.0 : 0.01;
+    const double sigmas = o.region_slack_pct ? 0.0 : 4.0;
+    const double est = (1.0 + slack) * cnt * scale + sigmas * std::sqrt(cnt + 1.0) * scale + kRxTile;
+    // regions start on 128-pair boundaries (1 KB of keys, 512 B of values), so
+    // the sort pass loads each from an aligned host address
+    reg_cap[p] = (std::min<uint64_t>(n, (uint64_t)std::ceil(est)) + 127) / 128 * 128;
+    reg_off[p] = regions;
+    regions += reg_cap[p];
+  }
+  const uint64_t want = regions + n / 256 + kRxTile;
   uint64_t *mid_keys = nullptr;
   uint32_t *mid_vals = nullptr;
-  std::vector<char> own;
+  uint64_t C = 0;  // pairs the intermediate holds
+  bool contig = true;
+  std::unique_ptr<char[]> own;
   HostReg reg_mid;
-  const uint64_t mid_bytes = n * 12;
-  if (depth == 0 && o.host_scratch && o.host_scratch_bytes >= mid_bytes) {
+  std::deque<Spill> spills;
+  if (depth == 0 && o.host_scratch && o.host_scratch_bytes >= 12 * n) {
+    C = o.host_scratch_bytes / 12 / 128 * 128;  // the value array then starts 1 KB-aligned too
+    contig = C >= want;  // else the blocked layout in the first 12 n bytes
+    if (!contig) C = n;
     mid_keys = (uint64_t *)o.host_scratch;
-    mid_vals = (uint32_t *)((char *)o.host_scratch + 8 * n);
-    VX_TRY(reg_mid.add(o.host_scratch, mid_bytes));
+    mid_vals = (uint32_t *)((char *)o.host_scratch + 8 * C);
+    VX_TRY(reg_mid.add(o.host_scratch, 12 * C));
   } else {
-    own.resize(mid_bytes);
-    mid_keys = (uint64_t *)own.data();
-    mid_vals = (uint32_t *)(own.data() + 8 * n);
-    VX_TRY(reg_mid.add(own.data(), mid_bytes));
+    C = (regions + n / 64 + kRxTile + 127) / 128 * 128;
+    own.reset(new (std::nothrow) char[12 * C + 4096]);
+    if (!own) {
+      set_error("vx_sort: no host memory for the %llu-pair intermediate", (unsigned long long)C);
+      return VX_E_NOMEM;
+    }
+    char *base = (char *)(((uintptr_t)own.get() + 4095) & ~(uintptr_t)4095);  // page-aligned
+    mid_keys = (uint64_t *)base;
+    mid_vals = (uint32_t *)(base + 8 * C);
+    VX_TRY(reg_mid.add(base, 12 * C));
   }
 
   // ---- pass 1: partition
   double tp = now_ms();
-  // partition-pass chunks of kPipelineRows pairs: long enough for efficient
-  // copies (576 MB) and few extents per partition, short enough that the pass
-  // pipelines over many chunks
-  const uint64_t R = std::min<uint64_t>(cap, kPipelineRows);
-  const uint64_t n_chunks = (n + R - 1) / R;
-  std::vector<uint64_t> bnd(n_chunks * (P + 1));
+  PartitionPass pp;
   {
-    DevBuf dbnd;
-    dbnd.arena = &ctx->arena;
-    dbnd.p = ctx->arena.alloc(8 * bnd.size());
-    if (!dbnd.p) {
-      set_error("vx_sort: boundary arrays do not fit the arena");
-      return VX_E_NOMEM;
-    }
-    PartitionPass pp;
+    uint64_t *h_bnd = nullptr;
+    VX_CUDA_TRY(cudaHostAlloc((void **)&h_bnd, 8 * n_chunks * (P + 1), cudaHostAllocDefault));
+    struct FreeHost {
+      void *p;
+      ~FreeHost() { cudaFreeHost(p); }
+    } free_bnd{h_bnd};
     pp.ctx = ctx;
     pp.keys = keys;
     pp.vals = vals;
@@ -860,31 +999,35 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     pp.d_spl = d_spl;
     pp.mid_keys = mid_keys;
     pp.mid_vals = mid_vals;
-    pp.d_bnd = dbnd.as<uint64_t>();
+    pp.h_bnd = h_bnd;
     pp.S = S;
+    pp.contig = contig;
+    pp.C = C;
+    pp.reg_off = reg_off;
+    pp.reg_cap = reg_cap;
+    pp.used.assign(P, 0);
+    pp.ovf = regions;
+    pp.spills = &spills;
+    pp.ext.resize(P);
     ExecStats es;
     VX_TRY(run_pipeline(ctx, pp, &es));
     VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
-    VX_CUDA_TRY(cudaMemcpy(bnd.data(), dbnd.p, 8 * bnd.size(), cudaMemcpyDeviceToHost));
     ss.bytes_h2d += es.bytes_h2d;
     ss.bytes_d2h += es.bytes_d2h;
     ss.kernel_launches += es.kernel_launches * 4;  // upsweep, row scan, totals, downsweep
   }
   ss.ms_partition += now_ms() - tp;
 
-  // ---- partition sizes, offsets, extents
+  // ---- partition sizes and output offsets
   std::vector<uint64_t> psize(P, 0), poff(P, 0);
-  for (uint64_t c = 0; c < n_chunks; ++c)
-    for (uint32_t p = 0; p < P; ++p) psize[p] += bnd[c * (P + 1) + p + 1] - bnd[c * (P + 1) + p];
+  for (uint32_t p = 0; p < P; ++p) {
+    for (const Extent &e : pp.ext[p]) psize[p] += e.len;
+    if (contig) ss.out_of_region_pairs += psize[p] - pp.used[p];
+  }
+  ss.spill_buffers += spills.size();
+  if (depth == 0) ss.contiguous_layout = contig ? 1u : 0u;
   for (uint32_t p = 1; p < P; ++p) poff[p] = poff[p - 1] + psize[p - 1];
-  auto extents = [&](uint32_t p) {
-    std::vector<Extent> e;
-    for (uint64_t c = 0; c < n_chunks; ++c) {
-      uint64_t b0 = bnd[c * (P + 1) + p], b1 = bnd[c * (P + 1) + p + 1];
-      if (b1 > b0) e.push_back({c * R + b0, b1 - b0});
-    }
-    return e;
-  };
+  auto extents = [&](uint32_t p) { return pp.ext[p]; };
   uint64_t mx = 0, mn = UINT64_MAX;
   for (uint32_t p = 0; p < P; ++p) {
     mx = std::max(mx, psize[p]);
@@ -902,8 +1045,6 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
   double tq = now_ms();
   SortPass sp;
   sp.ctx = ctx;
-  sp.mid_keys = mid_keys;
-  sp.mid_vals = mid_vals;
   sp.cap = cap;
   sp.out_keys = out_keys;
   sp.out_vals = out_vals;
@@ -948,8 +1089,8 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     if (single_key) {  // already in input order: copy through
       uint64_t at = poff[p];
       for (const Extent &e : ex) {
-        parallel_copy(out_keys + at, mid_keys + e.off, 8 * e.len);
-        parallel_copy(out_vals + at, mid_vals + e.off, 4 * e.len);
+        parallel_copy(out_keys + at, e.k, 8 * e.len);
+        parallel_copy(out_vals + at, e.v, 4 * e.len);
         at += e.len;
       }
       ss.passthrough_partitions += 1;
@@ -967,8 +1108,8 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     uint32_t *tv = (uint32_t *)(tmp.data() + 8 * psize[p]);
     uint64_t at = 0;
     for (const Extent &e : ex) {
-      parallel_copy(tk + at, mid_keys + e.off, 8 * e.len);
-      parallel_copy(tv + at, mid_vals + e.off, 4 * e.len);
+      parallel_copy(tk + at, e.k, 8 * e.len);
+      parallel_copy(tv + at, e.v, 4 * e.len);
       at += e.len;
     }
     HostReg rt;

@@ -110,7 +110,12 @@ def test_mlp_splitters_monotone_and_cover(ctx):
     assert sizes.sum() == n and sizes.max() < 0.5 * n
 
 
-def _sort_case(ctx_budget, n, dist, partitioner, max_slot=0, n_part=0, steps=0, scratch=True):
+def _sort_case(ctx_budget, n, dist, partitioner, max_slot=0, n_part=0, steps=0, scratch=True, sample=100_000,
+               slack=0):
+    """scratch: True = caller scratch of exactly 12 n bytes (per-chunk extents),
+    "roomy" = 12 (n + n / 8) bytes (a region per partition: at a few million
+    pairs the per-partition headroom is a larger share than at a billion),
+    False = none."""
     k, r = G.sort_input(n, dist)
     c = vx.vx_open(ctx_budget)
     try:
@@ -122,10 +127,11 @@ def _sort_case(ctx_budget, n, dist, partitioner, max_slot=0, n_part=0, steps=0, 
         o.partitioner = partitioner
         o.n_partitions = n_part
         o.seed = 3
-        o.sample_size = 100_000
+        o.sample_size = sample
+        o.region_slack_pct = slack
         o.max_slot_pairs = max_slot
         o.mlp_steps = steps
-        buf = np.zeros(12 * n, np.uint8) if scratch else None
+        buf = np.zeros(12 * (n + n // 8) if scratch == "roomy" else 12 * n, np.uint8) if scratch else None
         if scratch:
             o.host_scratch = buf.ctypes.data
             o.host_scratch_bytes = buf.nbytes
@@ -164,3 +170,30 @@ def test_untrained_model_still_exact():
 def test_single_slot_and_library_scratch():
     _sort_case(256 << 20, 100_000, "runs", vx.VX_PART_SAMPLE, scratch=False)
     _sort_case(256 << 20, 1_000_000, "uniform", vx.VX_PART_SAMPLE, max_slot=262_144, scratch=False)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs"])
+@pytest.mark.parametrize("part", [vx.VX_PART_SAMPLE, vx.VX_PART_LEARNED_PL])
+def test_out_of_core_sort_partition_regions(dist, part):
+    # a scratch with room for a region per partition: each partition is stored
+    # contiguously and loaded with one copy per column
+    st = _sort_case(256 << 20, 3_000_017, dist, part, max_slot=262_144, scratch="roomy")
+    assert st["contiguous_layout"] == 1 and st["n_partitions"] >= 12
+    assert st["spill_buffers"] == 0
+
+
+def test_out_of_core_sort_exact_scratch_uses_chunk_extents():
+    st = _sort_case(256 << 20, 1_000_003, "uniform", vx.VX_PART_SAMPLE, max_slot=262_144, scratch=True)
+    assert st["contiguous_layout"] == 0 and st["out_of_region_pairs"] == 0
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+def test_out_of_core_sort_region_overflow_and_spills(dist):
+    # a 200-key sample and 1 % headroom: many partitions outgrow their region,
+    # fill the overflow area and spill into buffers registered for the call;
+    # the output stays the stable sort
+    st = _sort_case(256 << 20, 3_000_017, dist, vx.VX_PART_SAMPLE, max_slot=262_144, scratch=False, sample=200,
+                    slack=1)
+    assert st["contiguous_layout"] == 1
+    assert st["out_of_region_pairs"] > 3_000_017 // 64
+    assert st["spill_buffers"] >= 1
