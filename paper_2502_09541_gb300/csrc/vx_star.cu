@@ -1704,7 +1704,7 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   }
   const uint64_t n_chunks = n_rows ? (n_rows + cr - 1) / cr : 0;
 
-  if (prep) {  // planning only: hand the query to another driver
+  if (prep) {  // planning only: hand the query to another executor
     prep->P = P;
     prep->acc = std::move(acc);
     prep->scratch = std::move(scratch);

@@ -179,7 +179,7 @@ struct GraphEntry {
 
 vx_status build_dim_table(vx_ctx *ctx, const DimSpec &d, BuiltDim *out, uint32_t *d_err, uint64_t *d_passed);
 vx_status check_err_word(vx_ctx *ctx, const uint32_t *d_err);
-// A planned star query ready to be executed chunk by chunk by another driver
+// A planned star query ready to be executed chunk by chunk by another executor
 // (the serving engine): kernel parameters (tables, predicates, roles, late
 // columns as zero-copy pointers), zeroed accumulators and the columns to stage.
 struct PreparedStar {
