@@ -1196,6 +1196,7 @@ struct StarExKernel : ExKernel {
   // per-slot events around the fused kernel (its own duration, immediate schedule)
   std::vector<cudaEvent_t> ev_a, ev_b, ev_c;  // fused kernel [a, b), gather [b, c)
   std::vector<uint8_t> ev_used;
+  bool graph_events = false;  // capturing: one event triple per chunk, recorded as graph nodes
   double ms_main = 0, ms_gather = 0;
   uint64_t main_launches = 0, launches = 0;
   ~StarExKernel() override {
@@ -1245,12 +1246,15 @@ struct StarExKernel : ExKernel {
     int threads = ctx->cfg.block_threads > 256 ? 256 : ctx->cfg.block_threads;
     int g = grid_for(ctx, (p.n + 7) / 8, threads);
     const size_t ek = ev_a.empty() ? 0 : it % ev_a.size();
-    const bool timed = !ev_a.empty() && ctx->cfg.sched == VX_SCHED_IMMEDIATE;
+    const bool timed = !ev_a.empty() && (graph_events || ctx->cfg.sched == VX_SCHED_IMMEDIATE);
+    auto rec = [&](cudaEvent_t e) {
+      return graph_events ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+    };
     if (chunk_has_late(it)) {  // filter/probe pass, then the late-column gather
       p.surv_list = (uint2 *)(slot + cols_bytes());
       p.surv_cnt = (unsigned int *)(slot + cols_bytes() + chunk_rows * 8);
       VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
-      if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
+      if (timed) VX_CUDA_TRY(rec(ev_a[ek]));
       const int kr = vec_width(p);
       if (kr) {
         VX_TRY((launch_vec<false, true>(ctx, p, kr, 0, s)));
@@ -1258,7 +1262,7 @@ struct StarExKernel : ExKernel {
         const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
         star_split_kernel<<<gs, 256, 0, s>>>(p);
       }
-      if (timed) VX_CUDA_TRY(cudaEventRecord(ev_b[ek], s));
+      if (timed) VX_CUDA_TRY(rec(ev_b[ek]));
       const int gg = ctx->num_sms * 4;
       if (smem) {
         static bool attr_g = false;
@@ -1274,13 +1278,13 @@ struct StarExKernel : ExKernel {
       VX_CUDA_TRY(cudaGetLastError());
       launches += 2;
       if (timed) {
-        VX_CUDA_TRY(cudaEventRecord(ev_c[ek], s));
-        ev_used[ek] = 2;
+        VX_CUDA_TRY(rec(ev_c[ek]));
+        if (!graph_events) ev_used[ek] = 2;
       }
       return VX_OK;
     }
     launches += 1;
-    if (timed) VX_CUDA_TRY(cudaEventRecord(ev_a[ek], s));
+    if (timed) VX_CUDA_TRY(rec(ev_a[ek]));
     const int kr = vec_width(p);
     if (kr) {  // vector path
       if (smem) {
@@ -1301,8 +1305,8 @@ struct StarExKernel : ExKernel {
     }
     VX_CUDA_TRY(cudaGetLastError());
     if (timed) {
-      VX_CUDA_TRY(cudaEventRecord(ev_b[ek], s));
-      ev_used[ek] = 1;
+      VX_CUDA_TRY(rec(ev_b[ek]));
+      if (!graph_events) ev_used[ek] = 1;
     }
     return VX_OK;
   }
@@ -1354,9 +1358,28 @@ vx_status star_graph(vx_ctx *ctx, StarExKernel &ek, const std::vector<std::share
   gp.err = e->err.as<uint32_t>();
   StarExKernel gk = ek;
   gk.proto = gp;
-  gk.ev_a.clear();  // the events belong to ek
-  gk.ev_b.clear();
   gk.ev_used.clear();
+  // the graph's own timing events (the entry owns them; gk only borrows them
+  // while capturing, and ek's belong to ek)
+  const uint64_t N = gk.size();
+  for (auto v : {&e->ev_a, &e->ev_b, &e->ev_c}) {
+    v->resize(N, nullptr);
+    for (uint64_t c = 0; c < N; ++c) VX_CUDA_TRY(cudaEventCreate(&(*v)[c]));
+  }
+  e->split.resize(N);
+  for (uint64_t c = 0; c < N; ++c) e->split[c] = gk.chunk_has_late(c) ? 1 : 0;
+  gk.ev_a = e->ev_a;
+  gk.ev_b = e->ev_b;
+  gk.ev_c = e->ev_c;
+  gk.graph_events = true;
+  struct Unborrow {
+    StarExKernel &k;
+    ~Unborrow() {
+      k.ev_a.clear();
+      k.ev_b.clear();
+      k.ev_c.clear();
+    }
+  } unborrow{gk};
   cudaStream_t s = ctx->s_compute;
   VX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   ExecStats est;
@@ -1791,6 +1814,17 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
   if (!ge && n_rows) VX_TRY(run_pipeline(ctx, ek, &es));
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
   VX_TRY(check_err_word(ctx, res_err));
+  if (ge) {  // the replay's fused-kernel and gather times, from its event nodes
+    for (size_t c = 0; c < ge->ev_a.size(); ++c) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, ge->ev_a[c], ge->ev_b[c]) == cudaSuccess) {
+        ek.ms_main += ms;
+        ek.main_launches += 1;
+      }
+      if (ge->split[c] && cudaEventElapsedTime(&ms, ge->ev_b[c], ge->ev_c[c]) == cudaSuccess) ek.ms_gather += ms;
+    }
+    cudaGetLastError();
+  }
   if (want_log && n_chunks && !ge) {  // statistics log: features and the exact survivor fraction per chunk
     std::vector<unsigned long long> sv(n_chunks);
     VX_CUDA_TRY(cudaMemcpy(sv.data(), P.chunk_surv, 8 * n_chunks, cudaMemcpyDeviceToHost));

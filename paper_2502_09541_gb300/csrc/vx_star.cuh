@@ -126,6 +126,7 @@ struct ChunkParams {
 };
 
 constexpr uint32_t kStarTileRows = 2048;  // rows of one block tile (256 threads x 8 rows)
+// ---- end of what the fused chunk kernel's device code reads
 
 // work item of the persistent multi-query kernel: rows [tile * kMultiTile,
 // (tile + 1) * kMultiTile) of query q's part of the staged chunk
@@ -172,8 +173,15 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   std::vector<std::shared_ptr<ResidentHT>> tables;
   uint64_t chunks = 0, bytes_h2d = 0, launches = 0;
+  // per chunk: events recorded as graph nodes around the fused kernel [a, b)
+  // and the late-column gather [b, c) (split chunks only), read after a replay
+  std::vector<cudaEvent_t> ev_a, ev_b, ev_c;
+  std::vector<uint8_t> split;
   ~GraphEntry() {
     if (exec) cudaGraphExecDestroy(exec);
+    for (auto v : {&ev_a, &ev_b, &ev_c})
+      for (cudaEvent_t e : *v)
+        if (e) cudaEventDestroy(e);
   }
 };
 
