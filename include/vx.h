@@ -225,11 +225,12 @@ typedef struct {
   uint32_t overflow_retries;
   double est_selectivity;  /* planner estimate used for the late/early decision */
   double ms_total;         /* wall time of the call */
-  double ms_kernel;        /* summed device time of the chunk kernels (CUDA events) */
+  double ms_kernel;        /* summed device time of the fused chunk kernels (CUDA events around each
+                              launch, as event nodes inside a captured graph) */
   uint64_t kernel_launches;/* kernels launched by the call */
   uint64_t late_chunks;    /* VX_LATE_PER_CHUNK: chunks whose aggregate columns were read by zero-copy */
   double ms_gather;        /* summed device time of the zero-copy gathers of late chunks (CUDA events;
-                              0 when not timed: graphs, DAG schedule, serving) */
+                              0 when not timed: DAG schedule, serving) */
   double ms_features;      /* wall time of the per-chunk feature pass before the pipeline (sampling
                               kernel, copy-back and the per-chunk decisions); 0 when it did not run */
 } vx_query_stats;
