@@ -673,7 +673,6 @@ struct PartitionPass : ExKernel {
   uint64_t *mid_keys;
   uint32_t *mid_vals;
   uint64_t *h_bnd;  // page-locked host, chunks x (P+1): chunk-local partition starts
-  int S;
   bool contig = false;
   uint64_t C = 0;                          // pairs of the intermediate
   std::vector<uint64_t> reg_off, reg_cap;  // contiguous layout
@@ -1000,7 +999,6 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
     pp.mid_keys = mid_keys;
     pp.mid_vals = mid_vals;
     pp.h_bnd = h_bnd;
-    pp.S = S;
     pp.contig = contig;
     pp.C = C;
     pp.reg_off = reg_off;
