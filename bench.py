@@ -618,6 +618,28 @@ def run_ours(args):
     }
     use_learned = learned_gbs >= plain_gbs
     host_gbs = learned_gbs if use_learned else plain_gbs
+
+    def step_roofline(stats_list, ms):
+        """Time the step's bytes need at the measured peaks (link: copy-engine
+        bytes plus zero-copy granules against the pinned H2D peak of this run;
+        HBM: each staged byte written by the copy engine and read by the fused
+        kernel) over the measured step time."""
+        link_b = sum(s["bytes_h2d"] + s["bytes_zero_copy"] for s in stats_list) / args.steps
+        hbm_b = 2 * sum(s["bytes_h2d"] for s in stats_list) / args.steps
+        t_link = link_b / (h2d_peak * 1e6)
+        t_hbm = hbm_b / (hbm_peak * 1e6)
+        return {"bound": "link" if t_link >= t_hbm else "hbm", "link_bytes": int(link_b), "hbm_bytes": int(hbm_b),
+                "link_peak_gbs": round(h2d_peak, 1), "hbm_peak_gbs": hbm_peak,
+                "roofline_ms": round(max(t_link, t_hbm), 3), "ms_per_step": round(ms, 3),
+                "link_gbs": round(link_b / (ms * 1e6), 1), "link_frac": round(link_b / (ms * 1e6) / h2d_peak, 4),
+                "frac": round(max(t_link, t_hbm) / ms, 4)}
+
+    forms["plain"]["step_roofline"] = step_roofline(stats_all, ms_step)
+    forms["learned"]["step_roofline"] = step_roofline(stats_l, ms_learned)
+    for fname, sl in (("plain", stats_all), ("learned", stats_l)):
+        forms[fname]["query_link_gbs"] = {
+            n: round(statistics.median((s["bytes_h2d"] + s["bytes_zero_copy"]) / (s["ms_total"] * 1e6)
+                                       for s in sl[i::len(TEMPLATES)]), 1) for i, n in enumerate(TEMPLATES)}
     cfg.use_graphs = 0
     cfg.chunk_bytes = 64 << 20
     cfg.n_slots = 3
@@ -653,6 +675,8 @@ def run_ours(args):
                                     "fused_of_ceiling": round(rf["achieved"] / ceil_gbs, 4)}
     roofline = roofline_learned if use_learned and roofline_learned["achieved"] else roofline_plain
     roofline["form"] = "learned" if roofline is roofline_learned else "plain"
+    # the step as a whole is bound by the host link: its roofline rides along
+    roofline["step"] = forms["learned" if use_learned else "plain"]["step_roofline"]
     forms["plain"]["roofline"] = {k: roofline_plain.get(k) for k in ("achieved", "frac", "avg_launch_us",
                                                                      "algorithmic_bytes_per_launch", "launch_ceiling")}
     forms["learned"]["roofline"] = {k: roofline_learned.get(k) for k in ("achieved", "frac", "avg_launch_us",
@@ -700,10 +724,37 @@ def run_ours(args):
         del fact
         line["sort"] = run_sort_extra(vx, G, args)
         line["join"] = run_join_extra(vx, G, args)
+    line["link_frac"] = line["link"]["link_frac"]
+    line["summary"] = summarize(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def summarize(line):
+    """The figures a reader needs first, repeated compactly as the line's last
+    key: both star forms with their link use, the out-of-core operators
+    learned vs plain, serving latency."""
+    f = line["forms"]
+    out = {"value": line["value"], "form": line["config"]["form"],
+           "star_gbs": {k: f[k]["value"] for k in ("plain", "learned")},
+           "star_link_frac": {k: f[k]["step_roofline"]["link_frac"] for k in ("plain", "learned")},
+           "star_step_roofline_frac": {k: f[k]["step_roofline"]["frac"] for k in ("plain", "learned")},
+           "fused_kernel_hbm_frac": line["roofline"].get("frac")}
+    sv = line.get("serving")
+    if sv:
+        out["serving_ms"] = {"p50": sv.get("p50_ms"), "p99": sv.get("p99_ms")}
+        if sv.get("rate_sweep"):
+            out["serving_sweep"] = [{"load": r["load"], "p50": r["p50_ms"], "p99": r["p99_ms"], "qps": r["qps"]}
+                                    for r in sv["rate_sweep"]]
+    so = line.get("sort")
+    if so:
+        out["sort_ms"] = {k: so[k]["ms"] for k in so if isinstance(so[k], dict) and "ms" in so[k]}
+    jo = line.get("join")
+    if jo:
+        out["join_ms"] = {k: jo[k]["ms"] for k in jo if isinstance(jo[k], dict) and "ms" in jo[k]}
+    return out
 
 
 def run_serve_only(args):

@@ -158,8 +158,9 @@ vx_status vx_filter(vx_ctx *ctx, const vx_pred *preds, int32_t n_preds, uint64_t
  *   - n_rows above 67,108,864 (2^26) returns VX_E_INVAL;
  *   - count > cap returns VX_E_CAPACITY after writing the first cap ids;
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress with that device current); make that first call
- *     before any stream capture;
+ *     (cudaGetSymbolAddress with that device current) and keeps it for the
+ *     life of the process, so the device must not be reset (cudaDeviceReset)
+ *     between calls; make that first call before any stream capture;
  *   - every call shares the one array, so calls whose work overlaps on the
  *     GPU (other streams, other host threads) race and give wrong results:
  *     serialise them. */

@@ -86,6 +86,10 @@ vx_status check_ctx(vx_ctx *ctx) {
     set_error("null context");
     return VX_E_INVAL;
   }
+  if (ctx->poisoned) {
+    set_error("context unusable: device work of an earlier call did not finish within its wait limit");
+    return VX_E_TIMEOUT;
+  }
   VX_CUDA_TRY(cudaSetDevice(ctx->device));
   return VX_OK;
 }
@@ -190,6 +194,21 @@ VX_API vx_status vx_close(vx_ctx *ctx) {
   if (!ctx) return VX_OK;
   cudaSetDevice(ctx->device);
   serve_shutdown(ctx);  // the engine thread takes the context lock: stop it first
+  bool leak = false;
+  {
+    std::lock_guard<std::recursive_mutex> g(ctx->mu);
+    leak = ctx->poisoned && !drain_streams(ctx);
+  }
+  if (leak) {
+    // device work that gave up on its wait is still running: the arena, the
+    // page-locked columns and the streams it may use are left as they are
+    // (never blocked on); only the host-side context is released
+    ctx->graphs.clear();
+    ctx->resident.clear();
+    ctx->cols.clear();
+    delete ctx;
+    return VX_E_TIMEOUT;
+  }
   {
     std::lock_guard<std::recursive_mutex> g(ctx->mu);
     if (ctx->s_compute) cudaStreamSynchronize(ctx->s_compute);

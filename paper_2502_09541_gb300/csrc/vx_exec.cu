@@ -5,13 +5,18 @@
 // on the device-to-host stream.  Two schedules:
 //   VX_SCHED_IMMEDIATE — a host loop issues a copy only when it can start at
 //     once (its slot is free and the previous user of the slot has finished),
-//     following the first design principle of Section 4.3, and keeps the
-//     device-to-host queue from running ahead of the host-to-device queue
-//     (the flow-control policy of Section 4.3); it waits with a 10 us back-off
-//     and a wall-clock limit.
+//     following the first design principle of Section 4.3.  A chunk's store is
+//     issued only once its kernel has completed, which in turn waited for its
+//     load, so the device-to-host queue can never drain ahead of the
+//     host-to-device queue (the flow-control policy of Section 4.3) and at
+//     most max_in_flight() chunks occupy the link at once.  The loop polls
+//     with a 10 us back-off (Section 4.3's retry period); the wall-clock limit
+//     wait_timeout_ms applies to the time since the last completed step, so a
+//     long operator that keeps making progress never times out.
 //   VX_SCHED_DAG — every copy and kernel is enqueued up front with stream and
 //     event dependencies (the baseline of Section 4.2).  Only operators whose
 //     outputs stay on the device use it.
+#include <algorithm>
 #include <thread>
 
 #include "vx_internal.h"
@@ -60,6 +65,34 @@ vx_status issue_copies(const std::vector<CopyOp> &ops, cudaMemcpyKind kind, cuda
 }
 
 }  // namespace
+
+bool drain_streams(vx_ctx *ctx) {
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t ss[3] = {ctx->s_compute, ctx->s_h2d, ctx->s_d2h};
+  bool ok = true;
+  for (int i = 0; i < 3; ++i)
+    if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev[i], ss[i]) != cudaSuccess)
+      ok = false;
+  const double limit = std::max<double>(ctx->cfg.wait_timeout_ms, kDrainLimitMs);
+  const double t0 = now_ms();
+  for (int i = 0; i < 3 && ok; ++i) {
+    while (true) {
+      cudaError_t q = cudaEventQuery(ev[i]);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady || now_ms() - t0 > limit) {
+        ok = false;
+        break;
+      }
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  if (!ok) ctx->poisoned = true;
+  return ok;
+}
 
 vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
   const uint64_t N = k.size();
@@ -110,8 +143,8 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
     return VX_OK;
   }
 
-  const double deadline = now_ms() + ctx->cfg.wait_timeout_ms;
-  uint64_t next_load = 0, next_retire = 0, loads_issued = 0, stores_issued = 0;
+  double last_progress = now_ms();
+  uint64_t next_load = 0, next_retire = 0;
   const uint64_t max_in_flight = (uint64_t)std::max(1, k.max_in_flight());
   while (next_retire < N) {
     bool progress = false;
@@ -131,7 +164,6 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
           VX_TRY(k.outputs(next_retire, base + (next_retire % S) * slot_bytes, ops));
           VX_TRY(issue_copies(ops, cudaMemcpyDeviceToHost, ctx->s_d2h, &st->bytes_d2h));
           VX_CUDA_TRY(cudaEventRecord(sl.ev_out, ctx->s_d2h));
-          ++stores_issued;
           sl.phase = 2;
         } else {
           sl.phase = 0;
@@ -149,9 +181,9 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
         break;
       }
     }
-    // load the next chunk when its slot is free and the copy engine queue is short;
-    // stores may not run ahead of loads (flow control)
-    if (next_load < N && next_load - next_retire < (uint64_t)S && stores_issued <= loads_issued) {
+    // load the next chunk when its slot is free and fewer than max_in_flight
+    // chunks are loaded, computing or storing
+    if (next_load < N && next_load - next_retire < (uint64_t)S) {
       SlotState &sl = es.s[next_load % S];
       if (sl.phase == 0 && next_load - next_retire < max_in_flight) {
         char *slot = base + (next_load % S) * slot_bytes;
@@ -167,17 +199,18 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
         sl.chunk = (int64_t)next_load;
         sl.phase = 1;
         ++next_load;
-        ++loads_issued;
         progress = true;
       }
     }
-    if (!progress) {
-      if (now_ms() > deadline) {
-        set_error("executor: wait limit of %u ms expired at chunk %llu of %llu", ctx->cfg.wait_timeout_ms,
-                  (unsigned long long)next_retire, (unsigned long long)N);
-        cudaStreamSynchronize(ctx->s_compute);
-        cudaStreamSynchronize(ctx->s_h2d);
-        cudaStreamSynchronize(ctx->s_d2h);
+    if (progress) {
+      last_progress = now_ms();
+    } else {
+      if (now_ms() - last_progress > ctx->cfg.wait_timeout_ms) {
+        set_error("executor: no chunk completed a step within the wait limit of %u ms (at chunk %llu of %llu)",
+                  ctx->cfg.wait_timeout_ms, (unsigned long long)next_retire, (unsigned long long)N);
+        // the ring goes back to the arena only once the work already issued
+        // into it has finished; that drain is bounded too
+        if (!drain_streams(ctx)) ring.arena = nullptr;
         return VX_E_TIMEOUT;
       }
       std::this_thread::sleep_for(std::chrono::microseconds(10));

@@ -143,6 +143,10 @@ struct vx_ctx {
   float reg_w[8] = {0};
   bool reg_trained = false;
   void *serve = nullptr;  // serving engine (vx_serve_start .. vx_serve_stop)
+  // set when device work of a call that gave up on a wait did not finish
+  // within the drain limit either: the arena blocks that work may still write
+  // are never handed out again, and every later call fails
+  bool poisoned = false;
 };
 
 namespace vx {
@@ -192,6 +196,13 @@ struct ExecStats {
 // Runs all chunks of `k` through a ring of cfg.n_slots staging slots allocated
 // from the arena (Section 5.3 pipelined executor).
 vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st);
+
+// Waits, without blocking on the device, until the work already issued on the
+// context's three streams has finished, for at most max(wait_timeout_ms,
+// kDrainLimitMs).  Returns false (and marks the context poisoned) if it had
+// not finished by then.
+constexpr double kDrainLimitMs = 10000;
+bool drain_streams(vx_ctx *ctx);
 
 // Enqueues every chunk of `k` as a stream/event DAG into a caller-owned ring
 // while the compute stream is being captured: the copy stream is forked from

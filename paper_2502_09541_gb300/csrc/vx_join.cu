@@ -423,7 +423,13 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
       if ((h.err & ERR_HT_FULL) || h.inserted > (uint64_t)(0.95 * cap)) {
         // the table overflowed its load limit: rebuild larger (learned sizing's retry)
         res.overflow_retries += 1;
-        cap = ((uint64_t)std::ceil(h.inserted / o.load_factor) + 4096) / kJoinBucket * kJoinBucket;
+        // at least double: an overflow from the probe-walk limit (clustered
+        // homes) is not cured by a table sized for the same load again; the
+        // last attempt takes the largest table that fits
+        const uint64_t need = (uint64_t)std::ceil(h.inserted / o.load_factor) + 4096;
+        uint64_t grow = std::max<uint64_t>(2 * cap, need);
+        if (grow > slots_max && need <= slots_max && cap < slots_max) grow = slots_max;
+        cap = grow / kJoinBucket * kJoinBucket;
         if (attempt >= 3) {
           set_error("vx_join: table sizing did not converge");
           return VX_E_NOMEM;

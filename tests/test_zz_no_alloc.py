@@ -1,5 +1,6 @@
 """The allocation-free filter entry point (vx_filter_device_static) against
-the allocating one (vx_filter), through the C ABI, on two calls in a row.
+the allocating one (vx_filter) and the oracle's filter, through the C ABI, on
+two calls in a row.
 
 The entry point serves callers that cannot let a library allocate device
 memory (a host framework's memory manager owns all of it, or a cudaMalloc
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import datagen as G
+import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +52,9 @@ def test_static_filter_matches_allocating_filter_twice():
     ]
     for preds in calls:
         exp = _reference(cols, preds, n)
+        # the allocating entry point agrees with the oracle's definition (Section 6.3 selection)
+        want = O.filter_rows([(cols[c], op, lo, hi) for c, op, lo, hi in preds], n)
+        assert np.array_equal(exp, want)
         out.fill_(-1)
         torch.cuda.synchronize()
         st, cnt = vx.vx_filter_device_static([t.data_ptr() for t in dev], preds, n, 0, out.data_ptr(), n)
