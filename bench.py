@@ -559,6 +559,17 @@ def run_ours(args):
     for i, n in enumerate(TEMPLATES):
         per_q_ms[n] = round(statistics.median(s["ms_total"] for s in stats_all[i::len(TEMPLATES)]), 3)
 
+    # copy / compute overlap of one run of every template (per-chunk CUDA
+    # events on the copy and compute streams), outside the timed steps
+    cfg.log_timeline = 1
+    vx.vx_set_config(ctx, cfg)
+    overlap = {}
+    for i, n in enumerate(TEMPLATES):
+        st_, _, _, _, qs = vx.vx_run_plan(ctx, plans[i])
+        overlap[n] = timeline_summary(vx.vx_last_timeline(ctx), qs["bytes_h2d"])
+    cfg.log_timeline = 0
+    vx.vx_set_config(ctx, cfg)
+
     # dominant kernel: the fused chunk kernel; algorithmic HBM bytes = staged
     # column bytes it reads (rows x staged columns x 4), over its own CUDA-event
     # time (immediate schedule: events around each launch; captured graphs:
@@ -701,6 +712,7 @@ def run_ours(args):
                  "link_frac": round(link_gbs / h2d_peak, 4), "host_frac": round(host_gbs / world / h2d_peak, 4)},
         "rows_per_s": round(rows_step * world / (ms_step / 1000)),
         "query_ms": per_q_ms,
+        "overlap": overlap,
         "call_overhead_ms": round(statistics.median(s["host_ms"] - s["ms_total"] for s in stats_all), 3),
         "roofline": roofline, "roofline_zero_copy_gather": gather,
         "e2e": {"value": round(e2e_gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": int(e2e_h2d),
@@ -730,6 +742,30 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def timeline_summary(tl, bytes_h2d):
+    """Copy / compute overlap of one pipeline from its per-chunk timeline
+    (columns: chunk, issue, h2d start/end, kernel start/end, d2h start/end;
+    ms).  Copies of one stream run one after another, so their busy time is
+    the sum of their durations; gaps are idle link time between them."""
+    if len(tl) == 0:
+        return None
+    h0, h1, k0, k1 = tl[:, 2], tl[:, 3], tl[:, 4], tl[:, 5]
+    wall = float(max(k1.max(), h1.max()) - h0.min())
+    dur = h1 - h0
+    per_chunk = bytes_h2d / len(tl)
+    gbs = per_chunk / np.maximum(dur, 1e-6) / 1e6
+    gaps = np.maximum(h0[1:] - h1[:-1], 0) if len(tl) > 1 else np.zeros(0)
+    # kernel time hidden under copies: kernel c overlaps copy c+1
+    hidden = sum(max(0.0, min(k1[c], h1[c + 1]) - max(k0[c], h0[c + 1])) for c in range(len(tl) - 1))
+    return {"chunks": int(len(tl)), "wall_ms": round(wall, 3), "link_busy": round(float(dur.sum()) / wall, 4),
+            "chunk_copy_gbs": {"min": round(float(gbs.min()), 1), "median": round(float(np.median(gbs)), 1),
+                               "max": round(float(gbs.max()), 1)},
+            "gap_ms": {"sum": round(float(gaps.sum()), 3), "max": round(float(gaps.max()) if len(gaps) else 0.0, 3)},
+            "kernel_ms": round(float((k1 - k0).sum()), 3),
+            "kernel_hidden_frac": round(hidden / max(float((k1 - k0)[:-1].sum()), 1e-9), 4),
+            "tail_ms": round(float(k1[-1] - h1[-1]), 3)}
 
 
 def summarize(line):

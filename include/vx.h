@@ -81,7 +81,8 @@ typedef struct {
   uint32_t wait_timeout_ms; /* limit of every host-side wait (default 60000) */
   int32_t log_chunk_stats;  /* vx_run_plan logs per-chunk features and survivor fractions (the
                                cardinality regressor's training data); not with use_graphs */
-  int32_t reserved;
+  int32_t log_timeline;     /* the immediate schedule records when every chunk's copies and kernel
+                               ran (vx_last_timeline); not with use_graphs */
 } vx_config;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -299,8 +300,25 @@ vx_status vx_drop_resident(vx_ctx *ctx);
 /* Statistics of the last completed call on this context. */
 vx_status vx_last_stats(vx_ctx *ctx, vx_query_stats *out);
 
+/* Per-chunk timeline of the last pipeline the immediate schedule ran with
+ * log_timeline set (the copy / compute overlap of Section 5.3's executor,
+ * measured with CUDA events on the copy and compute streams).  Row c of
+ * VX_TIMELINE_COLS floats: chunk index, host time the chunk's loads were
+ * issued, then start and end of its host-to-device copies, of its kernel and
+ * of its device-to-host copies (-1 when it had none); times in ms from the
+ * start of the pipeline.  Copies up to cap rows to out (row-major); *n =
+ * rows recorded. */
+#define VX_TIMELINE_COLS 8
+vx_status vx_last_timeline(vx_ctx *ctx, float *out, uint64_t cap, uint64_t *n);
+
 /* ---------------------------------------------------------------- sort */
 enum { VX_PART_SAMPLE = 0, VX_PART_LEARNED_PL = 1, VX_PART_LEARNED_MLP = 2 };
+/* Sort plans.  PARTITION: range-partition, then sort each partition (pass 1
+ * needs splitters: sample or learned).  MERGE: Section 6.1's SortExKernel then
+ * MergeExKernel: sort each contiguous chunk into a sorted run, cut the runs
+ * into partitions at exact ranks (binary search over the runs, no sample, no
+ * imbalance), merge each partition's segments; `partitioner` is not used. */
+enum { VX_SORT_PARTITION = 0, VX_SORT_MERGE = 1 };
 
 typedef struct {
   int32_t partitioner;        /* VX_PART_*: how the range partition's splitters are chosen */
@@ -320,7 +338,9 @@ typedef struct {
                                  bytes (stats: contiguous_layout) */
   uint64_t host_scratch_bytes;
   uint64_t max_slot_pairs;    /* optional cap on the pairs per staging slot (0 = from the arena) */
-  uint64_t *splitters_out;    /* optional: receives the P-1 top-level splitters */
+  uint64_t *splitters_out;    /* optional: receives the P-1 top-level splitters (PARTITION plan) */
+  int32_t plan;               /* VX_SORT_PARTITION (default) or VX_SORT_MERGE */
+  int32_t reserved;
 } vx_sort_opts;
 
 typedef struct {
@@ -338,20 +358,29 @@ typedef struct {
                                       spill buffers) */
   uint64_t spill_buffers;          /* host buffers registered for the call when the overflow area
                                       ran out */
+  uint32_t plan;                   /* VX_SORT_* that ran */
+  uint32_t n_runs;                 /* MERGE: sorted runs written by pass 1 */
+  double ms_merge_kernel;          /* MERGE: device time of the merge rounds (CUDA events) */
+  uint64_t merge_pass_pairs;       /* MERGE: pairs x executed merge rounds */
 } vx_sort_stats;
 
 /* Out-of-core sort of (uint64 key, uint32 row id) pairs held in two registered
  * host columns (Section 6.1 sorts 64-bit integers larger than device memory).
  * The output is the stable sort by key (equal keys keep input order) written
  * to out_keys/out_rowids (n elements each, caller-owned host memory).
- * Pass 1 range-partitions the input chunk by chunk into a host intermediate
- * with per-chunk boundary arrays (Section 6.2.1); pass 2 gathers each
- * partition's extents, radix-sorts it in HBM and stores it at its final
- * offset (Section 5.3 pipeline for both).  Splitters come from a sorted key
- * sample (VX_PART_SAMPLE) or from a learned monotone CDF model: a
+ * PARTITION plan: pass 1 range-partitions the input chunk by chunk into a
+ * host intermediate with per-chunk boundary arrays (Section 6.2.1); pass 2
+ * gathers each partition's extents, radix-sorts it in HBM and stores it at
+ * its final offset (Section 5.3 pipeline for both).  Splitters come from a
+ * sorted key sample (VX_PART_SAMPLE) or from a learned monotone CDF model: a
  * 1,024-segment piecewise-linear model (VX_PART_LEARNED_PL) or a 1-32-1 MLP
- * trained on the device (VX_PART_LEARNED_MLP).  Any splitters give the same
- * output; they decide only where to cut. */
+ * trained on the device (VX_PART_LEARNED_MLP).  MERGE plan (opts->plan): pass
+ * 1 radix-sorts each contiguous chunk into a sorted run of the intermediate;
+ * the runs are cut at exact ranks (vx_exact_splits) into equal partitions;
+ * pass 2 loads each partition's run segments and merges them (vx_merge_runs).
+ * Both plans and any splitters give the same output; they decide only where
+ * to cut.  The intermediate is opts->host_scratch when it holds 12 n bytes,
+ * else allocated for the call. */
 vx_status vx_sort(vx_ctx *ctx, int32_t key_col, int32_t rowid_col, uint64_t *out_keys, uint32_t *out_rowids,
                   const vx_sort_opts *opts, vx_sort_stats *stats);
 
@@ -379,6 +408,30 @@ vx_status vx_range_partition(vx_ctx *ctx, const uint64_t *keys, const uint32_t *
  * the count. */
 vx_status vx_sort_splitters(vx_ctx *ctx, int32_t key_col, int32_t partitioner, uint32_t n_partitions,
                             uint64_t sample_size, uint64_t seed, uint64_t *splitters_out, uint32_t *n_out);
+
+/* Exact cut of sorted runs (the data mapping of Section 6.1's MergeExKernel:
+ * regroup N sorted chunks into partitions with max(P_i) <= min(P_i+1)).  The
+ * runs are n_runs consecutive sorted pieces of `keys` (host memory, run r =
+ * [run_off[r], run_off[r+1]), run_off has n_runs + 1 entries starting at 0);
+ * for each target rank k = ranks[q] writes out[q * n_runs + r] = how many
+ * elements of run r precede the element of rank k in the stable order (by
+ * key, then by position in `keys`), so the cut takes exactly k elements and
+ * every element left of it orders before every element right of it.  A rank
+ * >= the total takes every run whole.  Works on the device: a fence per 4,096
+ * keys of every run in HBM, then per rank a binary search over the key value
+ * whose counts read the runs through mapped host memory.  n_runs <= 256.
+ * Runs that are not sorted give cuts of no meaning but stay within bounds. */
+vx_status vx_exact_splits(vx_ctx *ctx, const uint64_t *keys, const uint64_t *run_off, uint32_t n_runs,
+                          const uint64_t *ranks, uint32_t n_ranks, uint64_t *out);
+
+/* In-HBM stable merge of n_runs sorted runs of (key, value) pairs given
+ * back to back in host buffers (run r = [run_off[r], run_off[r+1])): the
+ * per-partition kernel of Section 6.1's MergeExKernel, pairwise merge-path
+ * merges in rounds over a double buffer, ties taken from the earlier run.
+ * Writes the merged pairs to out_keys/out_vals; the input must fit the arena
+ * twice over.  n_runs <= 256. */
+vx_status vx_merge_runs(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, const uint64_t *run_off,
+                        uint32_t n_runs, uint64_t *out_keys, uint32_t *out_vals);
 
 /* ---------------------------------------------------------------- join */
 typedef struct {

@@ -3,7 +3,8 @@
 Plain CPU definitions of every result of the out-of-core query hot path
 (Vortex, arXiv 2502.09541): the single-dimension and star join queries
 (Section 7.1), filter with stream compaction (Section 6.3), the stable sort of
-(key, row id) pairs (Section 6.1), the equi-join with count / payload checksum
+(key, row id) pairs (Section 6.1) and the exact cut of sorted runs that its
+merge plan partitions by, the equi-join with count / payload checksum
 / pair fingerprint (Section 6.2), find_boundary (Section 6.2.1, Fig. 9), range
 partitioning, sample and piecewise-linear CDF splitters, the monotone CDF MLP
 (fp64 forward/backward and Adam), the per-chunk cardinality regressor (fp64
@@ -107,6 +108,7 @@ def lib():
                 "or_adam_step": ([vp, vp, vp, vp, ci, ci, dbl, dbl, dbl, dbl], None),
                 "or_zero_copy_threshold": ([dbl, dbl, dbl, dbl], dbl),
                 "or_isolate_splitters": ([vp, u32, vp, u64, u32, vp], u32),
+                "or_exact_cut": ([vp, vp, u32, u64, vp], ci),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -247,6 +249,18 @@ def sort_pairs(keys, rowids):
     if st:
         raise RuntimeError(f"or_sort_pairs status {st}")
     return ok, orr
+
+
+def exact_cut(keys, run_off, k):
+    """Per run, how many of the first k elements of the stable order (by key,
+    then position) lie in it (Section 6.1 merge data mapping)."""
+    keys = _c(keys, np.uint64)
+    ro = _c(run_off, np.uint64)
+    out = np.zeros(len(ro) - 1, np.uint64)
+    st = lib().or_exact_cut(_p(keys), _p(ro), len(ro) - 1, int(k), _p(out))
+    if st:
+        raise RuntimeError(f"or_exact_cut status {st}")
+    return out
 
 
 def pair_fp(probe_row, payload):

@@ -243,6 +243,29 @@ OR_EXPORT int or_sort_pairs(const uint64_t *keys, const uint32_t *rowids, uint64
   return 0;
 }
 
+/* Exact cut of sorted runs (Section 6.1, MergeExKernel data mapping: regroup
+ * sorted chunks into partitions with max(P_i) <= min(P_i+1)).  The runs are
+ * consecutive pieces [run_off[r], run_off[r+1]) of keys.  Definition: order
+ * all n keys stably (by key, then by position), take the first k of that
+ * order, and count how many of them lie in each run.  k >= n takes every
+ * element. */
+OR_EXPORT int or_exact_cut(const uint64_t *keys, const uint64_t *run_off, uint32_t n_runs, uint64_t k,
+                           uint64_t *out) {
+  const uint64_t n = run_off[n_runs];
+  uint64_t *idx = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+  if (!idx) return OR_E_NOMEM;
+  for (uint64_t i = 0; i < n; ++i) idx[i] = i;
+  qsort_r(idx, n, sizeof(uint64_t), cmp_ki, (void *)keys);
+  for (uint32_t r = 0; r < n_runs; ++r) out[r] = 0;
+  for (uint64_t i = 0; i < k && i < n; ++i) {
+    uint32_t r = 0;
+    while (idx[i] >= run_off[r + 1]) ++r;
+    out[r] += 1;
+  }
+  free(idx);
+  return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* SplitMix64 output finalizer (Steele, Lea & Flood 2014): the mixing function
  * of the join pair fingerprint. */

@@ -44,7 +44,7 @@ class vx_config(ctypes.Structure):
                 ("late_mat", ctypes.c_int32), ("zc_threshold", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("wait_timeout_ms", ctypes.c_uint32), ("log_chunk_stats", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("log_timeline", ctypes.c_int32)]
 
 
 class vx_pred(ctypes.Structure):
@@ -89,13 +89,15 @@ class vx_result(ctypes.Structure):
 
 
 VX_PART_SAMPLE, VX_PART_LEARNED_PL, VX_PART_LEARNED_MLP = 0, 1, 2
+VX_SORT_PARTITION, VX_SORT_MERGE = 0, 1
 
 
 class vx_sort_opts(ctypes.Structure):
     _fields_ = [("partitioner", ctypes.c_int32), ("n_partitions", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("sample_size", ctypes.c_uint64), ("mlp_steps", ctypes.c_uint32), ("region_slack_pct", ctypes.c_uint32),
                 ("host_scratch", ctypes.c_void_p), ("host_scratch_bytes", ctypes.c_uint64),
-                ("max_slot_pairs", ctypes.c_uint64), ("splitters_out", ctypes.c_void_p)]
+                ("max_slot_pairs", ctypes.c_uint64), ("splitters_out", ctypes.c_void_p), ("plan", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class vx_sort_stats(ctypes.Structure):
@@ -107,7 +109,8 @@ class vx_sort_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("bytes_h2d", ctypes.c_uint64), ("bytes_d2h", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("ms_sort_kernel", ctypes.c_double),
                 ("radix_pass_pairs", ctypes.c_uint64), ("out_of_region_pairs", ctypes.c_uint64),
-                ("spill_buffers", ctypes.c_uint64)]
+                ("spill_buffers", ctypes.c_uint64), ("plan", ctypes.c_uint32), ("n_runs", ctypes.c_uint32),
+                ("ms_merge_kernel", ctypes.c_double), ("merge_pass_pairs", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -163,6 +166,7 @@ SIGNATURES = {
     "vx_run_plan": ([_vp, _P(vx_plan), _P(vx_result)], _i32),
     "vx_groupby": ([_vp, _P(vx_plan_gkey), _i32, _i32, _i32, _i32, _P(vx_pred), _i32, _P(vx_result)], _i32),
     "vx_last_stats": ([_vp, _P(vx_query_stats)], _i32),
+    "vx_last_timeline": ([_vp, _vp, _u64, _P(_u64)], _i32),
     "vx_drop_resident": ([_vp], _i32),
     "vx_probe_link": ([_vp, _u64, _u64, _P(_dbl), _P(_dbl), _P(_dbl)], _i32),
     "vx_probe_hbm_random": ([_vp, _u64, _u64, _P(_dbl)], _i32),
@@ -186,6 +190,8 @@ SIGNATURES = {
     "vx_wait": ([_vp, _u64, _P(vx_result), _u32], _i32),
     "vx_serve_stats_get": ([_vp, _P(vx_serve_stats)], _i32),
     "vx_serve_stop": ([_vp], _i32),
+    "vx_exact_splits": ([_vp, _vp, _vp, _u32, _vp, _u32, _vp], _i32),
+    "vx_merge_runs": ([_vp, _vp, _vp, _vp, _u32, _vp, _vp], _i32),
     "vx_filter_device_static": ([_vp, _i32, _P(vx_pred), _i32, _u64, _u64, _vp, _u64, _P(_u64), _vp], _i32),
 }
 
@@ -398,6 +404,19 @@ def vx_autotune(ctx, plan: vx_plan, sample_rows: int) -> vx_config:
     return c
 
 
+TIMELINE_COLS = ("chunk", "issue", "h2d_start", "h2d_end", "kernel_start", "kernel_end", "d2h_start", "d2h_end")
+
+
+def vx_last_timeline(ctx) -> np.ndarray:
+    """(chunks, 8) float32 rows: chunk, load issue, h2d start/end, kernel
+    start/end, d2h start/end in ms from the pipeline's start (-1: none)."""
+    n = ctypes.c_uint64()
+    _check(load().vx_last_timeline(ctx, None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, len(TIMELINE_COLS)), np.float32)
+    _check(load().vx_last_timeline(ctx, out.ctypes.data, n.value, ctypes.byref(n)))
+    return out
+
+
 def vx_last_stats(ctx) -> dict:
     s = vx_query_stats()
     _check(load().vx_last_stats(ctx, ctypes.byref(s)))
@@ -483,6 +502,28 @@ def vx_sort_splitters(ctx, key_col: int, partitioner: int, n_partitions: int, sa
     _check(load().vx_sort_splitters(ctx, key_col, partitioner, n_partitions, sample_size, seed, out.ctypes.data,
                                     ctypes.byref(k)))
     return out[:k.value].copy()
+
+
+def vx_exact_splits(ctx, keys, run_off, ranks):
+    """Per rank, the elements of each sorted run left of the exact cut:
+    array (len(ranks), n_runs)."""
+    keys = _np(keys, np.uint64)
+    ro = _np(run_off, np.uint64)
+    rk = _np(ranks, np.uint64)
+    out = np.zeros((len(rk), len(ro) - 1), np.uint64)
+    _check(load().vx_exact_splits(ctx, keys.ctypes.data, ro.ctypes.data, len(ro) - 1,
+                                  rk.ctypes.data if len(rk) else None, len(rk), out.ctypes.data))
+    return out
+
+
+def vx_merge_runs(ctx, keys, vals, run_off):
+    """Stable in-HBM merge of the sorted runs [run_off[r], run_off[r+1])."""
+    keys, vals = _np(keys, np.uint64), _np(vals, np.uint32)
+    ro = _np(run_off, np.uint64)
+    ok, ov = np.empty_like(keys), np.empty_like(vals)
+    _check(load().vx_merge_runs(ctx, keys.ctypes.data, vals.ctypes.data, ro.ctypes.data, len(ro) - 1,
+                                ok.ctypes.data, ov.ctypes.data))
+    return ok, ov
 
 
 def vx_mlp_loss_grad(ctx, theta, H, x, t):

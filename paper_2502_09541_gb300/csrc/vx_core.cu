@@ -331,6 +331,19 @@ VX_API vx_status vx_last_stats(vx_ctx *ctx, vx_query_stats *out) {
   return VX_OK;
 }
 
+VX_API vx_status vx_last_timeline(vx_ctx *ctx, float *out, uint64_t cap, uint64_t *n) {
+  clear_error();
+  if (!ctx || !n || (cap && !out)) {
+    set_error("vx_last_timeline: bad argument");
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  const uint64_t rows = ctx->timeline.size() / VX_TIMELINE_COLS;
+  *n = rows;
+  if (cap) memcpy(out, ctx->timeline.data(), sizeof(float) * VX_TIMELINE_COLS * std::min(cap, rows));
+  return VX_OK;
+}
+
 // ------------------------------------------------------------------ zero-copy probe
 // The Section 6.3 micro-benchmark: sum += pred[i % npred] % SEL == 0 ? v[i] : 0
 // with pred in device memory and v in host memory, read either through mapped

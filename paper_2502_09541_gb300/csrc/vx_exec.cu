@@ -29,19 +29,30 @@ struct SlotState {
   int64_t chunk = -1;
   int phase = 0;  // 0 free, 1 kernel issued, 2 storing
   cudaEvent_t ev_in = nullptr, ev_k0 = nullptr, ev_k = nullptr, ev_out = nullptr;
+  // timeline (log_timeline): timed events around the chunk's copies
+  cudaEvent_t ev_h0 = nullptr, ev_h1 = nullptr, ev_d0 = nullptr, ev_d1 = nullptr;
+  float issue_ms = 0;
 };
 
 struct EventSet {
   std::vector<SlotState> s;
+  cudaEvent_t ref = nullptr;  // timeline origin
   ~EventSet() {
-    for (auto &x : s) {
-      if (x.ev_in) cudaEventDestroy(x.ev_in);
-      if (x.ev_k0) cudaEventDestroy(x.ev_k0);
-      if (x.ev_k) cudaEventDestroy(x.ev_k);
-      if (x.ev_out) cudaEventDestroy(x.ev_out);
-    }
+    for (auto &x : s)
+      for (cudaEvent_t e : {x.ev_in, x.ev_k0, x.ev_k, x.ev_out, x.ev_h0, x.ev_h1, x.ev_d0, x.ev_d1})
+        if (e) cudaEventDestroy(e);
+    if (ref) cudaEventDestroy(ref);
   }
 };
+
+float since(cudaEvent_t ref, cudaEvent_t e) {
+  float ms = -1;
+  if (cudaEventElapsedTime(&ms, ref, e) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return ms;
+}
 
 // A copy over the host link runs at full rate only when its host address
 // starts on a 512-byte boundary: measured on this link, 12 GB each way with
@@ -119,6 +130,16 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
   }
   std::vector<CopyOp> ops;
   const bool dag = ctx->cfg.sched == VX_SCHED_DAG && !k.has_outputs();
+  const bool tl = ctx->cfg.log_timeline && !dag;
+  double t_origin = 0;
+  if (tl) {
+    ctx->timeline.clear();
+    for (auto &x : es.s)
+      for (cudaEvent_t *e : {&x.ev_h0, &x.ev_h1, &x.ev_d0, &x.ev_d1}) VX_CUDA_TRY(cudaEventCreate(e));
+    VX_CUDA_TRY(cudaEventCreate(&es.ref));
+    VX_CUDA_TRY(cudaEventRecord(es.ref, ctx->s_h2d));
+    t_origin = now_ms();
+  }
 
   if (dag) {
     for (uint64_t it = 0; it < N; ++it) {
@@ -159,10 +180,18 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
         if (cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k) == cudaSuccess) st->ms_kernel += ms;
         cudaGetLastError();
         k.on_retire(next_retire);
+        if (tl) {
+          const float row[VX_TIMELINE_COLS] = {(float)next_retire, sl.issue_ms, since(es.ref, sl.ev_h0),
+                                               since(es.ref, sl.ev_h1), since(es.ref, sl.ev_k0),
+                                               since(es.ref, sl.ev_k), -1.f, -1.f};
+          ctx->timeline.insert(ctx->timeline.end(), row, row + VX_TIMELINE_COLS);
+        }
         if (k.has_outputs()) {
           ops.clear();
           VX_TRY(k.outputs(next_retire, base + (next_retire % S) * slot_bytes, ops));
+          if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_d0, ctx->s_d2h));
           VX_TRY(issue_copies(ops, cudaMemcpyDeviceToHost, ctx->s_d2h, &st->bytes_d2h));
+          if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_d1, ctx->s_d2h));
           VX_CUDA_TRY(cudaEventRecord(sl.ev_out, ctx->s_d2h));
           sl.phase = 2;
         } else {
@@ -174,6 +203,11 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
         cudaError_t q = cudaEventQuery(sl.ev_out);
         if (q == cudaErrorNotReady) break;
         VX_CUDA_TRY(q);
+        if (tl) {  // this chunk's row is the last one recorded so far
+          float *row = &ctx->timeline[ctx->timeline.size() - VX_TIMELINE_COLS];
+          row[6] = since(es.ref, sl.ev_d0);
+          row[7] = since(es.ref, sl.ev_d1);
+        }
         sl.phase = 0;
         ++next_retire;
         progress = true;
@@ -189,7 +223,12 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
         char *slot = base + (next_load % S) * slot_bytes;
         ops.clear();
         k.inputs(next_load, slot, ops);
+        if (tl) {
+          sl.issue_ms = (float)(now_ms() - t_origin);
+          VX_CUDA_TRY(cudaEventRecord(sl.ev_h0, ctx->s_h2d));
+        }
         VX_TRY(issue_copies(ops, cudaMemcpyHostToDevice, ctx->s_h2d, &st->bytes_h2d));
+        if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_h1, ctx->s_h2d));
         VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
         VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
         VX_CUDA_TRY(cudaEventRecord(sl.ev_k0, ctx->s_compute));

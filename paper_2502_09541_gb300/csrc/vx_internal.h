@@ -147,6 +147,9 @@ struct vx_ctx {
   // within the drain limit either: the arena blocks that work may still write
   // are never handed out again, and every later call fails
   bool poisoned = false;
+  // per-chunk timeline of the last pipeline run with log_timeline (rows of
+  // VX_TIMELINE_COLS floats)
+  std::vector<float> timeline;
 };
 
 namespace vx {

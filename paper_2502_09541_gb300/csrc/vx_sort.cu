@@ -469,6 +469,12 @@ __global__ void isolate_splitters_kernel(const uint64_t *raw, uint32_t n_raw, co
 
 // ================================================================== host helpers
 
+vx_status radix_publish_enqueue(char *temp, uint64_t *host_word, cudaStream_t s) {
+  rx_publish<<<1, 1, 0, s>>>(radix_state_of(temp), 8, host_word);
+  VX_CUDA_TRY(cudaGetLastError());
+  return VX_OK;
+}
+
 static uint32_t ntiles_of(uint64_t n) { return (uint32_t)((n + kRxTile - 1) / kRxTile); }
 
 // temp layout: [RadixState | 8 byte histograms (u64) | per-tile region]; the
@@ -1142,7 +1148,7 @@ VX_API vx_status vx_sort(vx_ctx *ctx, int32_t key_col, int32_t rowid_col, uint64
   vx_sort_opts o{};
   if (opts) o = *opts;
   if (o.partitioner < VX_PART_SAMPLE || o.partitioner > VX_PART_LEARNED_MLP || o.n_partitions < 0 ||
-      o.n_partitions > 256) {
+      o.n_partitions > 256 || (o.plan != VX_SORT_PARTITION && o.plan != VX_SORT_MERGE)) {
     set_error("vx_sort: bad options");
     return VX_E_INVAL;
   }
@@ -1152,8 +1158,11 @@ VX_API vx_status vx_sort(vx_ctx *ctx, int32_t key_col, int32_t rowid_col, uint64
   VX_TRY(r2.add(out_rowids, 4 * n));
   vx_sort_stats ss{};
   double t0 = now_ms();
-  vx_status st = sort_contiguous(ctx, (const uint64_t *)kc->host, (const uint32_t *)vc->host,
-                                 (const uint64_t *)kc->dev, n, out_keys, out_rowids, o, ss, 0);
+  vx_status st = o.plan == VX_SORT_MERGE
+                     ? merge_sort_plan(ctx, (const uint64_t *)kc->host, (const uint32_t *)vc->host, n, out_keys,
+                                       out_rowids, o, ss)
+                     : sort_contiguous(ctx, (const uint64_t *)kc->host, (const uint32_t *)vc->host,
+                                       (const uint64_t *)kc->dev, n, out_keys, out_rowids, o, ss, 0);
   ss.ms_total = now_ms() - t0;
   if (stats) *stats = ss;
   return st;

@@ -231,6 +231,67 @@ def test_sort_special_cases():
     assert ok.tolist() == [0, 1, 2**63, 2**64 - 1]  # unsigned order
 
 
+# ------------------------------------------------------------------ exact cut of sorted runs
+def _runs(dist, n, n_runs, seed=0):
+    """n keys as n_runs consecutive runs, each sorted (stable, so equal keys
+    keep their input order), as the sort-merge plan's first pass leaves them."""
+    k, _ = G.sort_input(n, dist, seed=seed)
+    cuts = np.linspace(0, n, n_runs + 1).astype(np.uint64)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        k[a:b] = np.sort(k[a:b], kind="stable")
+    return k, cuts
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs"])
+def test_exact_cut_brute_force(dist):
+    """Pure-Python brute force: order the positions by (key, position), take
+    the first k, count them per run."""
+    n, n_runs = 600, 7
+    k, cuts = _runs(dist, n, n_runs, seed=2)
+    if dist == "zipf":  # heavy ties across runs
+        k[:] = np.sort(k % np.uint64(5))
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            k[a:b] = np.sort(k[a:b])
+    order = sorted(range(n), key=lambda i: (int(k[i]), i))
+    run_of = np.searchsorted(cuts, np.arange(n), side="right") - 1
+    for kk in (0, 1, 99, 300, 599, 600, 900):
+        want = np.zeros(n_runs, np.uint64)
+        for i in order[:kk]:
+            want[run_of[i]] += 1
+        assert np.array_equal(O.exact_cut(k, cuts, kk), want), kk
+
+
+def test_exact_cut_invariants():
+    """Sums to k; everything left of the cut orders before everything right
+    of it; grows with k; numpy's stable argsort gives the same counts."""
+    n, n_runs = 40_000, 13
+    k, cuts = _runs("zipf", n, n_runs, seed=3)
+    perm = np.argsort(k, kind="stable")
+    run_of = np.searchsorted(cuts, np.arange(n), side="right") - 1
+    prev = np.zeros(n_runs, np.uint64)
+    for kk in (0, 1, 4_999, 20_000, 33_333, n - 1, n):
+        c = O.exact_cut(k, cuts, kk)
+        assert int(c.sum()) == kk
+        assert np.all(c >= prev)
+        prev = c
+        assert np.array_equal(c, np.bincount(run_of[perm[:kk]], minlength=n_runs).astype(np.uint64))
+        left = [(int(k[cuts[r] + j]), int(cuts[r] + j)) for r in range(n_runs) for j in range(int(c[r]))]
+        right = [(int(k[cuts[r] + j]), int(cuts[r] + j)) for r in range(n_runs)
+                 for j in range(int(c[r]), int(cuts[r + 1] - cuts[r]))]
+        if left and right:
+            assert max(left) < min(right)
+
+
+def test_exact_cut_special_cases():
+    # one run: the cut is k itself; all keys equal: runs are taken whole, in order
+    k = np.sort(G.u64_uniform(1000, 1, 9))
+    assert O.exact_cut(k, np.array([0, 1000], np.uint64), 321).tolist() == [321]
+    k = np.full(1000, 7, np.uint64)
+    cuts = np.array([0, 100, 350, 350, 1000], np.uint64)
+    assert O.exact_cut(k, cuts, 400).tolist() == [100, 250, 0, 50]
+    assert O.exact_cut(k, cuts, 5000).tolist() == [100, 250, 0, 650]
+
+
 # ------------------------------------------------------------------ join
 @pytest.mark.parametrize("match,z", [(1.0, 0.0), (0.5, 0.0), (1.0, 1.0), (0.5, 1.0), (0.0, 0.0)])
 def test_join_against_generator_truth(match, z):
