@@ -352,8 +352,10 @@ def pinned_array(n, dtype):
 
 
 def run_sort_extra(vx, G, args):
-    """Out-of-core sort of (uint64 key, uint32 row id) pairs, Zipf(1.1) keys,
-    16 GiB budget: sample splitters (plain) vs learned PL and MLP models."""
+    """Out-of-core sort of (uint64 key, uint32 row id) pairs, 16 GiB budget:
+    partition-then-sort with sample splitters (plain) vs learned PL and MLP
+    models, and the merge plan (sorted runs, exact cuts), on Zipf(1.1) keys
+    and on 64 presorted runs."""
     import numpy as np
     n = args.sort_pairs
     t0 = time.perf_counter()
@@ -374,10 +376,11 @@ def run_sort_extra(vx, G, args):
         o.host_scratch = scratch.ctypes.data
         o.host_scratch_bytes = scratch.nbytes
         vx.vx_sort(ctx, kc, rc, ok, orr, o)  # warm-up: first pass over freshly pinned host pages
-        for name, part in (("plain_sample", vx.VX_PART_SAMPLE), ("learned_pl", vx.VX_PART_LEARNED_PL),
-                           ("learned_mlp", vx.VX_PART_LEARNED_MLP)):
+
+        def form(part, plan):
             o = vx.vx_sort_opts()
             o.partitioner = part
+            o.plan = plan
             o.host_scratch = scratch.ctypes.data
             o.host_scratch_bytes = scratch.nbytes
             o.sample_size = 1 << 20
@@ -385,15 +388,33 @@ def run_sort_extra(vx, G, args):
             # have come out up to 35 % slow on some boxes, whichever form ran)
             runs = [vx.vx_sort(ctx, kc, rc, ok, orr, o) for _ in range(2)]
             st = min(runs, key=lambda r: r["ms_total"])
-            out[name] = {"gpairs_s": round(n / st["ms_total"] / 1e6, 3), "ms": round(st["ms_total"], 1),
-                         "ms_runs": [round(r["ms_total"], 1) for r in runs],
-                         "partitions": st["n_partitions"], "imbalance": round(st["imbalance"], 3),
-                         "passthrough": st["passthrough_partitions"], "overflow_retries": st["overflow_retries"],
-                         "ms_partition": round(st["ms_partition"], 1), "ms_sort": round(st["ms_sort"], 1),
-                         "ms_train": round(st["ms_train"], 1),
-                         "partition_regions": bool(st["contiguous_layout"]),
-                         "out_of_region_pairs": st["out_of_region_pairs"],
-                         "link_gbs": round((st["bytes_h2d"] + st["bytes_d2h"]) / st["ms_total"] / 1e6, 1)}
+            d = {"gpairs_s": round(n / st["ms_total"] / 1e6, 3), "ms": round(st["ms_total"], 1),
+                 "ms_runs": [round(r["ms_total"], 1) for r in runs],
+                 "partitions": st["n_partitions"], "imbalance": round(st["imbalance"], 3),
+                 "passthrough": st["passthrough_partitions"], "overflow_retries": st["overflow_retries"],
+                 "ms_partition": round(st["ms_partition"], 1), "ms_sort": round(st["ms_sort"], 1),
+                 "ms_train": round(st["ms_train"], 1),
+                 "partition_regions": bool(st["contiguous_layout"]),
+                 "out_of_region_pairs": st["out_of_region_pairs"],
+                 "link_gbs": round((st["bytes_h2d"] + st["bytes_d2h"]) / st["ms_total"] / 1e6, 1)}
+            if plan == vx.VX_SORT_MERGE:  # pass 1 sorts runs, pass 2 merges: no sample, exact cuts
+                d.update({"runs": st["n_runs"], "ms_cut": round(st["ms_sample"], 2),
+                          "ms_merge_kernel": round(st["ms_merge_kernel"], 1)})
+                if st["ms_merge_kernel"] > 0:
+                    hbm_peak, _ = measured_peaks()
+                    ach = 24 * st["merge_pass_pairs"] / (st["ms_merge_kernel"] * 1e6)
+                    d["merge_roofline"] = {"kernel": "merge_round_kernel", "bound": "hbm", "unit": "GB/s",
+                                           "achieved": round(ach, 1), "peak": hbm_peak,
+                                           "frac": round(ach / hbm_peak, 4)}
+            return d, st
+
+        for name, part, plan in (("plain_sample", vx.VX_PART_SAMPLE, vx.VX_SORT_PARTITION),
+                                 ("learned_pl", vx.VX_PART_LEARNED_PL, vx.VX_SORT_PARTITION),
+                                 ("learned_mlp", vx.VX_PART_LEARNED_MLP, vx.VX_SORT_PARTITION),
+                                 ("merge_exact", vx.VX_PART_SAMPLE, vx.VX_SORT_MERGE)):
+            out[name], last = form(part, plan)
+            if plan == vx.VX_SORT_PARTITION:
+                st = last
         out["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
         # per-partition radix sorts against HBM: 24 algorithmic bytes per pair
         # and executed pass (the one-sweep scatter reads and writes the 12-byte
@@ -406,6 +427,14 @@ def run_sort_extra(vx, G, args):
                                      "achieved": round(ach, 1), "peak": hbm_peak, "frac": round(ach / hbm_peak, 4),
                                      "peak_kind": peak_kind, "pass_pairs": int(st["radix_pass_pairs"]),
                                      "ms_sort_kernel": round(st["ms_sort_kernel"], 1)}
+        # 64 presorted runs (the third key distribution): partition-then-sort
+        # against the merge plan on the same input
+        G.sort_input(n, "runs", keys=k, rowids=r)
+        vx.vx_sort(ctx, kc, rc, ok, orr, vx.vx_sort_opts())  # first pass over the rewritten pages
+        out["presorted_runs"] = {"plain_sample": form(vx.VX_PART_SAMPLE, vx.VX_SORT_PARTITION)[0],
+                                 "learned_pl": form(vx.VX_PART_LEARNED_PL, vx.VX_SORT_PARTITION)[0],
+                                 "merge_exact": form(vx.VX_PART_SAMPLE, vx.VX_SORT_MERGE)[0]}
+        out["presorted_runs"]["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
     finally:
         vx.vx_close(ctx)
     return out
@@ -474,6 +503,21 @@ def run_join_extra(vx, G, args):
                 "ms_sample": round(r["ms_sample"], 1), "overflow_retries": r["overflow_retries"],
                 "link_gbs": round(r["bytes_h2d"] / r["ms_total"] / 1e6, 1),
                 "count": r["count"], "exact": r["count"] == c_true and r["payload_sum"] == s_true}
+            if (match, zs) == (1.0, 1.0):
+                # the paper's radix-partitioned join (2^24 groups joined in shared
+                # memory) on the same skewed probes; its host intermediates are
+                # allocated and page-locked inside the call (ms_total), the two
+                # passes alone are ms
+                o = vx.vx_join_opts()
+                o.algorithm = vx.VX_JOIN_RADIX
+                rr = vx.vx_join(ctx, a, b, p, o)
+                ms = rr["ms_partition"] + rr["ms_probe"]
+                out["radix_match1_zipf1"] = {
+                    "gtuples_s": round((nb + npr) / ms / 1e6, 3), "ms": round(ms, 1), "ms_total": round(rr["ms_total"], 1),
+                    "ms_partition": round(rr["ms_partition"], 1), "ms_join": round(rr["ms_probe"], 1),
+                    "ms_join_kernel": round(rr["ms_probe_kernel"], 1), "ranges": rr["ranges"],
+                    "link_gbs": round((rr["bytes_h2d"] + rr["bytes_d2h"]) / ms / 1e6, 1),
+                    "exact": rr["count"] == c_true and rr["payload_sum"] == s_true}
     finally:
         vx.vx_close(ctx)
     return out
@@ -758,7 +802,7 @@ def timeline_summary(tl, bytes_h2d):
     gbs = per_chunk / np.maximum(dur, 1e-6) / 1e6
     gaps = np.maximum(h0[1:] - h1[:-1], 0) if len(tl) > 1 else np.zeros(0)
     # kernel time hidden under copies: kernel c overlaps copy c+1
-    hidden = sum(max(0.0, min(k1[c], h1[c + 1]) - max(k0[c], h0[c + 1])) for c in range(len(tl) - 1))
+    hidden = float(sum(max(0.0, float(min(k1[c], h1[c + 1]) - max(k0[c], h0[c + 1]))) for c in range(len(tl) - 1)))
     return {"chunks": int(len(tl)), "wall_ms": round(wall, 3), "link_busy": round(float(dur.sum()) / wall, 4),
             "chunk_copy_gbs": {"min": round(float(gbs.min()), 1), "median": round(float(np.median(gbs)), 1),
                                "max": round(float(gbs.max()), 1)},
@@ -787,6 +831,9 @@ def summarize(line):
     so = line.get("sort")
     if so:
         out["sort_ms"] = {k: so[k]["ms"] for k in so if isinstance(so[k], dict) and "ms" in so[k]}
+        pr = so.get("presorted_runs")
+        if pr:
+            out["sort_runs_ms"] = {k: v["ms"] for k, v in pr.items() if isinstance(v, dict)}
     jo = line.get("join")
     if jo:
         out["join_ms"] = {k: jo[k]["ms"] for k in jo if isinstance(jo[k], dict) and "ms" in jo[k]}

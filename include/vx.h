@@ -235,6 +235,10 @@ typedef struct {
                               0 when not timed: DAG schedule, serving) */
   double ms_features;      /* wall time of the per-chunk feature pass before the pipeline (sampling
                               kernel, copy-back and the per-chunk decisions); 0 when it did not run */
+  uint64_t surv_list_bytes;/* device bytes of one staging slot's survivor list (split mode): every
+                              row of a chunk, or with VX_LATE_PER_CHUNK the regressor's predicted
+                              survivors plus headroom (overflow_retries counts chunks rerun with a
+                              full list because their survivors did not fit) */
 } vx_query_stats;
 
 /* Result of vx_run_plan / vx_groupby: groups with count > 0 in ascending group
@@ -275,8 +279,16 @@ vx_status vx_regressor_fit(vx_ctx *ctx, const float *X, const float *y, uint64_t
  * fraction) and keeps
  * the 4 weights in the context; VX_LATE_PER_CHUNK plans then decide late vs
  * early materialization per chunk from the predicted selectivity against TH
- * (Section 6.3 decides from an estimator S_c given before the operator runs). */
+ * (Section 6.3 decides from an estimator S_c given before the operator runs)
+ * and size each staging slot's survivor list from the largest predicted
+ * survivor count of a late chunk (plus a quarter and four standard
+ * deviations): a chunk whose survivors do not fit is flagged on the device,
+ * left out of the aggregate and rerun with a full list, so results never
+ * depend on the prediction. */
 vx_status vx_regressor_train(vx_ctx *ctx, float lambda, float *w_out, uint64_t *n_used);
+
+/* Sets the regressor's 4 weights (as vx_regressor_train would leave them). */
+vx_status vx_regressor_set(vx_ctx *ctx, const float *w, int32_t d);
 
 /* Copies up to cap logged (features, target) rows; *n = rows logged. */
 vx_status vx_chunk_log(vx_ctx *ctx, float *X, float *y, uint64_t cap, uint64_t *n);
@@ -434,6 +446,16 @@ vx_status vx_merge_runs(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals,
                         uint32_t n_runs, uint64_t *out_keys, uint32_t *out_vals);
 
 /* ---------------------------------------------------------------- join */
+/* Join algorithms.  DIRECT: key-range partitions of the build side, each a
+ * hash table in HBM probed by the streamed probe side (no partition is
+ * written to host memory).  RADIX: Section 6.2's radix-partitioned join:
+ * RadixPartitionExKer clusters every chunk of both tables by the low
+ * radix_bits bits of the key and stores the clustered chunks and their
+ * boundary arrays (find_boundary, Fig. 9) in host memory; HashJoinExKer then
+ * loads ranges of groups, cut by binary search over the boundary arrays, and
+ * joins each group in shared memory. */
+enum { VX_JOIN_DIRECT = 0, VX_JOIN_RADIX = 1 };
+
 typedef struct {
   int32_t partitioner;  /* VX_PART_*: splitters over the build keys when P > 1 */
   int32_t n_partitions; /* 0 = smallest P whose hash tables fit the budget; <= 256 */
@@ -443,6 +465,8 @@ typedef struct {
   int32_t count_pass;   /* 1: size tables from an exact count pass over the build keys (plain
                            form); 0: from the partition sizes the model implies, rebuilding a
                            table that overflows (learned form) */
+  int32_t algorithm;    /* VX_JOIN_DIRECT (default) or VX_JOIN_RADIX */
+  int32_t radix_bits;   /* RADIX: group bits, 8, 16 or 24 (0 = 24, the paper's 2^24 groups) */
   int32_t reserved;
 } vx_join_opts;
 
@@ -456,17 +480,34 @@ typedef struct {
   double ms_sample, ms_train, ms_build, ms_probe, ms_kernel, ms_total;
   double ms_probe_kernel;  /* device time of the probe kernels alone (CUDA events); every probe key
                               is looked up in exactly one partition */
+  uint64_t bytes_d2h;      /* RADIX: clustered chunks and boundary arrays stored to host memory */
+  uint32_t algorithm;      /* VX_JOIN_* that ran */
+  uint32_t ranges;         /* RADIX: group ranges of the join pass */
+  double ms_partition;     /* RADIX: wall time of the partition passes of both tables */
 } vx_join_result;
 
 /* Equi-join of a build table (unique 64-bit keys, 64-bit payload) with a
  * probe key column, all in registered host memory and possibly larger than
- * the budget (Section 6.2; A.key == B.key).  The build keys are cut into
- * n_partitions key ranges; for each range an open-addressing table is built
- * in HBM from the streamed build side and the streamed probe side probes it
- * (Section 5.3 executor for every stream).  Returns VX_E_DUPKEY if a build
- * key repeats. */
+ * the budget (Section 6.2; A.key == B.key).  DIRECT: the build keys are cut
+ * into n_partitions key ranges; for each range an open-addressing table is
+ * built in HBM from the streamed build side and the streamed probe side
+ * probes it (Section 5.3 executor for every stream).  RADIX (opts->algorithm):
+ * the paper's radix-partitioned join (see VX_JOIN_RADIX); its host
+ * intermediates (16 B per build row, 12 B per probe row, 4 (2^bits + 1) B per
+ * chunk) are allocated for the call.  Returns VX_E_DUPKEY if a build key
+ * repeats. */
 vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, int32_t probe_key, const vx_join_opts *opts,
                   vx_join_result *out);
+
+/* The clustering step of Section 6.2.1's RadixPartitionExKer on one chunk of
+ * n < 2^32 keys (host buffers, in HBM for the call): a stable sort of
+ * (key, chunk-local row) by the low `bits` bits of the key (8, 16 or 24),
+ * written to out_keys / out_rows, and find_boundary (Fig. 9) of the
+ * clustered groups: out_boundary gets 2^bits + 1 entries, entry g = first
+ * position of group g (of the next non-empty group when g is empty), entry
+ * 2^bits = n. */
+vx_status vx_radix_cluster(vx_ctx *ctx, const uint64_t *keys, uint64_t n, int32_t bits, uint64_t *out_keys,
+                           uint32_t *out_rows, uint32_t *out_boundary);
 
 /* ---------------------------------------------------------------- learned CDF model */
 

@@ -77,7 +77,7 @@ class vx_query_stats(ctypes.Structure):
                 ("overflow_retries", ctypes.c_uint32), ("est_selectivity", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_kernel", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
                 ("late_chunks", ctypes.c_uint64), ("ms_gather", ctypes.c_double),
-                ("ms_features", ctypes.c_double)]
+                ("ms_features", ctypes.c_double), ("surv_list_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +89,7 @@ class vx_result(ctypes.Structure):
 
 
 VX_PART_SAMPLE, VX_PART_LEARNED_PL, VX_PART_LEARNED_MLP = 0, 1, 2
+VX_JOIN_DIRECT, VX_JOIN_RADIX = 0, 1
 VX_SORT_PARTITION, VX_SORT_MERGE = 0, 1
 
 
@@ -119,7 +120,7 @@ class vx_sort_stats(ctypes.Structure):
 class vx_join_opts(ctypes.Structure):
     _fields_ = [("partitioner", ctypes.c_int32), ("n_partitions", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("sample_size", ctypes.c_uint64), ("load_factor", ctypes.c_double), ("count_pass", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("algorithm", ctypes.c_int32), ("radix_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class vx_join_result(ctypes.Structure):
@@ -128,7 +129,8 @@ class vx_join_result(ctypes.Structure):
                 ("max_partition", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("ms_sample", ctypes.c_double), ("ms_train", ctypes.c_double),
                 ("ms_build", ctypes.c_double), ("ms_probe", ctypes.c_double), ("ms_kernel", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("ms_probe_kernel", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("ms_probe_kernel", ctypes.c_double), ("bytes_d2h", ctypes.c_uint64),
+                ("algorithm", ctypes.c_uint32), ("ranges", ctypes.c_uint32), ("ms_partition", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -183,6 +185,7 @@ SIGNATURES = {
     "vx_regressor_fit": ([_vp, _vp, _vp, _u64, _i32, _f32, _vp], _i32),
     "vx_regressor_train": ([_vp, _f32, _vp, _P(_u64)], _i32),
     "vx_chunk_log": ([_vp, _vp, _vp, _u64, _P(_u64)], _i32),
+    "vx_regressor_set": ([_vp, _vp, _i32], _i32),
     "vx_chunk_log_clear": ([_vp], _i32),
     "vx_serve_start": ([_vp, _P(vx_serve_opts)], _i32),
     "vx_submit": ([_vp, _P(vx_plan), _P(_u64)], _i32),
@@ -190,6 +193,7 @@ SIGNATURES = {
     "vx_wait": ([_vp, _u64, _P(vx_result), _u32], _i32),
     "vx_serve_stats_get": ([_vp, _P(vx_serve_stats)], _i32),
     "vx_serve_stop": ([_vp], _i32),
+    "vx_radix_cluster": ([_vp, _vp, _u64, _i32, _vp, _vp, _vp], _i32),
     "vx_exact_splits": ([_vp, _vp, _vp, _u32, _vp, _u32, _vp], _i32),
     "vx_merge_runs": ([_vp, _vp, _vp, _vp, _u32, _vp, _vp], _i32),
     "vx_filter_device_static": ([_vp, _i32, _P(vx_pred), _i32, _u64, _u64, _vp, _u64, _P(_u64), _vp], _i32),
@@ -333,6 +337,11 @@ def vx_regressor_train(ctx, lam=1e-6):
     n = ctypes.c_uint64()
     _check(load().vx_regressor_train(ctx, lam, w.ctypes.data, ctypes.byref(n)))
     return w, n.value
+
+
+def vx_regressor_set(ctx, w):
+    w = np.ascontiguousarray(w, np.float32)
+    _check(load().vx_regressor_set(ctx, w.ctypes.data, len(w)))
 
 
 def vx_chunk_log(ctx):
@@ -502,6 +511,17 @@ def vx_sort_splitters(ctx, key_col: int, partitioner: int, n_partitions: int, sa
     _check(load().vx_sort_splitters(ctx, key_col, partitioner, n_partitions, sample_size, seed, out.ctypes.data,
                                     ctypes.byref(k)))
     return out[:k.value].copy()
+
+
+def vx_radix_cluster(ctx, keys, bits):
+    """(clustered keys, chunk-local rows, boundary array of 2^bits + 1)."""
+    keys = _np(keys, np.uint64)
+    ok = np.empty_like(keys)
+    rows = np.empty(len(keys), np.uint32)
+    bnd = np.zeros((1 << bits) + 1, np.uint32)
+    _check(load().vx_radix_cluster(ctx, keys.ctypes.data, len(keys), bits, ok.ctypes.data, rows.ctypes.data,
+                                   bnd.ctypes.data))
+    return ok, rows, bnd
 
 
 def vx_exact_splits(ctx, keys, run_off, ranks):

@@ -287,10 +287,11 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
   const bool auto_load = o.load_factor <= 0;
   if (auto_load) o.load_factor = kJoinMaxAutoLoad;
   if (o.load_factor > 0.95 || o.n_partitions < 0 || o.n_partitions > 256 || o.partitioner < VX_PART_SAMPLE ||
-      o.partitioner > VX_PART_LEARNED_MLP) {
+      o.partitioner > VX_PART_LEARNED_MLP || (o.algorithm != VX_JOIN_DIRECT && o.algorithm != VX_JOIN_RADIX)) {
     set_error("vx_join: bad options");
     return VX_E_INVAL;
   }
+  if (o.algorithm == VX_JOIN_RADIX) return radix_join(ctx, bk, bp, pk, o, out);
   const uint64_t nb = bk->n_rows, np = pk->n_rows;
   vx_join_result res{};
   cudaStream_t s = ctx->s_compute;

@@ -469,8 +469,8 @@ __global__ void isolate_splitters_kernel(const uint64_t *raw, uint32_t n_raw, co
 
 // ================================================================== host helpers
 
-vx_status radix_publish_enqueue(char *temp, uint64_t *host_word, cudaStream_t s) {
-  rx_publish<<<1, 1, 0, s>>>(radix_state_of(temp), 8, host_word);
+vx_status radix_publish_enqueue(char *temp, uint64_t *host_word, cudaStream_t s, int npass) {
+  rx_publish<<<1, 1, 0, s>>>(radix_state_of(temp), npass, host_word);
   VX_CUDA_TRY(cudaGetLastError());
   return VX_OK;
 }
@@ -507,9 +507,10 @@ static vx_status radix_result(char *temp, cudaStream_t s, int *cur) {
   return VX_OK;
 }
 
-// Enqueues a stable LSD radix sort of b.keys[0]/b.vals[0] (n pairs) on s.
-// The sorted pairs end in buffer st->cur[8] (0 or 1).
-vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms) {
+// Enqueues a stable LSD radix sort of b.keys[0]/b.vals[0] (n pairs) on s by
+// the low npass bytes of the key (8: the whole key).  The sorted pairs end in
+// buffer st->cur[npass] (0 or 1).
+vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms, int npass) {
   uint32_t nt = ntiles_of(n);
   RadixState *st = radix_state_of(temp);
   unsigned long long *bh = (unsigned long long *)(temp + kStateBytes);
@@ -529,7 +530,7 @@ vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s
   rx_byte_hist<<<g, kRxThreads, 0, s>>>(b, n, bh);
   rx_init_state<<<1, 32, 0, s>>>(st, bh, n);
   rx_init_bases<<<8, kRxDigits, 0, s>>>(bh, bases);
-  for (int pass = 0; pass < 8; ++pass)  // a skipped pass returns at once and keeps the buffer
+  for (int pass = 0; pass < npass; ++pass)  // a skipped pass returns at once and keeps the buffer
     rx_downsweep<false, true><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, nullptr, nt,
                                                                       bases, tickets, status);
   VX_CUDA_TRY(cudaGetLastError());

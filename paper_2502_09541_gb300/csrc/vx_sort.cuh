@@ -13,11 +13,11 @@ constexpr int kMlpParams = 3 * kMlpHidden + 1;
 
 uint64_t radix_temp_bytes(uint64_t cap);
 RadixState *radix_state_of(char *temp);
-vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms);
+vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms, int npass = 8);
 // after radix_sort_enqueue on s: publishes to a mapped host word the buffer
 // holding the result (low byte), the executed passes (next byte) and whether
 // a look-back wait gave up (bit 16)
-vx_status radix_publish_enqueue(char *temp, uint64_t *host_word, cudaStream_t s);
+vx_status radix_publish_enqueue(char *temp, uint64_t *host_word, cudaStream_t s, int npass = 8);
 vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, uint32_t P, char *temp,
                                   cudaStream_t s);
 constexpr uint32_t kMaxRequestedPartitions = 128;  // isolation may add up to P-1 boundaries
@@ -31,6 +31,10 @@ constexpr int kMaxSortSlots = 6;                   // staging slots of the parti
 // with each.
 constexpr uint64_t kPipelineRows = 48ull << 20;
 constexpr uint64_t kSplitterBufBytes = 8ull * (512 + kPLSegments + 1 + 8);
+
+// the radix-partitioned join of vx_join (VX_JOIN_RADIX)
+vx_status radix_join(vx_ctx *ctx, const Column *bk, const Column *bp, const Column *pk, const vx_join_opts &o,
+                     vx_join_result *out);
 
 // the merge plan of vx_sort (sorted runs, exact cuts, merged partitions)
 vx_status merge_sort_plan(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, uint64_t n, uint64_t *out_keys,

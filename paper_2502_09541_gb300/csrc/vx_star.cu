@@ -540,7 +540,8 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
       if (n) {
         if (threadIdx.x == 0) st.base = atomicAdd(p.surv_cnt, n);
         __syncthreads();
-        for (unsigned int k = threadIdx.x; k < n; k += blockDim.x) p.surv_list[st.base + k] = st.e[k];
+        for (unsigned int k = threadIdx.x; k < n; k += blockDim.x)
+          if (st.base + k < p.surv_cap) p.surv_list[st.base + k] = st.e[k];
         __syncthreads();
         if (threadIdx.x == 0) st.n = 0;
         __syncthreads();
@@ -643,7 +644,8 @@ __global__ void __launch_bounds__(256) star_split_kernel(const ChunkParams p) {
     if (n) {
       if (threadIdx.x == 0) st.base = atomicAdd(p.surv_cnt, n);
       __syncthreads();
-      for (unsigned int k = threadIdx.x; k < n; k += blockDim.x) p.surv_list[st.base + k] = st.e[k];
+      for (unsigned int k = threadIdx.x; k < n; k += blockDim.x)
+        if (st.base + k < p.surv_cap) p.surv_list[st.base + k] = st.e[k];
       __syncthreads();
       if (threadIdx.x == 0) st.n = 0;
       __syncthreads();
@@ -657,16 +659,24 @@ __global__ void __launch_bounds__(256) star_split_kernel(const ChunkParams p) {
 
 // Split mode, pass 2: late payload columns of every survivor, read through
 // mapped host memory with one independent load per survivor in flight, and
-// aggregated into the group accumulators.
+// aggregated into the group accumulators.  A chunk whose survivors did not
+// fit the list is not aggregated at all: it is flagged for an exact rerun.
 template <bool kSmem>
 __global__ void __launch_bounds__(256) star_gather_kernel(const ChunkParams p) {
   extern __shared__ unsigned long long sacc[];
   unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
+  const unsigned int n = *p.surv_cnt;
+  if (n > p.surv_cap) {  // the same for every thread of every block
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (p.chunk_ovf) p.chunk_ovf[p.chunk_idx] = 1u;
+      else atomicOr(p.err, ERR_OVERFLOW);
+    }
+    return;
+  }
   if (kSmem) {
     for (uint32_t g = threadIdx.x; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
     __syncthreads();
   }
-  const unsigned int n = *p.surv_cnt;
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint2 e = p.surv_list[i];
     const int64_t a = p.agg_a_role >= 0 ? load_role(p, p.agg_a_role, e.x) : 0;
@@ -1174,6 +1184,10 @@ vx_status check_err_word(vx_ctx *ctx, const uint32_t *d_err) {
     set_error("hash table full");
     return VX_E_NOMEM;
   }
+  if (e & ERR_OVERFLOW) {
+    set_error("a survivor list overflowed with no rerun to catch it");
+    return VX_E_CUDA;
+  }
   return VX_OK;
 }
 
@@ -1191,8 +1205,12 @@ struct StarExKernel : ExKernel {
   // read through mapped host memory in chunks with chunk_late[it] set
   std::vector<uint8_t> switchable, chunk_late;
 
-  // split mode (late roles): survivor list region after the staged columns
+  // split mode (late roles): survivor list region after the staged columns,
+  // surv_rows entries (0: chunk_rows, which no chunk can overflow)
   bool any_late = false;
+  uint64_t surv_rows = 0;
+  // a subset of the chunks (their indices), e.g. the overflowed ones rerun
+  std::vector<uint64_t> only;
   // per-slot events around the fused kernel (its own duration, immediate schedule)
   std::vector<cudaEvent_t> ev_a, ev_b, ev_c;  // fused kernel [a, b), gather [b, c)
   std::vector<uint8_t> ev_used;
@@ -1205,14 +1223,16 @@ struct StarExKernel : ExKernel {
     for (auto e : ev_c) cudaEventDestroy(e);
   }
 
-  uint64_t size() override { return (n_rows + chunk_rows - 1) / chunk_rows; }
+  uint64_t size() override { return only.empty() ? (n_rows + chunk_rows - 1) / chunk_rows : only.size(); }
+  uint64_t cid(uint64_t it) const { return only.empty() ? it : only[it]; }
+  uint64_t surv_region() const { return surv_rows ? std::min(surv_rows, chunk_rows) : chunk_rows; }
   uint64_t cols_bytes() const { return (uint64_t)staged_cols.size() * ((chunk_rows * 4 + 255) & ~255ull); }
-  uint64_t slot_bytes() override { return cols_bytes() + (any_late ? chunk_rows * 8 + 256 : 0); }
+  uint64_t slot_bytes() override { return cols_bytes() + (any_late ? surv_region() * 8 + 256 : 0); }
   uint64_t col_off(size_t k) const { return k * ((chunk_rows * 4 + 255) & ~255ull); }
   bool chunk_has_late(uint64_t it) const {
     if (!any_late) return false;
     if (chunk_late.empty()) return true;  // one decision for the whole plan
-    return chunk_late[it] != 0;
+    return chunk_late[cid(it)] != 0;
   }
   void on_retire(uint64_t it) override {
     const size_t k = it % ev_a.size();
@@ -1226,21 +1246,22 @@ struct StarExKernel : ExKernel {
     cudaGetLastError();
     ev_used[k] = 0;
   }
-  uint64_t rows_of(uint64_t it) const { return std::min(chunk_rows, n_rows - it * chunk_rows); }
+  uint64_t rows_of(uint64_t it) const { return std::min(chunk_rows, n_rows - cid(it) * chunk_rows); }
   bool late_in(size_t k, uint64_t it) const {
-    return k < switchable.size() && switchable[k] && it < chunk_late.size() && chunk_late[it];
+    const uint64_t c = cid(it);
+    return k < switchable.size() && switchable[k] && c < chunk_late.size() && chunk_late[c];
   }
 
   void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) override {
-    const uint64_t r0 = row_begin + it * chunk_rows, n = rows_of(it);
+    const uint64_t r0 = row_begin + cid(it) * chunk_rows, n = rows_of(it);
     for (size_t k = 0; k < staged_cols.size(); ++k)
       if (!late_in(k, it)) h2d.push_back({(const char *)staged_cols[k]->host + r0 * 4, slot + col_off(k), n * 4});
   }
   vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
     ChunkParams p = proto;
-    p.row0 = row_begin + it * chunk_rows;
+    p.row0 = row_begin + cid(it) * chunk_rows;
     p.n = rows_of(it);
-    p.chunk_idx = it;
+    p.chunk_idx = cid(it);
     for (size_t k = 0; k < staged_cols.size(); ++k)
       p.staged[staged_role[k]] = late_in(k, it) ? nullptr : (const int32_t *)(slot + col_off(k));
     int threads = ctx->cfg.block_threads > 256 ? 256 : ctx->cfg.block_threads;
@@ -1252,7 +1273,8 @@ struct StarExKernel : ExKernel {
     };
     if (chunk_has_late(it)) {  // filter/probe pass, then the late-column gather
       p.surv_list = (uint2 *)(slot + cols_bytes());
-      p.surv_cnt = (unsigned int *)(slot + cols_bytes() + chunk_rows * 8);
+      p.surv_cnt = (unsigned int *)(slot + cols_bytes() + surv_region() * 8);
+      p.surv_cap = (unsigned int)surv_region();
       VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
       if (timed) VX_CUDA_TRY(rec(ev_a[ek]));
       const int kr = vec_width(p);
@@ -1323,11 +1345,12 @@ vx_status star_graph(vx_ctx *ctx, StarExKernel &ek, const std::vector<std::share
   ChunkParams kp = ek.proto;
   kp.g_sum = kp.g_cnt = nullptr;
   kp.err = nullptr;
+  kp.chunk_ovf = nullptr;
   kp.row0 = kp.n = 0;
   std::string key((const char *)&kp, sizeof kp);
   for (const Column *c : ek.staged_cols) key.append((const char *)&c->host, sizeof(void *));
-  const uint64_t dims[6] = {ek.row_begin, ek.n_rows, ek.chunk_rows, (uint64_t)ctx->cfg.n_slots,
-                            (uint64_t)ctx->cfg.block_threads, (uint64_t)ctx->cfg.blocks_per_sm};
+  const uint64_t dims[7] = {ek.row_begin, ek.n_rows, ek.chunk_rows, (uint64_t)ctx->cfg.n_slots,
+                            (uint64_t)ctx->cfg.block_threads, (uint64_t)ctx->cfg.blocks_per_sm, ek.surv_rows};
   key.append((const char *)dims, sizeof dims);
   key.append(ek.switchable.begin(), ek.switchable.end());
   key.append(ek.chunk_late.begin(), ek.chunk_late.end());
@@ -1340,22 +1363,27 @@ vx_status star_graph(vx_ctx *ctx, StarExKernel &ek, const std::vector<std::share
   const uint64_t slot = (ek.slot_bytes() + 255) & ~255ull;
   auto e = std::make_shared<GraphEntry>();
   e->tables = tables;
+  const uint64_t n_ch = ek.size();
+  const bool want_ovf = ek.proto.chunk_ovf != nullptr;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    e->ring.arena = e->acc.arena = e->err.arena = &ctx->arena;
+    e->ring.arena = e->acc.arena = e->err.arena = e->ovf.arena = &ctx->arena;
     e->ring.p = ctx->arena.alloc(slot * S);
     e->acc.p = ctx->arena.alloc(16 * G);
     e->err.p = ctx->arena.alloc(256);
-    if (e->ring.p && e->acc.p && e->err.p) break;
+    if (want_ovf) e->ovf.p = ctx->arena.alloc(4 * n_ch);
+    if (e->ring.p && e->acc.p && e->err.p && (!want_ovf || e->ovf.p)) break;
     e->ring.release();
     e->acc.release();
     e->err.release();
+    e->ovf.release();
     ctx->graphs.clear();
   }
-  if (!e->ring.p) return VX_OK;  // no room: run without a graph
+  if (!e->ring.p || !e->acc.p || !e->err.p || (want_ovf && !e->ovf.p)) return VX_OK;  // no room: run without a graph
   ChunkParams gp = ek.proto;
   gp.g_sum = e->acc.as<unsigned long long>();
   gp.g_cnt = gp.g_sum + G;
   gp.err = e->err.as<uint32_t>();
+  gp.chunk_ovf = want_ovf ? e->ovf.as<unsigned int>() : nullptr;
   StarExKernel gk = ek;
   gk.proto = gp;
   gk.ev_used.clear();
@@ -1384,7 +1412,8 @@ vx_status star_graph(vx_ctx *ctx, StarExKernel &ek, const std::vector<std::share
   VX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   ExecStats est;
   vx_status st = VX_OK;
-  if (cudaMemsetAsync(e->acc.p, 0, 16 * G, s) != cudaSuccess || cudaMemsetAsync(e->err.p, 0, 4, s) != cudaSuccess) {
+  if (cudaMemsetAsync(e->acc.p, 0, 16 * G, s) != cudaSuccess || cudaMemsetAsync(e->err.p, 0, 4, s) != cudaSuccess ||
+      (want_ovf && cudaMemsetAsync(e->ovf.p, 0, 4 * n_ch, s) != cudaSuccess)) {
     set_error("graph capture: memset failed");
     st = VX_E_CUDA;
   }
@@ -1781,6 +1810,7 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
     VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
     if (per_chunk) {
       ek.chunk_late.resize(n_chunks);
+      uint64_t cap_rows = 0;
       for (uint64_t c = 0; c < n_chunks; ++c) {
         const float *f = &feats[c * kChunkFeatures];
         double yhat = f[2];  // sampled selectivity when no regressor is trained
@@ -1790,15 +1820,37 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
         }
         ek.chunk_late[c] = yhat < TH ? 1 : 0;
         late_chunks += ek.chunk_late[c];
+        if (ek.chunk_late[c]) {
+          // survivor-list entries a late chunk gets: the predicted survivors
+          // with a quarter and four standard deviations of headroom (a chunk
+          // beyond it is rerun exactly)
+          const double pred = std::max(0.0, yhat) * (double)std::min(cr, n_rows - c * cr);
+          cap_rows = std::max<uint64_t>(cap_rows, (uint64_t)std::ceil(1.25 * pred + 4.0 * std::sqrt(pred + 1.0)) +
+                                                      2 * kStarTileRows);
+        }
       }
+      ek.surv_rows = std::max<uint64_t>(cap_rows, kStarTileRows);
     }
     ms_features = now_ms() - tf0;
+  }
+  // per-chunk survivor-list overflow flags (survivor lists sized from predictions)
+  DevBuf ovf;
+  if (per_chunk && late_chunks && n_chunks) {
+    ovf.arena = &ctx->arena;
+    ovf.p = ctx->arena.alloc(4 * n_chunks);
+    if (!ovf.p) {
+      set_error("overflow flags do not fit the arena");
+      return VX_E_NOMEM;
+    }
+    VX_CUDA_TRY(cudaMemsetAsync(ovf.p, 0, 4 * n_chunks, ctx->s_compute));
+    P.chunk_ovf = ovf.as<unsigned int>();
   }
   ek.proto = P;
 
   ExecStats es;
   void *res_acc = acc.p;
   uint32_t *res_err = d_err;
+  const unsigned int *res_ovf = P.chunk_ovf;
   std::shared_ptr<GraphEntry> ge;
   if (n_rows && ctx->cfg.use_graphs) {
     VX_TRY(star_graph(ctx, ek, tables, G, &ge));
@@ -1809,11 +1861,47 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
       es.kernel_launches = ge->launches;
       res_acc = ge->acc.p;
       res_err = ge->err.as<uint32_t>();
+      res_ovf = ge->ovf.p ? ge->ovf.as<unsigned int>() : nullptr;
     }
   }
   if (!ge && n_rows) VX_TRY(run_pipeline(ctx, ek, &es));
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
   VX_TRY(check_err_word(ctx, res_err));
+  uint32_t overflow_retries = 0;
+  if (res_ovf) {  // chunks whose survivors outgrew the predicted list: rerun them exactly
+    std::vector<unsigned int> fl(n_chunks);
+    VX_CUDA_TRY(cudaMemcpy(fl.data(), res_ovf, 4 * n_chunks, cudaMemcpyDeviceToHost));
+    StarExKernel rk;
+    for (uint64_t c = 0; c < n_chunks; ++c)
+      if (fl[c]) rk.only.push_back(c);
+    if (!rk.only.empty()) {
+      rk.ctx = ctx;
+      rk.proto = ek.proto;
+      rk.proto.g_sum = (unsigned long long *)res_acc;
+      rk.proto.g_cnt = rk.proto.g_sum + G;
+      rk.proto.err = res_err;
+      rk.proto.chunk_ovf = nullptr;
+      rk.proto.chunk_surv = nullptr;
+      rk.staged_cols = ek.staged_cols;
+      rk.staged_role = ek.staged_role;
+      rk.row_begin = ek.row_begin;
+      rk.n_rows = ek.n_rows;
+      rk.chunk_rows = ek.chunk_rows;
+      rk.smem = ek.smem;
+      rk.smem_bytes = ek.smem_bytes;
+      rk.switchable = ek.switchable;
+      rk.chunk_late = ek.chunk_late;
+      rk.any_late = ek.any_late;
+      rk.surv_rows = 0;  // worst case: every row of the chunk
+      ExecStats er;
+      VX_TRY(run_pipeline(ctx, rk, &er));
+      VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+      VX_TRY(check_err_word(ctx, res_err));
+      es.bytes_h2d += er.bytes_h2d;
+      overflow_retries = (uint32_t)rk.only.size();
+      ek.launches += rk.launches;
+    }
+  }
   if (ge) {  // the replay's fused-kernel and gather times, from its event nodes
     for (size_t c = 0; c < ge->ev_a.size(); ++c) {
       float ms = 0;
@@ -1871,6 +1959,8 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
     qs.bytes_zero_copy += (uint64_t)(zs * 64.0 * __builtin_popcount(switch_mask));
   }
   qs.late_chunks = late_chunks;
+  qs.overflow_retries = overflow_retries;
+  qs.surv_list_bytes = ek.any_late ? ek.surv_region() * 8 : 0;
   qs.bytes_logical = n_rows * 4ull * role_col.size();
   qs.ms_kernel = ek.main_launches ? ek.ms_main : es.ms_kernel;  // the fused kernel's own time when timed
   qs.ms_gather = ek.ms_gather;
@@ -2027,6 +2117,19 @@ VX_API vx_status vx_regressor_train(vx_ctx *ctx, float lambda, float *w_out, uin
   for (int k = 0; k < kChunkFeatures; ++k) ctx->reg_w[k] = w[k];
   ctx->reg_trained = true;
   if (w_out) memcpy(w_out, w, sizeof w);
+  return VX_OK;
+}
+
+VX_API vx_status vx_regressor_set(vx_ctx *ctx, const float *w, int32_t d) {
+  clear_error();
+  VX_TRY(check_ctx(ctx));
+  if (!w || d != kChunkFeatures) {
+    set_error("vx_regressor_set: %d weights expected", kChunkFeatures);
+    return VX_E_INVAL;
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  for (int k = 0; k < kChunkFeatures; ++k) ctx->reg_w[k] = w[k];
+  ctx->reg_trained = true;
   return VX_OK;
 }
 

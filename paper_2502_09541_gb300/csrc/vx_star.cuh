@@ -107,7 +107,9 @@ struct ChunkParams {
   unsigned long long *chunk_surv;  // optional per-chunk survivor counts (statistics log)
   uint64_t chunk_idx;
   uint2 *surv_list;                // split mode: (chunk row, group id) of every survivor
-  unsigned int *surv_cnt;
+  unsigned int *surv_cnt;          // survivors of the chunk (counted past surv_cap)
+  unsigned int surv_cap;           // entries surv_list holds; survivors past it are not written
+  unsigned int *chunk_ovf;         // optional per-chunk flag: the list overflowed, the chunk was not aggregated
   // vector path: the staged roles the row logic reads (predicates, keys,
   // fact group keys), and where each predicate / key / group key finds its
   // value among them
@@ -170,6 +172,7 @@ struct FilterParams {
 // tables it reads alive.
 struct GraphEntry {
   DevBuf ring, acc, err;
+  DevBuf ovf;  // per-chunk survivor-list overflow flags of the replay
   cudaGraphExec_t exec = nullptr;
   std::vector<std::shared_ptr<ResidentHT>> tables;
   uint64_t chunks = 0, bytes_h2d = 0, launches = 0;

@@ -135,3 +135,38 @@ def test_per_chunk_materialization_on_clustered_table():
             assert p["bytes_h2d"] + p["bytes_zero_copy"] < a["bytes_h2d"] + a["bytes_zero_copy"]
     finally:
         vx.vx_close(c)
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_survivor_lists_sized_by_prediction_overflow_reruns_exactly(graphs):
+    """The regressor sizes each slot's survivor list.  Zero weights predict
+    no survivors, so every late chunk overflows its list: the chunks are
+    flagged on the device, left out of the aggregate and rerun with a full
+    list, and the result stays the oracle's.  A trained regressor gives lists
+    far below the worst case of one entry per chunk row and no reruns."""
+    n = 4_000_000
+    fact = G.star_fact(n, seed=11)
+    dims = G.star_dims(0)
+    c, fid, did = _open_with(fact, dims)
+    try:
+        cfg = vx.vx_get_config(c)
+        cfg.use_graphs = graphs
+        vx.vx_set_config(c, cfg)
+        worst = 8 * _chunk_rows(8 << 20, 6)  # T2: 4 row-logic columns + price, cost
+        T = G.star_templates()["T2_10"]  # ~10 % of a chunk's rows survive
+        plan = vx.make_plan(T, fid, did, G.STAR_ATTR_CARD, vx.VX_LATE_PER_CHUNK)
+        vx.vx_regressor_set(c, np.zeros(4, np.float32))
+        for _ in range(2):  # with graphs: capture, then replay
+            bad = _check(vx.vx_run_plan(c, plan), T, fact, dims)
+            assert bad["late_chunks"] == bad["chunks"] and bad["overflow_retries"] == bad["chunks"]
+            assert bad["surv_list_bytes"] < worst
+        # the sampled selectivity itself (w = e_2) as the prediction, on a
+        # template below TH (~1 %)
+        T = G.star_templates()["T2_1"]
+        plan = vx.make_plan(T, fid, did, G.STAR_ATTR_CARD, vx.VX_LATE_PER_CHUNK)
+        vx.vx_regressor_set(c, np.array([0, 0, 1, 0], np.float32))
+        good = _check(vx.vx_run_plan(c, plan), T, fact, dims)
+        assert good["late_chunks"] == good["chunks"] and good["overflow_retries"] == 0
+        assert good["surv_list_bytes"] < worst / 20
+    finally:
+        vx.vx_close(c)
