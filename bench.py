@@ -668,7 +668,10 @@ def run_ours(args):
                   "chunk_bytes": 64 << 20, "sched": "immediate", "late": "per plan"},
         "learned": {"value": round(learned_gbs, 3), "ms_per_step": round(ms_learned, 3),
                     "link_gbs": round(link_l, 1), "chunk_bytes": int(tuned.chunk_bytes),
-                    "n_slots": int(tuned.n_slots), "graphs": True, "late": "per chunk (regressor)",
+                    "n_slots": int(tuned.n_slots),
+                    "kernel_shape": {"rows_per_thread": int(tuned.kernel_rows) or "vector (4)",
+                                     "blocks_per_sm": int(tuned.blocks_per_sm)},
+                    "graphs": True, "late": "per chunk (regressor)",
                     "regressor_chunks_logged": int(n_log), "clocks": clk2.summary()},
     }
     use_learned = learned_gbs >= plain_gbs
@@ -698,6 +701,8 @@ def run_ours(args):
     cfg.use_graphs = 0
     cfg.chunk_bytes = 64 << 20
     cfg.n_slots = 3
+    cfg.kernel_rows = 0
+    cfg.blocks_per_sm = 4
     vx.vx_set_config(ctx, cfg)
 
     # end to end through the public call: dimension tables rebuilt from host

@@ -83,6 +83,11 @@ typedef struct {
                                cardinality regressor's training data); not with use_graphs */
   int32_t log_timeline;     /* the immediate schedule records when every chunk's copies and kernel
                                ran (vx_last_timeline); not with use_graphs */
+  int32_t kernel_rows;      /* rows per thread of the fused chunk kernel: 0 = automatic (the vector
+                               path, 4 rows per thread read as 16-byte column vectors, where the
+                               columns allow; else 8 rows), 8 or 16 = the scalar kernel with that
+                               many rows per thread and at most blocks_per_sm blocks per SM */
+  int32_t reserved;
 } vx_config;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -257,6 +262,19 @@ typedef struct {
  * stream, resident dimension hash tables, zero-copy late materialization). */
 vx_status vx_run_plan(vx_ctx *ctx, const vx_plan *plan, vx_result *out);
 
+/* The same star plan run one operator at a time with host intermediates
+ * (Section 6.4: operators extended with the IO decoupling can be chained,
+ * with CPU memory holding the intermediate results): a filter over the fact
+ * predicates, one probe per dimension in plan order and the aggregate, each
+ * a pipelined pass over the fact chunks that loads the previous operator's
+ * (row, group code) entries from page-locked host memory and stores its own
+ * there, so no intermediate has to fit the device budget.  An operator
+ * stages a chunk's fact columns by copy engine when its input holds at least
+ * TH of the chunk's rows, else reads them through mapped host memory.  The
+ * result equals vx_run_plan's; the intermediates (16 bytes per fact row of
+ * the plan's range) are kept by the context between calls. */
+vx_status vx_run_plan_operators(vx_ctx *ctx, const vx_plan *plan, vx_result *out);
+
 /* Group-by aggregation over fact columns only (a star plan without
  * dimensions): keys are int32 fact columns with codes in [0, card). */
 vx_status vx_groupby(vx_ctx *ctx, const vx_plan_gkey *keys, int32_t n_keys, int32_t agg_op, int32_t agg_a,
@@ -295,13 +313,15 @@ vx_status vx_chunk_log(vx_ctx *ctx, float *X, float *y, uint64_t cap, uint64_t *
 /* Clears the log and the trained regressor. */
 vx_status vx_chunk_log_clear(vx_ctx *ctx);
 
-/* Autotuner of the executor for one plan: times the plan over its first
- * sample_rows fact rows for every chunk size in {8, 16, 32, 64, 128, 256} MiB
- * and staging ring depth in {2, 3, 4} that fits the arena (best of two timed
- * runs after one warm-up each), keeps the fastest in the context's config and
- * returns it.  Section 8.1 sweeps Exchange's packet size the same way (fixed
- * per-copy overhead against pipeline depth).  Results do not depend on the
- * configuration, only the time does. */
+/* Autotuner of the executor and the fused kernel's launch shape for one
+ * plan: times the plan over its first sample_rows fact rows (best of two
+ * timed runs after one warm-up each) for every chunk size in {8, 16, 32, 64,
+ * 128, 256} MiB and staging ring depth in {2, 3, 4} that fits the arena, then,
+ * at the fastest of those, for every kernel shape in {automatic vector path,
+ * scalar 8 or 16 rows per thread at 4 or 8 blocks per SM}; keeps the fastest
+ * in the context's config and returns it.  Section 8.1 sweeps Exchange's
+ * packet size the same way (fixed per-copy overhead against pipeline depth).
+ * Results do not depend on the configuration, only the time does. */
 vx_status vx_autotune(vx_ctx *ctx, const vx_plan *plan, uint64_t sample_rows, vx_config *best);
 
 /* Frees the dimension hash tables that vx_run_plan keeps resident on the

@@ -44,7 +44,7 @@ class vx_config(ctypes.Structure):
                 ("late_mat", ctypes.c_int32), ("zc_threshold", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("wait_timeout_ms", ctypes.c_uint32), ("log_chunk_stats", ctypes.c_int32),
-                ("log_timeline", ctypes.c_int32)]
+                ("log_timeline", ctypes.c_int32), ("kernel_rows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class vx_pred(ctypes.Structure):
@@ -166,6 +166,7 @@ SIGNATURES = {
     "vx_unregister_host_column": ([_vp, _i32], _i32),
     "vx_filter": ([_vp, _P(vx_pred), _i32, _u64, _u64, _vp, _u64, _P(_u64)], _i32),
     "vx_run_plan": ([_vp, _P(vx_plan), _P(vx_result)], _i32),
+    "vx_run_plan_operators": ([_vp, _P(vx_plan), _P(vx_result)], _i32),
     "vx_groupby": ([_vp, _P(vx_plan_gkey), _i32, _i32, _i32, _i32, _P(vx_pred), _i32, _P(vx_result)], _i32),
     "vx_last_stats": ([_vp, _P(vx_query_stats)], _i32),
     "vx_last_timeline": ([_vp, _vp, _u64, _P(_u64)], _i32),
@@ -299,6 +300,20 @@ def vx_run_plan(ctx, plan: vx_plan, cap: int = 1 << 16):
     c = np.zeros(cap, np.uint64)
     res = vx_result(cap, gid.ctypes.data, s.ctypes.data, c.ctypes.data, 0, vx_query_stats())
     st = load().vx_run_plan(ctx, ctypes.byref(plan), ctypes.byref(res))
+    if st not in (VX_OK, VX_E_CAPACITY):
+        _check(st)
+    n = min(res.n_out, cap)
+    return st, gid[:n], s[:n], c[:n], res.stats.as_dict()
+
+
+def vx_run_plan_operators(ctx, plan: vx_plan, cap: int = 1 << 16):
+    """The plan one operator at a time with host intermediates; returns
+    (status, gid, sum, cnt, stats) like vx_run_plan."""
+    gid = np.zeros(cap, np.uint64)
+    s = np.zeros(cap, np.int64)
+    c = np.zeros(cap, np.uint64)
+    res = vx_result(cap, gid.ctypes.data, s.ctypes.data, c.ctypes.data, 0, vx_query_stats())
+    st = load().vx_run_plan_operators(ctx, ctypes.byref(plan), ctypes.byref(res))
     if st not in (VX_OK, VX_E_CAPACITY):
         _check(st)
     n = min(res.n_out, cap)

@@ -220,6 +220,7 @@ VX_API vx_status vx_close(vx_ctx *ctx) {
       if (c.live && c.we_registered) cudaHostUnregister((void *)c.host);
     ctx->cols.clear();
     if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
+    if (ctx->op_host) cudaFreeHost(ctx->op_host);
     if (ctx->own_compute && ctx->s_compute) cudaStreamDestroy(ctx->s_compute);
     if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
     if (ctx->s_d2h) cudaStreamDestroy(ctx->s_d2h);
@@ -241,7 +242,8 @@ VX_API vx_status vx_set_config(vx_ctx *ctx, const vx_config *cfg) {
   if (cfg->n_slots < 2 || cfg->n_slots > 16 || cfg->chunk_bytes < 4096 || cfg->block_threads < 64 ||
       cfg->block_threads > 1024 || (cfg->block_threads & 31) || cfg->blocks_per_sm < 1 ||
       cfg->blocks_per_sm > 32 || (cfg->sched != VX_SCHED_IMMEDIATE && cfg->sched != VX_SCHED_DAG) ||
-      cfg->wait_timeout_ms == 0 || cfg->zc_threshold < 0 || cfg->zc_threshold > 1) {
+      cfg->wait_timeout_ms == 0 || cfg->zc_threshold < 0 || cfg->zc_threshold > 1 ||
+      (cfg->kernel_rows != 0 && cfg->kernel_rows != 8 && cfg->kernel_rows != 16)) {
     set_error("vx_set_config: value out of range");
     return VX_E_INVAL;
   }

@@ -150,6 +150,10 @@ struct vx_ctx {
   // per-chunk timeline of the last pipeline run with log_timeline (rows of
   // VX_TIMELINE_COLS floats)
   std::vector<float> timeline;
+  // page-locked host intermediates of operator-at-a-time plans, kept between
+  // calls and grown on demand
+  char *op_host = nullptr;
+  uint64_t op_host_bytes = 0;
 };
 
 namespace vx {

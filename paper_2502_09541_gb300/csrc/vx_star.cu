@@ -13,48 +13,12 @@
 #include <cstdio>
 
 #include "vx_internal.h"
+#include "vx_probe.cuh"
 #include "vx_star.cuh"
 
 namespace vx {
 
 // ================================================================== device code
-
-// Every comparison operator as one inclusive range [lo, hi] tested on uint32
-// offsets, v - lo <= hi - lo, optionally complemented: NE is the complement of
-// [lo, lo], and an empty range (BETWEEN with lo > hi, LT INT_MIN, GT INT_MAX,
-// an unknown operator) is the complement of the full range.  Built once per
-// predicate, so the per-row test is a subtract and a compare.
-struct PredRange {
-  uint32_t lo, span;
-  bool inv;
-};
-
-__device__ __forceinline__ PredRange pred_range(int32_t op, int32_t lo, int32_t hi) {
-  int32_t a = lo, b = hi;
-  bool inv = false, none = false;
-  switch (op) {
-    case VX_BETWEEN: none = lo > hi; break;
-    case VX_EQ: b = lo; break;
-    case VX_NE: b = lo, inv = true; break;
-    case VX_LT: none = lo == INT_MIN, a = INT_MIN, b = lo - (lo != INT_MIN); break;
-    case VX_LE: a = INT_MIN, b = lo; break;
-    case VX_GT: none = lo == INT_MAX, a = lo + (lo != INT_MAX), b = INT_MAX; break;
-    case VX_GE: a = lo, b = INT_MAX; break;
-    default: none = true;
-  }
-  if (none) a = INT_MIN, b = INT_MAX, inv = true;
-  return PredRange{(uint32_t)a, (uint32_t)b - (uint32_t)a, inv};
-}
-
-__device__ __forceinline__ bool pred_in(const PredRange &r, int32_t v) { return ((uint32_t)v - r.lo <= r.span) != r.inv; }
-
-__device__ __forceinline__ bool pred_ok(int32_t v, int32_t op, int32_t lo, int32_t hi) {
-  return pred_in(pred_range(op, lo, hi), v);
-}
-
-__device__ __forceinline__ uint32_t ht_hash32(int32_t k, uint32_t log2cap) {
-  return ((uint32_t)k * 0x9E3779B1u) >> (32u - log2cap);
-}
 
 // Inserts every dimension row: value = group-code contribution of the row if
 // it passes the dimension predicates, HT_FILTERED otherwise (so duplicate keys
@@ -110,39 +74,6 @@ __global__ void ht_build_kernel(const DimBuildParams p) {
 __global__ void fill_u64_kernel(uint64_t *p, uint64_t n, uint64_t v) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
     p[i] = v;
-}
-
-__device__ __forceinline__ bool ht_lookup(const uint64_t *__restrict__ slots, uint32_t log2cap, int32_t key,
-                                          uint32_t &val) {
-  const uint32_t mask = (1u << log2cap) - 1u;
-  uint32_t h = ht_hash32(key, log2cap);
-  for (uint32_t n = 0; n <= mask; ++n) {
-    const uint64_t s = __ldg(&slots[h]);
-    const uint32_t v = (uint32_t)(s >> 32);
-    if (v == HT_EMPTY_VAL) return false;
-    if ((int32_t)(uint32_t)s == key) {
-      val = v;
-      return v != HT_FILTERED;
-    }
-    h = (h + 1u) & mask;
-  }
-  return false;
-}
-
-// lookup in dimension d of a plan: direct map or hash table
-__device__ __forceinline__ bool dim_lookup(const ChunkParams &p, int d, int32_t key, uint32_t &val) {
-  if (p.dspan[d]) {
-    const uint32_t idx = (uint32_t)(key - p.dmin[d]);
-    if (idx >= p.dspan[d]) return false;
-    val = __ldg(reinterpret_cast<const uint32_t *>(p.ht[d]) + idx);
-    return val < HT_FILTERED;
-  }
-  return ht_lookup(p.ht[d], p.ht_log2[d], key, val);
-}
-
-__device__ __forceinline__ int32_t load_role(const ChunkParams &p, int r, uint64_t i) {
-  const int32_t *s = p.staged[r];
-  return s ? __ldg(&s[i]) : p.zc[r][p.row0 + i];
 }
 
 // Fused chunk kernel: per row (kRows rows per thread, strided by blockDim for
@@ -1277,7 +1208,7 @@ struct StarExKernel : ExKernel {
       p.surv_cap = (unsigned int)surv_region();
       VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
       if (timed) VX_CUDA_TRY(rec(ev_a[ek]));
-      const int kr = vec_width(p);
+      const int kr = ctx->cfg.kernel_rows ? 0 : vec_width(p);
       if (kr) {
         VX_TRY((launch_vec<false, true>(ctx, p, kr, 0, s)));
       } else {
@@ -1307,12 +1238,25 @@ struct StarExKernel : ExKernel {
     }
     launches += 1;
     if (timed) VX_CUDA_TRY(rec(ev_a[ek]));
-    const int kr = vec_width(p);
+    const int kr = ctx->cfg.kernel_rows ? 0 : vec_width(p);
     if (kr) {  // vector path
       if (smem) {
         VX_TRY((launch_vec<true, false>(ctx, p, kr, smem_bytes, s)));
       } else {
         VX_TRY((launch_vec<false, false>(ctx, p, kr, 0, s)));
+      }
+    } else if (ctx->cfg.kernel_rows == 16) {  // scalar kernel, 16 rows per thread
+      g = grid_for(ctx, (p.n + 15) / 16, threads);
+      if (smem) {
+        static bool attr16 = false;
+        if (!attr16) {
+          VX_CUDA_TRY(cudaFuncSetAttribute(star_chunk_kernel<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(16 * kSmemGroups)));
+          attr16 = true;
+        }
+        star_chunk_kernel<true, 16><<<g, threads, smem_bytes, s>>>(p);
+      } else {
+        star_chunk_kernel<false, 16><<<g, threads, 0, s>>>(p);
       }
     } else if (smem) {
       static bool attr_set = false;
@@ -1349,8 +1293,9 @@ vx_status star_graph(vx_ctx *ctx, StarExKernel &ek, const std::vector<std::share
   kp.row0 = kp.n = 0;
   std::string key((const char *)&kp, sizeof kp);
   for (const Column *c : ek.staged_cols) key.append((const char *)&c->host, sizeof(void *));
-  const uint64_t dims[7] = {ek.row_begin, ek.n_rows, ek.chunk_rows, (uint64_t)ctx->cfg.n_slots,
-                            (uint64_t)ctx->cfg.block_threads, (uint64_t)ctx->cfg.blocks_per_sm, ek.surv_rows};
+  const uint64_t dims[8] = {ek.row_begin, ek.n_rows, ek.chunk_rows, (uint64_t)ctx->cfg.n_slots,
+                            (uint64_t)ctx->cfg.block_threads, (uint64_t)ctx->cfg.blocks_per_sm, ek.surv_rows,
+                            (uint64_t)ctx->cfg.kernel_rows};
   key.append((const char *)dims, sizeof dims);
   key.append(ek.switchable.begin(), ek.switchable.end());
   key.append(ek.chunk_late.begin(), ek.chunk_late.end());
@@ -2192,6 +2137,33 @@ VX_API vx_status vx_autotune(vx_ctx *ctx, const vx_plan *plan, uint64_t sample_r
         best_ms = ms;
         best_cfg = c;
       }
+    }
+  }
+  // launch shape of the fused kernel at the best chunking: the automatic
+  // vector path against the scalar kernel at 8 or 16 rows per thread and 4
+  // or 8 resident blocks per SM
+  const int shapes[5][2] = {{0, 0}, {8, 4}, {8, 8}, {16, 4}, {16, 8}};
+  const vx_config chunked = best_cfg;
+  for (const auto &sh : shapes) {
+    vx_config c = chunked;
+    c.kernel_rows = sh[0];
+    if (sh[1]) c.blocks_per_sm = sh[1];
+    if (c.kernel_rows == chunked.kernel_rows && c.blocks_per_sm == chunked.blocks_per_sm) continue;
+    ctx->cfg = c;
+    ctx->graphs.clear();
+    double ms = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {
+      vx_result r{};
+      r.cap = UINT64_MAX;
+      if (run_star(ctx, &p, &r, true) != VX_OK) {
+        ms = 1e300;
+        break;
+      }
+      if (rep > 0) ms = std::min(ms, r.stats.ms_total);
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_cfg = c;
     }
   }
   ctx->graphs.clear();

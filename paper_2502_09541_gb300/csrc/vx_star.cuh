@@ -206,6 +206,8 @@ struct PreparedStar {
 };
 
 bool evict_unused_resident(vx_ctx *ctx);
+// a star plan one operator at a time with host intermediates
+vx_status run_star_operators(vx_ctx *ctx, const vx_plan *plan, vx_result *out);
 
 // Plans and runs a star query; with prep != nullptr it only plans (tables
 // built, accumulators zeroed) and moves the plan into *prep.

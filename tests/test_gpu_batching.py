@@ -1,5 +1,6 @@
-"""Batching: the star pipeline captured as one CUDA graph and replayed, and the
-chunk-size / ring-depth autotuner.  Results must be identical to the oracle
+"""Batching: the star pipeline captured as one CUDA graph and replayed, the
+autotuner of chunk size, ring depth and kernel launch shape, and every launch
+shape it may pick.  Results must be identical to the oracle
 (and to the executor's) on every replay."""
 import numpy as np
 import pytest
@@ -77,8 +78,33 @@ def test_autotuner_picks_a_candidate_and_keeps_results(star):
     best = vx.vx_autotune(ctx, plan, 2_000_000)
     assert best.chunk_bytes in [m << 20 for m in (8, 16, 32, 64, 128, 256)]
     assert best.n_slots in (2, 3, 4)
+    assert best.kernel_rows in (0, 8, 16) and best.blocks_per_sm in (4, 8)
     cur = vx.vx_get_config(ctx)
     assert cur.chunk_bytes == best.chunk_bytes and cur.n_slots == best.n_slots
+    assert cur.kernel_rows == best.kernel_rows and cur.blocks_per_sm == best.blocks_per_sm
     st, gid, s, c, _ = vx.vx_run_plan(ctx, plan)
     gid_e, s_e, c_e = _expect(T, fact, dims)
     assert np.array_equal(gid, gid_e) and np.array_equal(s, s_e) and np.array_equal(c, c_e)
+
+
+@pytest.mark.parametrize("rows,bps", [(0, 4), (8, 4), (8, 8), (16, 4), (16, 8)])
+@pytest.mark.parametrize("late", [vx.VX_LATE_FORCE_EARLY, vx.VX_LATE_FORCE_LATE])
+def test_kernel_shapes_bit_exact(star, rows, bps, late):
+    """Every launch shape the autotuner may pick (vector path, scalar kernel
+    at 8 or 16 rows per thread and 4 or 8 blocks per SM), in both the fused
+    and the split (late-column gather) forms."""
+    ctx, fact, dims, fid, did = star
+    cfg = vx.vx_get_config(ctx)
+    saved = (cfg.kernel_rows, cfg.blocks_per_sm, cfg.chunk_bytes)
+    cfg.kernel_rows, cfg.blocks_per_sm, cfg.chunk_bytes = rows, bps, 8 << 20
+    vx.vx_set_config(ctx, cfg)
+    try:
+        for name in ("T2_1", "T3_10"):
+            T = G.star_templates()[name]
+            st, gid, s, c, _ = vx.vx_run_plan(ctx, vx.make_plan(T, fid, did, G.STAR_ATTR_CARD, late, 1_001, 3_999_999))
+            gid_e, s_e, c_e = _expect(T, fact, dims, 1_001, 3_999_999)
+            assert st == vx.VX_OK
+            assert np.array_equal(gid, gid_e) and np.array_equal(s, s_e) and np.array_equal(c, c_e)
+    finally:
+        cfg.kernel_rows, cfg.blocks_per_sm, cfg.chunk_bytes = saved
+        vx.vx_set_config(ctx, cfg)
