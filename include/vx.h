@@ -552,16 +552,40 @@ typedef struct {
   uint32_t n_slots;     /* staging slots (0 = 3) */
 } vx_serve_opts;
 
+enum { VX_QUERY_STAR = 0, VX_QUERY_SORT = 1, VX_QUERY_JOIN = 2 };
+
 typedef struct {
   uint64_t submitted, completed, failed, cycles, bytes_h2d, active_peak;
-  double p50_ms, p99_ms, mean_ms, max_ms; /* latency from vx_submit to completion */
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency from submission to completion, all queries */
   double wall_ms;                         /* since vx_serve_start */
   uint64_t work_rows;                     /* query rows evaluated by the multi-query kernels */
   double ms_kernel;                       /* their device time (CUDA events) */
   double ms_admit;                        /* host time spent admitting (planning) queries */
   double ms_cycle;                        /* host time spent issuing scan cycles */
   double ms_wait;                         /* of which waiting for a staging slot's previous kernel */
+  uint64_t completed_kind[3];             /* per VX_QUERY_* */
+  double p50_kind_ms[3], p99_kind_ms[3];
 } vx_serve_stats;
+
+/* A sort- or join-shaped query for the serving engine (vx_submit_op). */
+typedef struct {
+  int32_t kind;                 /* VX_QUERY_SORT or VX_QUERY_JOIN */
+  int32_t key_col, val_col;     /* sort: uint64 key and uint32 row-id columns; join: build key and payload */
+  int32_t probe_col;            /* join: probe key column */
+  uint64_t row_begin, row_end;  /* sort: pairs [row_begin, row_end); join: probe rows; row_end 0 = all */
+  uint64_t *out_keys;           /* sort: the row_end - row_begin sorted keys, caller-owned until done */
+  uint32_t *out_rowids;         /* sort: their row ids */
+  uint64_t device_budget;       /* device bytes the query holds while it runs (0 = a quarter of the arena) */
+  vx_sort_opts sort;            /* sort: as for vx_sort (host_scratch, if given, must be the query's own) */
+  vx_join_opts join;            /* join: as for vx_join (VX_JOIN_DIRECT) */
+} vx_op_request;
+
+typedef struct {
+  vx_sort_stats sort;     /* sort queries */
+  vx_join_result join;    /* join queries: count, payload sum, pair fingerprint (probe rows are global) */
+  double ms_total;        /* submission to completion */
+  double ms_queued;       /* submission to admission */
+} vx_op_result;
 
 /* Starts the serving engine of a context: a thread that runs one shared
  * circular scan over the registered fact columns.  Each cycle stages one chunk
@@ -571,13 +595,25 @@ typedef struct {
  * (tables stay resident and are shared by plans with equal dimension
  * filters) and attach at the current chunk (continuous batching); a query
  * completes once it has seen every chunk of its row range.  Results equal
- * vx_run_plan's.  While serving, other calls on the context are serialised
- * with the engine. */
+ * vx_run_plan's.  Sort- and join-shaped queries (vx_submit_op) go to a second
+ * thread: each is admitted once its device budget can be carved from the
+ * arena (first come, first served) and runs as its own out-of-core operator
+ * on its own streams, overlapping the shared scan on the device.  While
+ * serving, other calls on the context are serialised with the engine. */
 vx_status vx_serve_start(vx_ctx *ctx, const vx_serve_opts *opts);
 /* Queues a plan; *ticket identifies it.  Does not block on device work. */
 vx_status vx_submit(vx_ctx *ctx, const vx_plan *plan, uint64_t *ticket);
+/* Queues a sort- or join-shaped query; *ticket identifies it (vx_wait_op,
+ * vx_poll).  The result equals vx_sort's on the range (a stable sort of the
+ * pairs [row_begin, row_end)) or vx_join's with the probe rows restricted to
+ * the range. */
+vx_status vx_submit_op(vx_ctx *ctx, const vx_op_request *req, uint64_t *ticket);
+/* Blocks until the query of an op ticket finished or timeout_ms passed
+ * (VX_E_TIMEOUT); fills out and returns the query's status. */
+vx_status vx_wait_op(vx_ctx *ctx, uint64_t ticket, vx_op_result *out, uint32_t timeout_ms);
 /* *done = 1 once the query finished; then fills out (groups, stats with
- * stats.ms_total = latency) and returns the query's status. */
+ * stats.ms_total = latency; for an op ticket only n_out = 0 and
+ * stats.ms_total) and returns the query's status. */
 vx_status vx_poll(vx_ctx *ctx, uint64_t ticket, vx_result *out, int32_t *done);
 /* Blocks until the query finished or timeout_ms passed (VX_E_TIMEOUT). */
 vx_status vx_wait(vx_ctx *ctx, uint64_t ticket, vx_result *out, uint32_t timeout_ms);

@@ -146,10 +146,27 @@ class vx_serve_stats(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("wall_ms", ctypes.c_double), ("work_rows", ctypes.c_uint64),
                 ("ms_kernel", ctypes.c_double), ("ms_admit", ctypes.c_double), ("ms_cycle", ctypes.c_double),
-                ("ms_wait", ctypes.c_double)]
+                ("ms_wait", ctypes.c_double), ("completed_kind", ctypes.c_uint64 * 3),
+                ("p50_kind_ms", ctypes.c_double * 3), ("p99_kind_ms", ctypes.c_double * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: (list(getattr(self, k)) if k.endswith("_kind") or k.endswith("_kind_ms") else getattr(self, k))
+                for k, _ in self._fields_}
+
+
+VX_QUERY_STAR, VX_QUERY_SORT, VX_QUERY_JOIN = 0, 1, 2
+
+
+class vx_op_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("key_col", ctypes.c_int32), ("val_col", ctypes.c_int32),
+                ("probe_col", ctypes.c_int32), ("row_begin", ctypes.c_uint64), ("row_end", ctypes.c_uint64),
+                ("out_keys", ctypes.c_void_p), ("out_rowids", ctypes.c_void_p), ("device_budget", ctypes.c_uint64),
+                ("sort", vx_sort_opts), ("join", vx_join_opts)]
+
+
+class vx_op_result(ctypes.Structure):
+    _fields_ = [("sort", vx_sort_stats), ("join", vx_join_result), ("ms_total", ctypes.c_double),
+                ("ms_queued", ctypes.c_double)]
 
 
 _P = ctypes.POINTER
@@ -194,6 +211,8 @@ SIGNATURES = {
     "vx_wait": ([_vp, _u64, _P(vx_result), _u32], _i32),
     "vx_serve_stats_get": ([_vp, _P(vx_serve_stats)], _i32),
     "vx_serve_stop": ([_vp], _i32),
+    "vx_submit_op": ([_vp, _P(vx_op_request), _P(_u64)], _i32),
+    "vx_wait_op": ([_vp, _u64, _P(vx_op_result), _u32], _i32),
     "vx_radix_cluster": ([_vp, _vp, _u64, _i32, _vp, _vp, _vp], _i32),
     "vx_exact_splits": ([_vp, _vp, _vp, _u32, _vp, _u32, _vp], _i32),
     "vx_merge_runs": ([_vp, _vp, _vp, _vp, _u32, _vp, _vp], _i32),
@@ -410,6 +429,20 @@ def vx_wait(ctx, ticket: int, timeout_ms: int = 600_000, cap: int = 1 << 13):
         _check(st)
     n = min(res.n_out, cap)
     return st, gid[:n], s[:n], c[:n], res.stats.as_dict()
+
+
+def vx_submit_op(ctx, req: vx_op_request) -> int:
+    t = ctypes.c_uint64()
+    _check(load().vx_submit_op(ctx, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def vx_wait_op(ctx, ticket: int, timeout_ms: int = 600_000) -> dict:
+    """Waits for a sort / join ticket; returns {"sort": ..., "join": ...,
+    "ms_total": ..., "ms_queued": ...}."""
+    r = vx_op_result()
+    _check(load().vx_wait_op(ctx, ticket, ctypes.byref(r), timeout_ms))
+    return {"sort": r.sort.as_dict(), "join": r.join.as_dict(), "ms_total": r.ms_total, "ms_queued": r.ms_queued}
 
 
 def vx_serve_stats_get(ctx) -> dict:

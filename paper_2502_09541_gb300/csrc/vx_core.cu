@@ -138,6 +138,52 @@ static vx_status init_common(vx_ctx *ctx) {
   return VX_OK;
 }
 
+vx_status open_child(vx_ctx *parent, uint64_t bytes, vx_ctx **out) {
+  *out = nullptr;
+  std::unique_ptr<vx_ctx> c(new vx_ctx());
+  {
+    std::lock_guard<std::recursive_mutex> g(parent->mu);
+    c->arena_base = (char *)parent->arena.alloc(bytes);
+    if (!c->arena_base) {
+      set_error("no room for a %llu-byte operator budget (%llu of %llu bytes free)", (unsigned long long)bytes,
+                (unsigned long long)parent->arena.largest_free(), (unsigned long long)parent->arena.capacity());
+      return VX_E_NOMEM;
+    }
+    c->arena_bytes = bytes;
+    c->own_arena = false;
+    c->cols = parent->cols;
+    for (auto &col : c->cols) col.we_registered = false;  // the parent owns the registrations
+  }
+  vx_status st = init_common(c.get());
+  if (st == VX_OK) {
+    c->cfg = parent->cfg;
+    c->cfg.use_graphs = 0;
+    c->cfg.log_timeline = 0;
+    c->cfg.log_chunk_stats = 0;
+  }
+  if (st != VX_OK) {
+    close_child(parent, c.release());
+    return st;
+  }
+  *out = c.release();
+  return VX_OK;
+}
+
+void close_child(vx_ctx *parent, vx_ctx *child) {
+  if (!child) return;
+  char *block = child->arena_base;
+  const bool leak = child->poisoned && !drain_streams(child);
+  if (leak) {  // work still running in the block: neither the block nor the streams are given back
+    child->cols.clear();
+    delete child;
+    return;
+  }
+  child->arena_base = nullptr;  // borrowed from the parent
+  vx_close(child);
+  std::lock_guard<std::recursive_mutex> g(parent->mu);
+  if (block) parent->arena.free(block);
+}
+
 }  // namespace vx
 
 using namespace vx;

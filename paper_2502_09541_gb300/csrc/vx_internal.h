@@ -211,6 +211,13 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st);
 constexpr double kDrainLimitMs = 10000;
 bool drain_streams(vx_ctx *ctx);
 
+// A context over a block of `bytes` from the parent's arena, with its own
+// streams and scalar block, sharing the parent's registered columns (the
+// parent keeps their registrations): one operator runs in it concurrently
+// with the parent's own work.  close_child gives the block back.
+vx_status open_child(vx_ctx *parent, uint64_t bytes, vx_ctx **out);
+void close_child(vx_ctx *parent, vx_ctx *child);
+
 // Enqueues every chunk of `k` as a stream/event DAG into a caller-owned ring
 // while the compute stream is being captured: the copy stream is forked from
 // and joined back into the compute stream, nothing is synchronised.

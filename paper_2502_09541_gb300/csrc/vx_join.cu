@@ -245,6 +245,7 @@ struct StreamPass : ExKernel {
   const uint64_t *keys;
   const uint64_t *payload;  // null for the probe side
   uint64_t n, R;
+  uint64_t row_base = 0;  // global row of keys[0] (the probe fingerprint uses global rows)
   std::function<vx_status(const uint64_t *, const uint64_t *, uint64_t, uint64_t, cudaStream_t)> fn;
   uint64_t size() override { return (n + R - 1) / R; }
   uint64_t rows(uint64_t it) const { return std::min(R, n - it * R); }
@@ -255,7 +256,8 @@ struct StreamPass : ExKernel {
     if (payload) h2d.push_back({payload + it * R, slot + kb(), 8 * rows(it)});
   }
   vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
-    return fn((const uint64_t *)slot, payload ? (const uint64_t *)(slot + kb()) : nullptr, rows(it), it * R, s);
+    return fn((const uint64_t *)slot, payload ? (const uint64_t *)(slot + kb()) : nullptr, rows(it), row_base + it * R,
+              s);
   }
 };
 
@@ -271,15 +273,24 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
   VX_TRY(check_ctx(ctx));
   if (!out) return VX_E_INVAL;
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
-  const double t0 = now_ms();
   const Column *bk = get_col(ctx, build_key, -1);
   const Column *bp = get_col(ctx, build_payload, -1);
   const Column *pk = get_col(ctx, probe_key, -1);
   if (!bk || !bp || !pk) return VX_E_INVAL;
+  return join_columns(ctx, bk, bp, pk, 0, pk->n_rows, opts, out);
+}
+
+namespace vx {
+
+vx_status join_columns(vx_ctx *ctx, const Column *bk, const Column *bp, const Column *pk, uint64_t probe_begin,
+                       uint64_t probe_end, const vx_join_opts *opts, vx_join_result *out) {
+  const double t0 = now_ms();
   if (bk->elem != 8 || bp->elem != 8 || pk->elem != 8 || bk->n_rows != bp->n_rows) {
     set_error("vx_join: keys and payload must be 64-bit columns; build key and payload of equal length");
     return VX_E_INVAL;
   }
+  probe_end = std::min(probe_end, pk->n_rows);
+  probe_begin = std::min(probe_begin, probe_end);
   vx_join_opts o{};
   if (opts) o = *opts;
   // load factor 0 = automatic: partitions are counted at load 0.8, then each
@@ -291,8 +302,14 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
     set_error("vx_join: bad options");
     return VX_E_INVAL;
   }
-  if (o.algorithm == VX_JOIN_RADIX) return radix_join(ctx, bk, bp, pk, o, out);
-  const uint64_t nb = bk->n_rows, np = pk->n_rows;
+  if (o.algorithm == VX_JOIN_RADIX) {
+    if (probe_begin != 0 || probe_end != pk->n_rows) {
+      set_error("vx_join: the radix join probes whole columns");
+      return VX_E_UNSUPPORTED;
+    }
+    return radix_join(ctx, bk, bp, pk, o, out);
+  }
+  const uint64_t nb = bk->n_rows, np = probe_end - probe_begin;
   vx_join_result res{};
   cudaStream_t s = ctx->s_compute;
   DevBuf accb;
@@ -441,10 +458,11 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
       double tp0 = now_ms();
       StreamPass ppass;
       ppass.ctx = ctx;
-      ppass.keys = (const uint64_t *)pk->host;
+      ppass.keys = (const uint64_t *)pk->host + probe_begin;
       ppass.payload = nullptr;
       ppass.n = np;
       ppass.R = 2 * R;
+      ppass.row_base = probe_begin;
       ppass.fn = [&](const uint64_t *k, const uint64_t *, uint64_t n, uint64_t row0, cudaStream_t st) -> vx_status {
         join_probe_kernel<4><<<grid_of(ctx, (n + 3) / 4, 256, 4), 256, 0, st>>>(k, n, row0, lo, hi, last, t, cap,
                                                                                acc);
@@ -471,3 +489,5 @@ VX_API vx_status vx_join(vx_ctx *ctx, int32_t build_key, int32_t build_payload, 
   *out = res;
   return VX_OK;
 }
+
+}  // namespace vx

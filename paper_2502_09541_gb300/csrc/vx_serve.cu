@@ -19,12 +19,16 @@
 #include <thread>
 
 #include "vx_internal.h"
+#include "vx_sort.cuh"
 #include "vx_star.cuh"
 
 namespace vx {
 
 struct ServeQuery {
   uint64_t id = 0;
+  int kind = VX_QUERY_STAR;
+  vx_op_request op{};     // sort / join queries
+  vx_op_result op_res{};
   vx_plan plan{};
   double t_submit = 0, t_admit = 0, t_done = 0;
   PreparedStar prep;
@@ -58,6 +62,11 @@ struct ServeEngine {
   double ms_wait = 0;                  // of which waiting for a slot's previous kernel
   double t_start = 0;
   std::vector<double> latencies;
+  std::vector<double> lat_kind[3];
+  // sort / join queries: their own worker thread and device budgets
+  std::thread op_th;
+  std::deque<ServeQuery *> op_pending;
+  bool op_running = false;
   // staging ring
   int S = 3;
   uint32_t max_cols = 12, max_items = 0;
@@ -104,6 +113,7 @@ static void finalize(ServeEngine &e, ServeQuery *q) {
   q->ev_done = nullptr;
   q->state = 3;
   e.latencies.push_back(q->stats.ms_total);
+  e.lat_kind[VX_QUERY_STAR].push_back(q->stats.ms_total);
 }
 
 static void fail(ServeEngine &e, ServeQuery *q, vx_status st) {
@@ -140,7 +150,7 @@ static void admit(ServeEngine &e) {
       std::swap(e.ctx->s_compute, e.s_plan);
     }
     e.ms_admit += now_ms() - t_adm;
-    if (st == VX_E_NOMEM && !e.active.empty()) return;  // wait for memory to free up
+    if (st == VX_E_NOMEM && (!e.active.empty() || e.op_running)) return;  // wait for memory to free up
     e.pending.pop_front();
     if (st == VX_OK && q->prep.G > kServeMaxGroups) {
       set_error("serving: at most %llu groups per query", (unsigned long long)kServeMaxGroups);
@@ -377,6 +387,100 @@ static void engine_loop(ServeEngine *e) {
   }
 }
 
+// runs one sort or join query in a child context over its own device budget
+static vx_status run_op(vx_ctx *child, ServeQuery *q) {
+  const vx_op_request &r = q->op;
+  if (r.kind == VX_QUERY_SORT) {
+    const Column *kc = get_col(child, r.key_col, VX_U64);
+    const Column *vc = get_col(child, r.val_col, VX_U32);
+    if (!kc || !vc || kc->n_rows != vc->n_rows) {
+      set_error("sort query: key and row-id columns must be uint64 / uint32 of equal length");
+      return VX_E_INVAL;
+    }
+    const uint64_t re = r.row_end ? std::min(r.row_end, kc->n_rows) : kc->n_rows;
+    const uint64_t rb = std::min(r.row_begin, re), n = re - rb;
+    if (n && (!r.out_keys || !r.out_rowids)) {
+      set_error("sort query: null output");
+      return VX_E_INVAL;
+    }
+    HostReg r1, r2;
+    VX_TRY(r1.add(r.out_keys, 8 * n));
+    VX_TRY(r2.add(r.out_rowids, 4 * n));
+    vx_sort_stats ss{};
+    const double t0 = now_ms();
+    const uint64_t *k = (const uint64_t *)kc->host + rb;
+    const uint32_t *v = (const uint32_t *)vc->host + rb;
+    vx_status st = r.sort.plan == VX_SORT_MERGE
+                       ? merge_sort_plan(child, k, v, n, r.out_keys, r.out_rowids, r.sort, ss)
+                       : sort_contiguous(child, k, v, (const uint64_t *)kc->dev + rb, n, r.out_keys, r.out_rowids,
+                                         r.sort, ss, 0);
+    ss.ms_total = now_ms() - t0;
+    q->op_res.sort = ss;
+    return st;
+  }
+  const Column *bk = get_col(child, r.key_col, -1);
+  const Column *bp = get_col(child, r.val_col, -1);
+  const Column *pk = get_col(child, r.probe_col, -1);
+  if (!bk || !bp || !pk) return VX_E_INVAL;
+  if (r.join.algorithm != VX_JOIN_DIRECT) {
+    set_error("join query: serving runs the direct join");
+    return VX_E_UNSUPPORTED;
+  }
+  return join_columns(child, bk, bp, pk, r.row_begin, r.row_end ? r.row_end : pk->n_rows, &r.join, &q->op_res.join);
+}
+
+// Sort / join worker: first come, first served; a query is admitted once its
+// device budget can be carved from the arena (star queries finishing free it)
+static void op_loop(ServeEngine *e) {
+  cudaSetDevice(e->ctx->device);
+  std::unique_lock<std::mutex> lk(e->mu);
+  while (!e->stop) {
+    if (e->op_pending.empty()) {
+      e->cv.wait_for(lk, std::chrono::milliseconds(5));
+      continue;
+    }
+    ServeQuery *q = e->op_pending.front();
+    const uint64_t cap = e->ctx->arena.capacity();
+    const uint64_t budget = q->op.device_budget ? q->op.device_budget : cap / 4;
+    e->op_running = true;
+    lk.unlock();
+    vx_ctx *child = nullptr;
+    vx_status st = budget > cap ? VX_E_NOMEM : open_child(e->ctx, budget, &child);
+    if (st == VX_E_NOMEM && budget <= cap) {  // wait for memory to free up
+      lk.lock();
+      e->op_running = false;
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(500));
+      lk.lock();
+      continue;
+    }
+    lk.lock();
+    e->op_pending.pop_front();
+    q->t_admit = now_ms();
+    q->state = 1;
+    lk.unlock();
+    if (st == VX_OK) st = run_op(child, q);
+    std::string err = st == VX_OK ? std::string() : std::string(vx_last_error());
+    if (child) close_child(e->ctx, child);
+    lk.lock();
+    e->op_running = false;
+    q->status = st;
+    q->error = err;
+    q->t_done = now_ms();
+    q->op_res.ms_total = q->t_done - q->t_submit;
+    q->op_res.ms_queued = q->t_admit - q->t_submit;
+    q->stats.ms_total = q->op_res.ms_total;
+    q->state = 3;
+    if (st == VX_OK) {
+      e->latencies.push_back(q->op_res.ms_total);
+      e->lat_kind[q->kind].push_back(q->op_res.ms_total);
+    } else {
+      e->failed += 1;
+    }
+    e->cv_done.notify_all();
+  }
+}
+
 static ServeEngine *engine_of(vx_ctx *ctx) { return reinterpret_cast<ServeEngine *>(ctx->serve); }
 
 void serve_shutdown(vx_ctx *ctx) {
@@ -388,6 +492,7 @@ void serve_shutdown(vx_ctx *ctx) {
   }
   e->cv.notify_all();
   if (e->th.joinable()) e->th.join();
+  if (e->op_th.joinable()) e->op_th.join();
   cudaStreamSynchronize(ctx->s_compute);
   cudaStreamSynchronize(ctx->s_h2d);
   for (auto &kv : e->all)
@@ -457,7 +562,56 @@ VX_API vx_status vx_serve_start(vx_ctx *ctx, const vx_serve_opts *opts) {
   ServeEngine *raw = e.release();
   ctx->serve = raw;
   raw->th = std::thread(engine_loop, raw);
+  raw->op_th = std::thread(op_loop, raw);
   return VX_OK;
+}
+
+VX_API vx_status vx_submit_op(vx_ctx *ctx, const vx_op_request *req, uint64_t *ticket) {
+  clear_error();
+  if (!ctx || !req || !ticket || (req->kind != VX_QUERY_SORT && req->kind != VX_QUERY_JOIN)) {
+    set_error("vx_submit_op: bad argument");
+    return VX_E_INVAL;
+  }
+  ServeEngine *e = engine_of(ctx);
+  if (!e) {
+    set_error("vx_submit_op: serving not started");
+    return VX_E_INVAL;
+  }
+  std::unique_ptr<ServeQuery> q(new ServeQuery());
+  q->kind = req->kind;
+  q->op = *req;
+  q->t_submit = now_ms();
+  {
+    std::lock_guard<std::mutex> g(e->mu);
+    if (e->fatal != VX_OK) return e->fatal;
+    q->id = e->next_id++;
+    *ticket = q->id;
+    e->op_pending.push_back(q.get());
+    e->all[q->id] = std::move(q);
+  }
+  e->cv.notify_all();
+  return VX_OK;
+}
+
+VX_API vx_status vx_wait_op(vx_ctx *ctx, uint64_t ticket, vx_op_result *out, uint32_t timeout_ms) {
+  clear_error();
+  if (!ctx) return VX_E_INVAL;
+  ServeEngine *e = engine_of(ctx);
+  if (!e) return VX_E_INVAL;
+  std::unique_lock<std::mutex> lk(e->mu);
+  auto it = e->all.find(ticket);
+  if (it == e->all.end() || it->second->kind == VX_QUERY_STAR) {
+    set_error("vx_wait_op: unknown op ticket");
+    return VX_E_INVAL;
+  }
+  ServeQuery *q = it->second.get();
+  if (!e->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return q->state == 3; })) {
+    set_error("vx_wait_op: query %llu not done within %u ms", (unsigned long long)ticket, timeout_ms);
+    return VX_E_TIMEOUT;
+  }
+  if (out) *out = q->op_res;
+  if (q->status != VX_OK) set_error("query %llu failed: %s", (unsigned long long)q->id, q->error.c_str());
+  return q->status;
 }
 
 VX_API vx_status vx_submit(vx_ctx *ctx, const vx_plan *plan, uint64_t *ticket) {
@@ -489,6 +643,11 @@ static vx_status copy_result(ServeQuery *q, vx_result *out) {
     return q->status;
   }
   if (!out) return VX_OK;
+  if (q->kind != VX_QUERY_STAR) {
+    out->n_out = 0;
+    out->stats = q->stats;
+    return VX_OK;
+  }
   const uint64_t n = q->gid.size();
   for (uint64_t i = 0; i < n && i < out->cap; ++i) {
     if (out->gid) out->gid[i] = q->gid[i];
@@ -554,19 +713,24 @@ VX_API vx_status vx_serve_stats_get(vx_ctx *ctx, vx_serve_stats *out) {
   s.bytes_h2d = e->bytes_h2d;
   s.active_peak = e->active_peak;
   s.wall_ms = now_ms() - e->t_start;
-  if (!e->latencies.empty()) {
-    std::vector<double> l = e->latencies;
+  auto pct = [](std::vector<double> l, double p) {  // nearest-rank percentile
+    if (l.empty()) return 0.0;
     std::sort(l.begin(), l.end());
-    auto pct = [&](double p) {
-      size_t i = (size_t)std::ceil(p * l.size()) ;
-      return l[std::min(l.size() - 1, i ? i - 1 : 0)];
-    };
-    s.p50_ms = pct(0.50);
-    s.p99_ms = pct(0.99);
-    s.max_ms = l.back();
+    const size_t i = (size_t)std::ceil(p * l.size());
+    return l[std::min(l.size() - 1, i ? i - 1 : 0)];
+  };
+  if (!e->latencies.empty()) {
+    s.p50_ms = pct(e->latencies, 0.50);
+    s.p99_ms = pct(e->latencies, 0.99);
+    s.max_ms = *std::max_element(e->latencies.begin(), e->latencies.end());
     double t = 0;
-    for (double v : l) t += v;
-    s.mean_ms = t / l.size();
+    for (double v : e->latencies) t += v;
+    s.mean_ms = t / e->latencies.size();
+  }
+  for (int k = 0; k < 3; ++k) {
+    s.completed_kind[k] = e->lat_kind[k].size();
+    s.p50_kind_ms[k] = pct(e->lat_kind[k], 0.50);
+    s.p99_kind_ms[k] = pct(e->lat_kind[k], 0.99);
   }
   *out = s;
   return VX_OK;

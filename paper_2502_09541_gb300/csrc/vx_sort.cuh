@@ -32,6 +32,13 @@ constexpr int kMaxSortSlots = 6;                   // staging slots of the parti
 constexpr uint64_t kPipelineRows = 48ull << 20;
 constexpr uint64_t kSplitterBufBytes = 8ull * (512 + kPLSegments + 1 + 8);
 
+// out-of-core sort (partition plan) of n contiguous host pairs; dev_keys is
+// the device-visible address of keys
+vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, const uint64_t *dev_keys, uint64_t n,
+                          uint64_t *out_keys, uint32_t *out_vals, const vx_sort_opts &o, vx_sort_stats &ss, int depth);
+// equi-join of the build columns with probe rows [probe_begin, probe_end)
+vx_status join_columns(vx_ctx *ctx, const Column *bk, const Column *bp, const Column *pk, uint64_t probe_begin,
+                       uint64_t probe_end, const vx_join_opts *opts, vx_join_result *out);
 // the radix-partitioned join of vx_join (VX_JOIN_RADIX)
 vx_status radix_join(vx_ctx *ctx, const Column *bk, const Column *bp, const Column *pk, const vx_join_opts &o,
                      vx_join_result *out);

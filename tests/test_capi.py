@@ -37,7 +37,8 @@ def test_library_exports_every_declared_symbol():
 
 
 STRUCTS = ["vx_config", "vx_pred", "vx_plan_dim", "vx_plan_gkey", "vx_plan", "vx_query_stats", "vx_result",
-           "vx_sort_opts", "vx_sort_stats", "vx_join_opts", "vx_join_result", "vx_serve_opts", "vx_serve_stats"]
+           "vx_sort_opts", "vx_sort_stats", "vx_join_opts", "vx_join_result", "vx_serve_opts", "vx_serve_stats",
+           "vx_op_request", "vx_op_result"]
 
 
 def test_struct_layouts_match_header(tmp_path):

@@ -118,3 +118,97 @@ def test_poll_unknown_ticket_and_empty_range(tables):
         assert st == vx.VX_OK and len(gid) == 0
     finally:
         vx.vx_close(c)
+
+
+def test_sort_and_join_queries_in_the_mix(tables):
+    """Sort- and join-shaped queries (log-uniform row ranges of shared sort
+    and join tables) served beside star queries: each result equals the same
+    operator run alone on the context and the oracle, and the operators'
+    work overlapped the star scan (their latency counted per kind)."""
+    fact, dims = tables
+    ns, nb, npr = 3_000_000, 400_000, 5_000_000
+    sk, sr = G.sort_input(ns, "zipf", seed=4)
+    bk, bp = G.build_side(nb)
+    pk = G.probe_side(npr, nb, 0.5, 1.0, seed=6)
+    c, fid, did = _open(1 << 30, fact, dims)
+    try:
+        kc = vx.vx_register_host_column(c, "sk", sk)
+        rc = vx.vx_register_host_column(c, "sr", sr)
+        a = vx.vx_register_host_column(c, "bk", bk)
+        b = vx.vx_register_host_column(c, "bp", bp)
+        p = vx.vx_register_host_column(c, "pk", pk)
+        rng = np.random.default_rng(9)
+        ops = []
+        for i in range(8):
+            n = ns if i % 2 == 0 else npr
+            size = int(np.exp(rng.uniform(np.log(100_000), np.log(n))))
+            rb = int(rng.integers(0, n - size + 1))
+            ops.append(("sort" if i % 2 == 0 else "join", rb, rb + size, i % 4 == 0))
+        # alone: the same operators on the context itself (sort on a copy of the range)
+        alone = []
+        for kind, rb, re, merge in ops:
+            if kind == "sort":
+                c2 = vx.vx_open(256 << 20)
+                try:
+                    k2 = vx.vx_register_host_column(c2, "k", sk[rb:re].copy())
+                    r2 = vx.vx_register_host_column(c2, "r", sr[rb:re].copy())
+                    ok, orr = np.empty(re - rb, np.uint64), np.empty(re - rb, np.uint32)
+                    o = vx.vx_sort_opts()
+                    o.plan = vx.VX_SORT_MERGE if merge else vx.VX_SORT_PARTITION
+                    vx.vx_sort(c2, k2, r2, ok, orr, o)
+                finally:
+                    vx.vx_close(c2)
+                alone.append((ok, orr))
+            else:
+                alone.append(None)
+        vx.vx_serve_start(c, chunk_rows=1 << 19, max_active=8)
+        star_mix = _mix(12, 5)
+        outs, tickets, stars = [], [], []
+        for i, (kind, rb, re, merge) in enumerate(ops):
+            name, srb, sre = star_mix[i]
+            stars.append((name, srb, sre, vx.vx_submit(c, vx.make_plan(G.star_templates()[name], fid, did,
+                                                                       G.STAR_ATTR_CARD, vx.VX_LATE_AUTO, srb, sre))))
+            req = vx.vx_op_request()
+            req.row_begin, req.row_end = rb, re
+            req.device_budget = 192 << 20
+            if kind == "sort":
+                req.kind, req.key_col, req.val_col = vx.VX_QUERY_SORT, kc, rc
+                ok, orr = np.empty(re - rb, np.uint64), np.empty(re - rb, np.uint32)
+                req.out_keys, req.out_rowids = ok.ctypes.data, orr.ctypes.data
+                req.sort.plan = vx.VX_SORT_MERGE if merge else vx.VX_SORT_PARTITION
+                outs.append((ok, orr))
+            else:
+                req.kind, req.key_col, req.val_col, req.probe_col = vx.VX_QUERY_JOIN, a, b, p
+                outs.append(None)
+            tickets.append(vx.vx_submit_op(c, req))
+            time.sleep(0.002)
+        res = [vx.vx_wait_op(c, t) for t in tickets]
+        star_res = [vx.vx_wait(c, t) for *_, t in stars]
+        stats = vx.vx_serve_stats_get(c)
+        vx.vx_serve_stop(c)
+        assert stats["failed"] == 0
+        assert stats["completed_kind"] == [len(stars), 4, 4]
+        for k in range(3):
+            assert 0 < stats["p50_kind_ms"][k] <= stats["p99_kind_ms"][k]
+        for (kind, rb, re, merge), o, al, r in zip(ops, outs, alone, res):
+            if kind == "sort":
+                ek, er = O.sort_pairs(sk[rb:re], sr[rb:re])
+                assert np.array_equal(o[0], ek) and np.array_equal(o[1], er)
+                assert np.array_equal(al[0], ek) and np.array_equal(al[1], er)
+            else:
+                j = r["join"]
+                exp = O.join(bk, bp, pk[rb:re], probe_row0=rb, nthreads=8)
+                assert (j["count"], j["payload_sum"], j["pair_fp"]) == exp
+                cj = vx.vx_open(256 << 20)
+                try:
+                    d = vx.vx_join(cj, vx.vx_register_host_column(cj, "a", bk), vx.vx_register_host_column(cj, "b", bp),
+                                   vx.vx_register_host_column(cj, "p", pk[rb:re].copy()), vx.vx_join_opts())
+                finally:
+                    vx.vx_close(cj)
+                assert (d["count"], d["payload_sum"]) == (j["count"], j["payload_sum"])
+        for (name, srb, sre, _), r in zip(stars, star_res):
+            es, ec = O.star(G.star_templates()[name], fact, dims, srb, sre, nthreads=8)
+            nz = np.nonzero(ec)[0]
+            assert r[0] == vx.VX_OK and np.array_equal(r[1], nz) and np.array_equal(r[2], es[nz])
+    finally:
+        vx.vx_close(c)
