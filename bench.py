@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--workload", default="star", choices=["star", "sort", "join", "serve"],
                     help="star: the full benchmark line; sort / join / serve: that part alone")
     ap.add_argument("--serve-plain-queries", type=int, default=100)
+    ap.add_argument("--sweep-queries", type=int, default=60, help="mixed serving queries per arrival rate (0: no sweep)")
+    ap.add_argument("--sweep-sort-pairs", type=int, default=100_000_000)
+    ap.add_argument("--sweep-join-build", type=int, default=50_000_000)
+    ap.add_argument("--sweep-join-probe", type=int, default=600_000_000)
     ap.add_argument("--serve-chunk-rows", type=int, default=1 << 21, help="rows per shared-scan chunk")
     ap.add_argument("--serve-max-active", type=int, default=32, help="queries attached to the scan at once")
     ap.add_argument("--serve-slots", type=int, default=0, help="staging slots of the shared scan (0: library default)")
@@ -293,6 +297,100 @@ def run_serving(vx, G, ctx, fid, did, args):
                         "p99_ms": round(float(np_.percentile(lat, 99)), 3), "mean_ms": round(float(np_.mean(lat)), 3),
                         "qps": round(k / wall, 2), "host_gbs": round(sum(logical_of[:k]) / wall / 1e9, 3),
                         "form": "one query at a time, first come first served (same arrivals)"}
+    return out
+
+
+def run_serving_sweep(vx, G, ctx, fid, did, args):
+    """Mixed serving at a sweep of arrival rates: 70 % star queries, 15 %
+    join-shaped (probe-row ranges of a shared join table) and 15 % sort-shaped
+    (row ranges of a shared pair table), sizes log-uniform; the saturation
+    rate is the throughput of a burst of all queries at once, then Poisson
+    arrivals at fractions of it.  Sort queries run one at a time in the
+    engine's operator thread, so they share one output and one intermediate
+    buffer here (their results are checked in the tests, not here)."""
+    import numpy as np
+    n_star = args.rows
+    ns, nb, npr = args.sweep_sort_pairs, args.sweep_join_build, args.sweep_join_probe
+    t0 = time.perf_counter()
+    sk, sr = G.sort_input(ns, "zipf", seed=8, keys=pinned_array(ns, np.uint64), rowids=pinned_array(ns, np.uint32))
+    bk, bp = G.build_side(nb, keys=pinned_array(nb, np.int64), payload=pinned_array(nb, np.int64))
+    pk = G.probe_side(npr, nb, 1.0, 1.0, out=pinned_array(npr, np.int64))
+    ok, orr = pinned_array(ns, np.uint64), pinned_array(ns, np.uint32)
+    scratch = pinned_array(12 * (ns + ns // 16) + (1 << 24), np.uint8)
+    gen = time.perf_counter() - t0
+    kc = vx.vx_register_host_column(ctx, "sweep.sk", sk)
+    rc = vx.vx_register_host_column(ctx, "sweep.sr", sr)
+    a = vx.vx_register_host_column(ctx, "sweep.bk", bk)
+    b = vx.vx_register_host_column(ctx, "sweep.bp", bp)
+    p = vx.vx_register_host_column(ctx, "sweep.pk", pk)
+    tmpls = G.star_templates()
+    rng = np.random.default_rng(11)
+
+    def draw(k):
+        qs = []
+        for _ in range(k):
+            u = rng.uniform()
+            kind = "star" if u < 0.7 else "join" if u < 0.85 else "sort"
+            n = {"star": n_star, "join": npr, "sort": ns}[kind]
+            size = int(math.exp(rng.uniform(math.log(1_000_000), math.log(n))))
+            rb = int(rng.integers(0, n - size + 1))
+            qs.append((kind, TEMPLATES[int(rng.integers(0, len(TEMPLATES)))], rb, rb + size))
+        return qs
+
+    def submit(q):
+        kind, name, rb, re = q
+        if kind == "star":
+            return ("star", vx.vx_submit(ctx, vx.make_plan(tmpls[name], fid, did, G.STAR_ATTR_CARD,
+                                                          vx.VX_LATE_AUTO, rb, re)))
+        req = vx.vx_op_request()
+        req.row_begin, req.row_end = rb, re
+        if kind == "sort":
+            req.kind, req.key_col, req.val_col = vx.VX_QUERY_SORT, kc, rc
+            req.out_keys, req.out_rowids = ok.ctypes.data, orr.ctypes.data
+            req.sort.host_scratch = scratch.ctypes.data
+            req.sort.host_scratch_bytes = scratch.nbytes
+        else:
+            req.kind, req.key_col, req.val_col, req.probe_col = vx.VX_QUERY_JOIN, a, b, p
+        return ("op", vx.vx_submit_op(ctx, req))
+
+    def run(qs, arrivals):
+        vx.vx_serve_start(ctx, chunk_rows=args.serve_chunk_rows, max_active=args.serve_max_active,
+                          n_slots=args.serve_slots)
+        t_start = time.perf_counter()
+        tickets = []
+        for q, ta in zip(qs, arrivals):
+            now = time.perf_counter() - t_start
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(submit(q))
+        for kind, t in tickets:
+            if kind == "star":
+                assert vx.vx_wait(ctx, t)[0] == vx.VX_OK
+            else:
+                vx.vx_wait_op(ctx, t)
+        wall = time.perf_counter() - t_start
+        st = vx.vx_serve_stats_get(ctx)
+        vx.vx_serve_stop(ctx)
+        return wall, st
+
+    k = args.sweep_queries
+    wall, st = run(draw(k), [0.0] * k)  # burst: the saturation throughput
+    sat = k / wall
+    out = {"mix": "70% star, 15% join, 15% sort", "queries_per_point": k, "generate_s": round(gen, 1),
+           "saturation_qps": round(sat, 2), "sort_pairs": ns, "join_build": nb, "join_probe": npr,
+           "rate_sweep": []}
+    for f in (0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
+        qs = draw(k)
+        arrivals = np.cumsum(rng.exponential(1.0 / (f * sat), k)) - 1.0 / (f * sat)
+        wall, st = run(qs, arrivals)
+        out["rate_sweep"].append({
+            "load": f, "rate_qps": round(f * sat, 2), "qps": round(k / wall, 2), "p50_ms": round(st["p50_ms"], 2),
+            "p99_ms": round(st["p99_ms"], 2),
+            "p50_ms_kind": {n: round(st["p50_kind_ms"][i], 2) for i, n in enumerate(("star", "sort", "join"))},
+            "p99_ms_kind": {n: round(st["p99_kind_ms"][i], 2) for i, n in enumerate(("star", "sort", "join"))},
+            "completed_kind": dict(zip(("star", "sort", "join"), st["completed_kind"])), "failed": st["failed"]})
+    for col in (kc, rc, a, b, p):
+        vx.vx_unregister_host_column(ctx, col)
     return out
 
 
@@ -744,6 +842,9 @@ def run_ours(args):
                                                                          "launch_ceiling")}
 
     serving = run_serving(vx, G, ctx, fid, did, args) if not args.no_extras and args.serve_queries > 0 else None
+    if serving is not None and args.sweep_queries > 0:
+        serving["mixed"] = run_serving_sweep(vx, G, ctx, fid, did, args)
+        serving["rate_sweep"] = serving["mixed"]["rate_sweep"]
     clustered = run_clustered(vx, G, ctx, did, args) if not args.no_extras and args.clustered_rows else None
 
     line = {
