@@ -87,7 +87,9 @@ typedef struct {
                                path, 4 rows per thread read as 16-byte column vectors, where the
                                columns allow; else 8 rows), 8 or 16 = the scalar kernel with that
                                many rows per thread and at most blocks_per_sm blocks per SM */
-  int32_t reserved;
+  uint32_t lookback_spin_limit; /* polls a radix sort pass makes of one predecessor tile's published
+                               count before it gives up, sets its error word and the call returns
+                               VX_E_TIMEOUT (0 = 2^20) */
 } vx_config;
 
 /* ---------------------------------------------------------------- lifetime */

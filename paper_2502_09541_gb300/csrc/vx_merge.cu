@@ -287,7 +287,7 @@ struct RunPass : ExKernel {
   vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
     RadixBufs b = bufs(slot);
     const uint64_t m = rows(it);
-    VX_TRY(radix_sort_enqueue(b, m, temp(slot), s, ctx->num_sms));
+    VX_TRY(radix_sort_enqueue(b, m, temp(slot), s, ctx->num_sms, 8, ctx->cfg.lookback_spin_limit));
     const uint64_t nf = (m + kFenceStride - 1) / kFenceStride;
     run_fences_kernel<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>((nf + 255) / 256, 1024)), 256, 0, s>>>(
         b.keys[0], b.keys[1], radix_state_of(temp(slot)), m, d_fences + it * fences_per_run);

@@ -38,11 +38,12 @@ struct RadixBufs {
 };
 
 // per-pass device state: cur[0..8], skip[0..7], an error word (a look-back
-// wait that gave up), totals[256], base[257]
+// wait that gave up), the polls a look-back makes of one predecessor word
+// before giving up, totals[256], base[257]
 struct RadixState {
   int32_t cur[12];
   int32_t skip[12];
-  uint32_t err, pad;
+  uint32_t err, spin_limit;
   uint64_t totals[kRxDigits];
   uint64_t base[kRxDigits + 1];
 };

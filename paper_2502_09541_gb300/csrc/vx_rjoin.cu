@@ -326,7 +326,7 @@ struct RjPartitionPass : ExKernel {
     RadixBufs b = bufs(slot);
     const uint64_t m = rows(it);
     rj_iota_kernel<<<grid_for(ctx, m, 256, 8), 256, 0, s>>>(b.vals[0], m);
-    VX_TRY(radix_sort_enqueue(b, m, temp(slot), s, ctx->num_sms, npass));
+    VX_TRY(radix_sort_enqueue(b, m, temp(slot), s, ctx->num_sms, npass, ctx->cfg.lookback_spin_limit));
     const RadixState *st = radix_state_of(temp(slot));
     VX_TRY(find_boundary_enqueue(ctx, b, st, npass, m, bits, bnd(slot), carry(slot), s));
     if (payload)
@@ -692,7 +692,7 @@ VX_API vx_status vx_radix_cluster(vx_ctx *ctx, const uint64_t *keys, uint64_t n,
   const int npass = bits / 8;
   if (n) VX_CUDA_TRY(cudaMemcpyAsync(b.keys[0], keys, 8 * n, cudaMemcpyHostToDevice, s));
   rj_iota_kernel<<<grid_for(ctx, m, 256, 8), 256, 0, s>>>(b.vals[0], n);
-  VX_TRY(radix_sort_enqueue(b, n, temp, s, ctx->num_sms, npass));
+  VX_TRY(radix_sort_enqueue(b, n, temp, s, ctx->num_sms, npass, ctx->cfg.lookback_spin_limit));
   const RadixState *st = radix_state_of(temp);
   VX_TRY(find_boundary_enqueue(ctx, b, st, npass, n, bits, bnd, carry, s));
   RadixState h;

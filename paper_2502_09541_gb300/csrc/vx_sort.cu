@@ -161,11 +161,12 @@ __global__ void __launch_bounds__(kRxThreads) rx_byte_hist(const RadixBufs b, ui
     if ((&h[0][0])[i]) atomicAdd(&bh[i], (unsigned long long)(&h[0][0])[i]);
 }
 
-__global__ void rx_init_state(RadixState *st, const unsigned long long *bh, uint64_t n) {
+__global__ void rx_init_state(RadixState *st, const unsigned long long *bh, uint64_t n, uint32_t spin_limit) {
   const int p = threadIdx.x;  // 8 threads
   if (p == 0) {
     st->cur[0] = 0;
     st->err = 0;
+    st->spin_limit = spin_limit;
   }
   if (p < 8) {
     int full = 0;
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_downsweep(RadixBufs b, Radix
       volatile unsigned long long *sw = status + (uint64_t)tile * kRxDigits + d;
       *sw = rx_status_word(tile == 0 ? kRxFlagIncl : kRxFlagAgg, pass, run);
       uint64_t prefix = 0;  // pairs of digit d in the tiles before this one
+      const uint32_t limit = st->spin_limit;
       for (uint32_t t = tile; t > 0;) {  // look back over the predecessors' words
         --t;
         const volatile unsigned long long *pw = status + (uint64_t)t * kRxDigits + d;
@@ -293,14 +295,15 @@ __global__ void __launch_bounds__(kRxThreads, 2) rx_downsweep(RadixBufs b, Radix
         uint32_t spins = 0;
         while ((word >> 62) == 0 || (int)((word >> 59) & 7u) != pass) {
           // give up after the limit, or at once when another tile already gave up
-          if (++spins > kRxSpinLimit || ((spins & 1023u) == 0 && *(volatile uint32_t *)&st->err)) {
-            spins = kRxSpinLimit + 1;
+          if (++spins > limit || ((spins & 1023u) == 0 && *(volatile uint32_t *)&st->err)) {
+            spins = limit + 1;
             break;
           }
           __nanosleep(32);
           word = *pw;
         }
-        if (spins > kRxSpinLimit) {  // a predecessor never published: report, keep going
+        if (spins > limit) {  // a predecessor never published: report, keep going (a partial
+                              // prefix only lowers this tile's positions, all inside the pass's n)
           atomicOr(&st->err, 1u);
           break;
         }
@@ -510,7 +513,8 @@ static vx_status radix_result(char *temp, cudaStream_t s, int *cur) {
 // Enqueues a stable LSD radix sort of b.keys[0]/b.vals[0] (n pairs) on s by
 // the low npass bytes of the key (8: the whole key).  The sorted pairs end in
 // buffer st->cur[npass] (0 or 1).
-vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms, int npass) {
+vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms, int npass,
+                             uint32_t spin_limit) {
   uint32_t nt = ntiles_of(n);
   RadixState *st = radix_state_of(temp);
   unsigned long long *bh = (unsigned long long *)(temp + kStateBytes);
@@ -528,7 +532,7 @@ vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s
   VX_CUDA_TRY(cudaMemsetAsync(tickets, 0, kTicketBytes + (uint64_t)kRxDigits * nt * 8, s));
   int g = (int)std::min<uint64_t>((n + kRxThreads - 1) / kRxThreads, (uint64_t)num_sms * 4);
   rx_byte_hist<<<g, kRxThreads, 0, s>>>(b, n, bh);
-  rx_init_state<<<1, 32, 0, s>>>(st, bh, n);
+  rx_init_state<<<1, 32, 0, s>>>(st, bh, n, spin_limit ? spin_limit : kRxSpinLimit);
   rx_init_bases<<<8, kRxDigits, 0, s>>>(bh, bases);
   for (int pass = 0; pass < npass; ++pass)  // a skipped pass returns at once and keeps the buffer
     rx_downsweep<false, true><<<nt, kRxThreads, kRxScatterSmem, s>>>(b, st, pass, n, 8 * pass, nullptr, 0, nullptr, nt,
@@ -621,7 +625,7 @@ vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uin
   char *temp = q + 2 * ((4 * m + 255) & ~255ull);
   sample_keys_kernel<<<ctx->num_sms * 2, 256, 0, s>>>(dev_keys, n, m, seed, b.keys[0], b.vals[0]);
   VX_CUDA_TRY(cudaGetLastError());
-  VX_TRY(radix_sort_enqueue(b, m, temp, s, ctx->num_sms));
+  VX_TRY(radix_sort_enqueue(b, m, temp, s, ctx->num_sms, 8, ctx->cfg.lookback_spin_limit));
   int cur = 0;
   VX_TRY(radix_result(temp, s, &cur));
   *sorted_ptr = b.keys[cur];
@@ -826,7 +830,7 @@ struct SortPass : ExKernel {
     }
   }
   vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
-    VX_TRY(radix_sort_enqueue(bufs(slot), job_n[it], temp(slot), s, ctx->num_sms));
+    VX_TRY(radix_sort_enqueue(bufs(slot), job_n[it], temp(slot), s, ctx->num_sms, 8, ctx->cfg.lookback_spin_limit));
     rx_publish<<<1, 1, 0, s>>>(radix_state_of(temp(slot)), 8, ctx->d_scalars + 64 + (it % S));
     VX_CUDA_TRY(cudaGetLastError());
     return VX_OK;
@@ -1197,7 +1201,7 @@ VX_API vx_status vx_radix_sort_pairs(vx_ctx *ctx, const uint64_t *keys, const ui
   cudaStream_t s = ctx->s_compute;
   VX_CUDA_TRY(cudaMemcpyAsync(b.keys[0], keys, 8 * n, cudaMemcpyHostToDevice, s));
   VX_CUDA_TRY(cudaMemcpyAsync(b.vals[0], vals, 4 * n, cudaMemcpyHostToDevice, s));
-  VX_TRY(radix_sort_enqueue(b, n, temp, s, ctx->num_sms));
+  VX_TRY(radix_sort_enqueue(b, n, temp, s, ctx->num_sms, 8, ctx->cfg.lookback_spin_limit));
   int cur = 0;
   VX_TRY(radix_result(temp, s, &cur));
   VX_CUDA_TRY(cudaMemcpyAsync(out_keys, b.keys[cur], 8 * n, cudaMemcpyDeviceToHost, s));

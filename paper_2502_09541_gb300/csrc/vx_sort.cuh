@@ -13,7 +13,10 @@ constexpr int kMlpParams = 3 * kMlpHidden + 1;
 
 uint64_t radix_temp_bytes(uint64_t cap);
 RadixState *radix_state_of(char *temp);
-vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms, int npass = 8);
+// spin_limit: polls of one predecessor's look-back word before the pass gives
+// up and sets the error word (0 = the default of 2^20)
+vx_status radix_sort_enqueue(RadixBufs b, uint64_t n, char *temp, cudaStream_t s, int num_sms, int npass = 8,
+                             uint32_t spin_limit = 0);
 // after radix_sort_enqueue on s: publishes to a mapped host word the buffer
 // holding the result (low byte), the executed passes (next byte) and whether
 // a look-back wait gave up (bit 16)

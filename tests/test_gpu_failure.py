@@ -82,3 +82,28 @@ def test_progressing_pipeline_outlives_its_wait_limit(star_ctx):
     es, ec = O.star(T, fact, dims, nthreads=16)
     nz = np.nonzero(ec)[0]
     assert np.array_equal(gid, nz) and np.array_equal(s, es[nz]) and np.array_equal(cnt, ec[nz])
+
+
+def test_radix_lookback_limit_gives_up_with_a_status():
+    """The one-sweep radix passes wait for their predecessor tiles' published
+    counts with a bounded poll.  A limit of one poll makes some waits run out
+    (thousands of tiles race): the pass records it in its error word, keeps
+    every write inside the buffers, and the call returns VX_E_TIMEOUT instead
+    of hanging; the same context then sorts correctly at the default limit."""
+    n = 20_000_000
+    k, r = G.sort_input(n, "uniform", seed=2)
+    c = vx.vx_open(1 << 30)
+    try:
+        cfg = vx.vx_get_config(c)
+        cfg.lookback_spin_limit = 1
+        vx.vx_set_config(c, cfg)
+        with pytest.raises(vx.VxError) as e:
+            vx.vx_radix_sort_pairs(c, k, r)
+        assert e.value.status == vx.VX_E_TIMEOUT and "look-back" in str(e.value)
+        cfg.lookback_spin_limit = 0
+        vx.vx_set_config(c, cfg)
+        ok, orr = vx.vx_radix_sort_pairs(c, k, r)
+    finally:
+        vx.vx_close(c)
+    ek, er = O.sort_pairs(k, r)
+    assert np.array_equal(ok, ek) and np.array_equal(orr, er)
