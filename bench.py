@@ -887,6 +887,12 @@ def run_ours(args):
         line["sort"] = run_sort_extra(vx, G, args)
         line["join"] = run_join_extra(vx, G, args)
     line["link_frac"] = line["link"]["link_frac"]
+    busy = [v["link_busy"] for v in overlap.values() if v]
+    # fraction of each query's pipeline time the host-to-device copy engine
+    # was busy (per-chunk timeline): 1.0 = copies back to back, fully
+    # overlapping the kernels, whatever rate the link gives at the time
+    line["copy_engine_busy"] = round(min(busy), 4) if busy else None
+    line["roofline"]["step"]["copy_engine_busy"] = line["copy_engine_busy"]
     line["summary"] = summarize(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -927,7 +933,8 @@ def summarize(line):
            "star_gbs": {k: f[k]["value"] for k in ("plain", "learned")},
            "star_link_frac": {k: f[k]["step_roofline"]["link_frac"] for k in ("plain", "learned")},
            "star_step_roofline_frac": {k: f[k]["step_roofline"]["frac"] for k in ("plain", "learned")},
-           "fused_kernel_hbm_frac": line["roofline"].get("frac")}
+           "fused_kernel_hbm_frac": line["roofline"].get("frac"),
+           "copy_engine_busy": line.get("copy_engine_busy")}
     sv = line.get("serving")
     if sv:
         out["serving_ms"] = {"p50": sv.get("p50_ms"), "p99": sv.get("p99_ms")}

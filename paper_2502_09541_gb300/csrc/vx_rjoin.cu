@@ -38,6 +38,10 @@ constexpr int kRjSeg = 4096;               // boundary entries per block of the 
 constexpr int kRjWarps = 8;
 constexpr int kRjTable = 256;              // slots of a warp's shared-memory table
 constexpr uint64_t kRjEmpty = ~0ull;       // empty slot key; a build key equal to it is kept aside
+// a group with more probe tuples than this (skewed probe keys) is joined by
+// kRjHeavyParts blocks at once instead of one warp
+constexpr uint64_t kRjHeavy = 8192;
+constexpr uint32_t kRjHeavyCap = 1u << 16, kRjHeavyParts = 32;
 
 __device__ __forceinline__ uint64_t rj_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -152,7 +156,78 @@ struct RjJoinParams {
   uint64_t probe_chunk_rows;     // R of the probe side's partition pass
   uint32_t key_shift;            // the group bits: the in-group hash uses the key above them
   RjAcc *acc;
+  uint32_t *heavy;               // groups left to rj_heavy_kernel (at most kRjHeavyCap)
+  unsigned int *heavy_n;
 };
+
+// the build tuples of group g into an open-addressing table of cap slots in
+// shared memory (threads t = 0, stride of them cooperate); a build key equal
+// to the empty marker goes to sent[0..1]
+__device__ __forceinline__ void rj_build_group(const RjJoinParams &p, uint64_t g, uint32_t cap, uint32_t t,
+                                               uint32_t stride, unsigned long long *tkey, unsigned long long *tpay,
+                                               unsigned long long *sent) {
+  for (uint32_t c = 0; c < p.na; ++c) {
+    const uint32_t *bd = p.abnd + (uint64_t)c * (p.ng + 1);
+    const uint64_t at = p.abase[c] + (bd[g] - bd[0]);
+    const uint32_t m = bd[g + 1] - bd[g];
+    for (uint32_t i = t; i < m; i += stride) {
+      const uint64_t k = p.akeys[at + i], pay = p.apay[at + i];
+      if (k == kRjEmpty) {
+        if (atomicExch(&sent[0], 1ull)) atomicOr(&p.acc->err, ERR_DUPKEY);
+        sent[1] = pay;
+        continue;
+      }
+      uint32_t h = (uint32_t)(rj_mix(k >> p.key_shift) & (cap - 1));
+      for (uint32_t step = 0; step < cap; ++step) {
+        const unsigned long long old = atomicCAS(&tkey[h], kRjEmpty, k);
+        if (old == kRjEmpty) {
+          tpay[h] = pay;
+          break;
+        }
+        if (old == k) {
+          atomicOr(&p.acc->err, ERR_DUPKEY);
+          break;
+        }
+        h = (h + 1) & (cap - 1);
+      }
+    }
+  }
+}
+
+// one probe tuple against group g: the shared-memory table, or (in_smem
+// false) a scan of the group's build tuples
+__device__ __forceinline__ bool rj_probe_one(const RjJoinParams &p, uint64_t g, uint64_t k, bool in_smem,
+                                             uint32_t cap, const unsigned long long *tkey,
+                                             const unsigned long long *tpay, const unsigned long long *sent,
+                                             uint64_t &pay) {
+  if (in_smem) {
+    if (k == kRjEmpty) {
+      pay = sent[1];
+      return sent[0] != 0;
+    }
+    uint32_t h = (uint32_t)(rj_mix(k >> p.key_shift) & (cap - 1));
+    for (uint32_t step = 0; step < cap; ++step) {
+      const unsigned long long kk = tkey[h];
+      if (kk == k) {
+        pay = tpay[h];
+        return true;
+      }
+      if (kk == kRjEmpty) return false;
+      h = (h + 1) & (cap - 1);
+    }
+    return false;
+  }
+  for (uint32_t ca = 0; ca < p.na; ++ca) {
+    const uint32_t *ad = p.abnd + (uint64_t)ca * (p.ng + 1);
+    const uint64_t aat = p.abase[ca] + (ad[g] - ad[0]);
+    for (uint32_t j = 0; j < ad[g + 1] - ad[g]; ++j)
+      if (p.akeys[aat + j] == k) {
+        pay = p.apay[aat + j];
+        return true;
+      }
+  }
+  return false;
+}
 
 __global__ void __launch_bounds__(32 * kRjWarps) rj_join_kernel(const RjJoinParams p) {
   __shared__ unsigned long long tkey[kRjWarps][kRjTable];
@@ -162,13 +237,29 @@ __global__ void __launch_bounds__(32 * kRjWarps) rj_join_kernel(const RjJoinPara
   unsigned long long cnt = 0, psum = 0, fp = 0;
   const uint64_t warps = (uint64_t)gridDim.x * kRjWarps;
   for (uint64_t g = blockIdx.x * (uint64_t)kRjWarps + w; g < p.ng; g += warps) {
-    // build tuples of the group, per chunk
-    uint64_t nbuild = 0;
+    // build and probe tuples of the group, over the chunks
+    uint64_t nbuild = 0, nprobe = 0;
     for (uint32_t c = lane; c < p.na; c += 32) {
       const uint32_t *bd = p.abnd + (uint64_t)c * (p.ng + 1);
       nbuild += bd[g + 1] - bd[g];
     }
-    for (int off = 16; off > 0; off >>= 1) nbuild += __shfl_xor_sync(0xffffffffu, nbuild, off);
+    for (uint32_t c = lane; c < p.nb; c += 32) {
+      const uint32_t *bd = p.bbnd + (uint64_t)c * (p.ng + 1);
+      nprobe += bd[g + 1] - bd[g];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      nbuild += __shfl_xor_sync(0xffffffffu, nbuild, off);
+      nprobe += __shfl_xor_sync(0xffffffffu, nprobe, off);
+    }
+    if (nprobe > kRjHeavy) {  // many blocks take this group in the second kernel, if the list has room
+      unsigned int slot = 0;
+      if (lane == 0) slot = atomicAdd(p.heavy_n, 1u);
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (slot < kRjHeavyCap) {
+        if (lane == 0) p.heavy[slot] = (uint32_t)g;
+        continue;
+      }
+    }
     const bool in_smem = nbuild <= kRjTable / 2;
     uint32_t cap = 32;
     while (cap < 2 * nbuild && cap < kRjTable) cap <<= 1;
@@ -176,72 +267,16 @@ __global__ void __launch_bounds__(32 * kRjWarps) rj_join_kernel(const RjJoinPara
       for (uint32_t i = lane; i < cap; i += 32) tkey[w][i] = kRjEmpty;
       if (lane == 0) sent[w][0] = 0;
       __syncwarp();
-      for (uint32_t c = lane; c < p.na; c += 32) {
-        const uint32_t *bd = p.abnd + (uint64_t)c * (p.ng + 1);
-        const uint64_t at = p.abase[c] + (bd[g] - bd[0]);
-        for (uint32_t i = 0; i < bd[g + 1] - bd[g]; ++i) {
-          const uint64_t k = p.akeys[at + i], pay = p.apay[at + i];
-          if (k == kRjEmpty) {
-            if (atomicExch(&sent[w][0], 1ull)) atomicOr(&p.acc->err, ERR_DUPKEY);
-            sent[w][1] = pay;
-            continue;
-          }
-          uint32_t h = (uint32_t)(rj_mix(k >> p.key_shift) & (cap - 1));
-          for (uint32_t step = 0; step < cap; ++step) {
-            const unsigned long long old = atomicCAS(&tkey[w][h], kRjEmpty, k);
-            if (old == kRjEmpty) {
-              tpay[w][h] = pay;
-              break;
-            }
-            if (old == k) {
-              atomicOr(&p.acc->err, ERR_DUPKEY);
-              break;
-            }
-            h = (h + 1) & (cap - 1);
-          }
-        }
-      }
+      rj_build_group(p, g, cap, lane, 32, tkey[w], tpay[w], sent[w]);
       __syncwarp();
     }
-    // probe tuples of the group, per chunk
-    for (uint32_t c = lane; c < p.nb; c += 32) {
+    for (uint32_t c = 0; c < p.nb; ++c) {  // lanes stripe each chunk's probe tuples of the group
       const uint32_t *bd = p.bbnd + (uint64_t)c * (p.ng + 1);
       const uint64_t at = p.bbase[c] + (bd[g] - bd[0]);
       const uint32_t m = bd[g + 1] - bd[g];
-      for (uint32_t i = 0; i < m; ++i) {
-        const uint64_t k = p.bkeys[at + i];
-        bool hit = false;
+      for (uint32_t i = lane; i < m; i += 32) {
         uint64_t pay = 0;
-        if (in_smem) {
-          if (k == kRjEmpty) {
-            hit = sent[w][0] != 0;
-            pay = sent[w][1];
-          } else {
-            uint32_t h = (uint32_t)(rj_mix(k >> p.key_shift) & (cap - 1));
-            for (uint32_t step = 0; step < cap; ++step) {
-              const unsigned long long kk = tkey[w][h];
-              if (kk == k) {
-                hit = true;
-                pay = tpay[w][h];
-                break;
-              }
-              if (kk == kRjEmpty) break;
-              h = (h + 1) & (cap - 1);
-            }
-          }
-        } else {  // a group too large for the table: scan its build tuples
-          for (uint32_t ca = 0; ca < p.na && !hit; ++ca) {
-            const uint32_t *ad = p.abnd + (uint64_t)ca * (p.ng + 1);
-            const uint64_t aat = p.abase[ca] + (ad[g] - ad[0]);
-            for (uint32_t j = 0; j < ad[g + 1] - ad[g]; ++j)
-              if (p.akeys[aat + j] == k) {
-                hit = true;
-                pay = p.apay[aat + j];
-                break;
-              }
-          }
-        }
-        if (hit) {
+        if (rj_probe_one(p, g, p.bkeys[at + i], in_smem, cap, tkey[w], tpay[w], sent[w], pay)) {
           const uint64_t row = (uint64_t)c * p.probe_chunk_rows + p.brows[at + i];
           cnt += 1;
           psum += pay;
@@ -260,6 +295,75 @@ __global__ void __launch_bounds__(32 * kRjWarps) rj_join_kernel(const RjJoinPara
     atomicAdd(&p.acc->count, cnt);
     atomicAdd(&p.acc->psum, psum);
     atomicAdd(&p.acc->fp, fp);
+  }
+}
+
+// groups with many probe tuples: work item (heavy group h, part q) of
+// kRjHeavyParts per group; the block builds the group's table in shared
+// memory and probes every kRjHeavyParts-th stripe of 256 tuples of each chunk
+__global__ void __launch_bounds__(256) rj_heavy_kernel(const RjJoinParams p) {
+  __shared__ unsigned long long tkey[kRjTable], tpay[kRjTable], sent[2];
+  __shared__ unsigned long long red[3][8];
+  const unsigned int nh = *p.heavy_n < kRjHeavyCap ? *p.heavy_n : kRjHeavyCap;
+  unsigned long long cnt = 0, psum = 0, fp = 0;
+  for (uint64_t wi = blockIdx.x; wi < (uint64_t)nh * kRjHeavyParts; wi += gridDim.x) {
+    const uint64_t g = p.heavy[wi / kRjHeavyParts];
+    const uint32_t part = (uint32_t)(wi % kRjHeavyParts);
+    uint64_t nbuild = 0;
+    for (uint32_t c = 0; c < p.na; ++c) {
+      const uint32_t *bd = p.abnd + (uint64_t)c * (p.ng + 1);
+      nbuild += bd[g + 1] - bd[g];
+    }
+    const bool in_smem = nbuild <= kRjTable / 2;
+    uint32_t cap = 32;
+    while (cap < 2 * nbuild && cap < kRjTable) cap <<= 1;
+    __syncthreads();  // the previous item's probes are done with the table
+    if (in_smem) {
+      for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) tkey[i] = kRjEmpty;
+      if (threadIdx.x == 0) sent[0] = 0;
+      __syncthreads();
+      rj_build_group(p, g, cap, threadIdx.x, blockDim.x, tkey, tpay, sent);
+      __syncthreads();
+    }
+    for (uint32_t c = 0; c < p.nb; ++c) {
+      const uint32_t *bd = p.bbnd + (uint64_t)c * (p.ng + 1);
+      const uint64_t at = p.bbase[c] + (bd[g] - bd[0]);
+      const uint32_t m = bd[g + 1] - bd[g];
+      for (uint64_t i = (uint64_t)part * 256 + threadIdx.x; i < m; i += (uint64_t)kRjHeavyParts * 256) {
+        uint64_t pay = 0;
+        if (rj_probe_one(p, g, p.bkeys[at + i], in_smem, cap, tkey, tpay, sent, pay)) {
+          const uint64_t row = (uint64_t)c * p.probe_chunk_rows + p.brows[at + i];
+          cnt += 1;
+          psum += pay;
+          fp += rj_mix(row ^ ((pay << 17) | (pay >> 47)));
+        }
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    psum += __shfl_down_sync(0xffffffffu, psum, off);
+    fp += __shfl_down_sync(0xffffffffu, fp, off);
+  }
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = cnt;
+    red[1][w] = psum;
+    red[2][w] = fp;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0, f = 0;
+    for (int k = 0; k < 8; ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      f += red[2][k];
+    }
+    if (a) {
+      atomicAdd(&p.acc->count, a);
+      atomicAdd(&p.acc->psum, b);
+      atomicAdd(&p.acc->fp, f);
+    }
   }
 }
 
@@ -356,7 +460,7 @@ struct RjPartitionPass : ExKernel {
 // one range of groups and where its pieces sit in a slot
 struct RjRange {
   uint64_t g0, g1;
-  uint64_t akeys, apay, bkeys, brows, abnd, bbnd, abase, bbase, bytes;  // byte offsets in the slot
+  uint64_t akeys, apay, bkeys, brows, abnd, bbnd, abase, bbase, heavy, bytes;  // byte offsets in the slot
   uint64_t na_tuples, nb_tuples;
 };
 
@@ -423,10 +527,14 @@ struct RjJoinPass : ExKernel {
     p.probe_chunk_rows = RB;
     p.key_shift = (uint32_t)bits;
     p.acc = acc;
+    p.heavy = (uint32_t *)(slot + r.heavy);
+    p.heavy_n = (unsigned int *)(slot + r.heavy + 4ull * kRjHeavyCap);
     const size_t e = it % S;
+    VX_CUDA_TRY(cudaMemsetAsync(p.heavy_n, 0, 4, s));
     if (!ev0.empty()) VX_CUDA_TRY(cudaEventRecord(ev0[e], s));
     const uint64_t blocks = (p.ng + kRjWarps - 1) / kRjWarps;
     rj_join_kernel<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)ctx->num_sms * 8), 32 * kRjWarps, 0, s>>>(p);
+    rj_heavy_kernel<<<(unsigned)ctx->num_sms * 4, 256, 0, s>>>(p);
     VX_CUDA_TRY(cudaGetLastError());
     if (!ev1.empty()) VX_CUDA_TRY(cudaEventRecord(ev1[e], s));
     return VX_OK;
@@ -557,7 +665,8 @@ vx_status radix_join(vx_ctx *ctx, const Column *bk, const Column *bp, const Colu
     r.bbnd = r.abnd + al(4 * NA * ng1);
     r.abase = r.bbnd + al(4 * NB * ng1);
     r.bbase = r.abase + 8 * NA;
-    r.bytes = r.abase + al(8 * (NA + NB));
+    r.heavy = r.abase + al(8 * (NA + NB));
+    r.bytes = r.heavy + al(4 * kRjHeavyCap + 256);
   };
   RjJoinPass jp;
   jp.ctx = ctx;
