@@ -138,20 +138,21 @@ def measured_peaks():
 
 
 STAR_KERNEL_END = {"vx_star.cu": b"// ---- end of the fused chunk kernel's device code",
-                   "vx_star.cuh": b"// ---- end of what the fused chunk kernel's device code reads"}
+                   "vx_star.cuh": b"// ---- end of what the fused chunk kernel's device code reads",
+                   "vx_probe.cuh": None}  # the row-logic helpers: the whole file
 
 
 def kernel_source_digest():
     """sha256 of the fused star kernel's device code: vx_star.cu and
-    vx_star.cuh, each up to its end marker (ties a stored ncu figure to that
-    code)."""
+    vx_star.cuh, each up to its end marker, and vx_probe.cuh (ties a stored
+    ncu figure to that code)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2502_09541_gb300", "csrc")
-    for f in ("vx_star.cu", "vx_star.cuh"):
+    for f, end in STAR_KERNEL_END.items():
         with open(os.path.join(csrc, f), "rb") as fh:
             text = fh.read()
-        cut = text.find(STAR_KERNEL_END[f])
+        cut = text.find(end) if end else -1
         h.update(text if cut < 0 else text[:cut])
     return h.hexdigest()
 

@@ -12,7 +12,7 @@ def _copy_tree(tmp_path):
     root = tmp_path / "repo"
     csrc = root / "paper_2502_09541_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for f in ("vx_star.cu", "vx_star.cuh"):
+    for f in ("vx_star.cu", "vx_star.cuh", "vx_probe.cuh"):
         shutil.copy(os.path.join(bench.ROOT, "paper_2502_09541_gb300", "csrc", f), csrc / f)
     (root / "profiles").mkdir()
     shutil.copy(os.path.join(bench.ROOT, "profiles", "star_chunk_kernel_traffic.txt"),
@@ -45,3 +45,13 @@ def test_digest_follows_device_code_only(tmp_path, monkeypatch):
         _edit(csrc2 / f, True, bench.STAR_KERNEL_END[f])
         assert bench.kernel_source_digest() != base
         assert bench.traffic_ratio() is None
+
+
+def test_digest_covers_the_row_logic_header(tmp_path, monkeypatch):
+    root, csrc = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    base = bench.kernel_source_digest()
+    p = csrc / "vx_probe.cuh"
+    p.write_bytes(p.read_bytes() + b"\n// edited\n")
+    assert bench.kernel_source_digest() != base
+    assert bench.traffic_ratio() is None
