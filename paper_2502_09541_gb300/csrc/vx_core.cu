@@ -157,6 +157,8 @@ vx_status open_child(vx_ctx *parent, uint64_t bytes, vx_ctx **out) {
   vx_status st = init_common(c.get());
   if (st == VX_OK) {
     c->cfg = parent->cfg;
+    // staging slots in proportion to the block: at most a sixteenth of it per chunk
+    c->cfg.chunk_bytes = std::min<uint64_t>(parent->cfg.chunk_bytes, std::max<uint64_t>(bytes / 16, 1ull << 20));
     c->cfg.use_graphs = 0;
     c->cfg.log_timeline = 0;
     c->cfg.log_chunk_stats = 0;
