@@ -63,12 +63,27 @@ __device__ __forceinline__ bool ht_lookup(const uint64_t *__restrict__ slots, ui
   return false;
 }
 
+// value idx of a direct map of vb-byte values (1, 2 or 4), widened to 32
+// bits: the two largest values of a narrow width are the markers, which map
+// to HT_EMPTY_VAL (no such key) and HT_FILTERED (key filtered out)
+__device__ __forceinline__ uint32_t dmap_get(const void *map, uint32_t vb, uint32_t idx) {
+  if (vb == 1) {
+    const uint32_t v = __ldg(reinterpret_cast<const uint8_t *>(map) + idx);
+    return v >= 0xFEu ? v + 0xFFFFFF00u : v;
+  }
+  if (vb == 2) {
+    const uint32_t v = __ldg(reinterpret_cast<const uint16_t *>(map) + idx);
+    return v >= 0xFFFEu ? v + 0xFFFF0000u : v;
+  }
+  return __ldg(reinterpret_cast<const uint32_t *>(map) + idx);
+}
+
 // lookup in dimension d of a plan: direct map or hash table
 __device__ __forceinline__ bool dim_lookup(const ChunkParams &p, int d, int32_t key, uint32_t &val) {
   if (p.dspan[d]) {
     const uint32_t idx = (uint32_t)(key - p.dmin[d]);
     if (idx >= p.dspan[d]) return false;
-    val = __ldg(reinterpret_cast<const uint32_t *>(p.ht[d]) + idx);
+    val = dmap_get(p.ht[d], p.dvb[d], idx);
     return val < HT_FILTERED;
   }
   return ht_lookup(p.ht[d], p.ht_log2[d], key, val);

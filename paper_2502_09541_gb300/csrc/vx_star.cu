@@ -123,14 +123,13 @@ __device__ __forceinline__ void star_rows(const ChunkParams &p, uint64_t base, u
 #pragma unroll
       for (int j = 0; j < kRows; ++j) key[j] = alive[j] ? load_role(p, p.dim_role[d], row[j]) : 0;
       if (p.dspan[d]) {  // direct map: one load per row, no probing
-        const uint32_t *__restrict__ map = reinterpret_cast<const uint32_t *>(slots);
         const int32_t kmin = p.dmin[d];
-        const uint32_t span = p.dspan[d];
+        const uint32_t span = p.dspan[d], vb = p.dvb[d];
         uint32_t v[kRows];
 #pragma unroll
         for (int j = 0; j < kRows; ++j) {
           const uint32_t idx = (uint32_t)(key[j] - kmin);
-          v[j] = (alive[j] && idx < span) ? __ldg(&map[idx]) : HT_EMPTY_VAL;
+          v[j] = (alive[j] && idx < span) ? dmap_get(slots, vb, idx) : HT_EMPTY_VAL;
         }
 #pragma unroll
         for (int j = 0; j < kRows; ++j) {
@@ -303,12 +302,12 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
 #pragma unroll
     for (int j = 0; j < kN; ++j) key[j] = vals(s, j);
     if (p.dspan[d]) {
-      const uint32_t *__restrict__ map = reinterpret_cast<const uint32_t *>(p.ht[d]);
+      const uint32_t vb = p.dvb[d];
       uint32_t v[kN];
 #pragma unroll
       for (int j = 0; j < kN; ++j) {
         const uint32_t idx = (uint32_t)(key[j] - p.dmin[d]);
-        v[j] = (alive[j] && idx < p.dspan[d]) ? __ldg(&map[idx]) : HT_EMPTY_VAL;
+        v[j] = (alive[j] && idx < p.dspan[d]) ? dmap_get(p.ht[d], vb, idx) : HT_EMPTY_VAL;
       }
 #pragma unroll
       for (int j = 0; j < kN; ++j) {
@@ -1001,6 +1000,18 @@ static int grid_for(vx_ctx *ctx, uint64_t work_items, int threads) {
   return want < 1 ? 1 : (int)want;
 }
 
+// a 4-byte direct map repacked to vb = 1 or 2 bytes per key (the markers
+// become the width's two largest values)
+__global__ void pack_dmap_kernel(const uint32_t *in, uint64_t n, void *out, uint32_t vb) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = in[i];
+    if (vb == 1)
+      reinterpret_cast<uint8_t *>(out)[i] = v == HT_EMPTY_VAL ? 0xFFu : v == HT_FILTERED ? 0xFEu : (uint8_t)v;
+    else
+      reinterpret_cast<uint16_t *>(out)[i] = v == HT_EMPTY_VAL ? 0xFFFFu : v == HT_FILTERED ? 0xFFFEu : (uint16_t)v;
+  }
+}
+
 __global__ void key_minmax_kernel(const int32_t *key, uint64_t n, int *out) {
   int lo = INT_MAX, hi = INT_MIN;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -1095,6 +1106,28 @@ vx_status build_dim_table(vx_ctx *ctx, const DimSpec &d, BuiltDim *out, uint32_t
   if (rows) {
     ht_build_kernel<<<grid_for(ctx, rows, 256), 256, 0, s>>>(bp);
     VX_CUDA_TRY(cudaGetLastError());
+  }
+  // a direct map whose largest group-code contribution fits a narrower value
+  // (below that width's two markers) is repacked to 1 or 2 bytes per key
+  if (out->span && rows) {
+    uint64_t vmax = 0;
+    for (int a = 0; a < d.n_attr; ++a)
+      if (d.stride[a] && d.card[a] > 0) vmax += (uint64_t)(d.card[a] - 1) * d.stride[a];
+    const uint32_t vb = vmax < 0xFEu ? 1 : vmax < 0xFFFEu ? 2 : 4;
+    if (vb < 4) {
+      DevBuf packed;
+      packed.arena = &ctx->arena;
+      packed.p = ctx->arena.alloc((uint64_t)vb * out->span);
+      if (packed.p) {  // else the 4-byte map stays
+        pack_dmap_kernel<<<grid_for(ctx, out->span, 256), 256, 0, s>>>(out->buf.as<uint32_t>(), out->span,
+                                                                         packed.p, vb);
+        VX_CUDA_TRY(cudaGetLastError());
+        // the 4-byte map goes back to the arena only once the packing has read it
+        VX_CUDA_TRY(cudaStreamSynchronize(s));
+        out->buf = std::move(packed);
+        out->vbytes = vb;
+      }
+    }
   }
   return VX_OK;
 }
@@ -1568,6 +1601,7 @@ vx_status run_star(vx_ctx *ctx, const vx_plan *plan, vx_result *out, bool use_re
       P.ht_log2[d] = tables[d]->dim.log2cap;
       P.dmin[d] = tables[d]->dim.kmin;
       P.dspan[d] = tables[d]->dim.span;
+      P.dvb[d] = (uint8_t)tables[d]->dim.vbytes;
     }
   }
   // ---- selectivity estimate: dimension pass fractions x sampled fact predicates

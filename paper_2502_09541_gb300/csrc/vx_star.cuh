@@ -40,13 +40,17 @@ struct DimSpec {
 
 // A dimension table on the device: an open-addressing hash table of 8-byte
 // slots, or — when the keys are dense (span <= 2 x rows) — a direct map of one
-// 4-byte value per key in [kmin, kmin + span).
+// value per key in [kmin, kmin + span), 1, 2 or 4 bytes wide: the narrowest
+// that holds the dimension's largest group-code contribution below its two
+// marker values (no such key, key filtered out), so the map of a 2M-row
+// dimension takes 2 MB instead of 8 and stays in L2 while chunks stream.
 struct BuiltDim {
   DevBuf buf;
   uint32_t log2cap = 0;
   uint64_t rows = 0, passed = 0;
   int32_t kmin = 0;
   uint32_t span = 0;  // > 0: direct map
+  uint32_t vbytes = 4;  // direct map: bytes per value (1, 2 or 4)
 };
 
 struct ResidentHT {
@@ -94,6 +98,7 @@ struct ChunkParams {
   uint32_t ht_log2[VX_MAX_DIMS];
   int32_t dmin[VX_MAX_DIMS];
   uint32_t dspan[VX_MAX_DIMS];
+  uint8_t dvb[VX_MAX_DIMS];         // direct map: bytes per value (1, 2 or 4; see dmap_get)
   int n_fgk;
   int8_t fgk_role[VX_MAX_GKEYS];
   int32_t fgk_card[VX_MAX_GKEYS];

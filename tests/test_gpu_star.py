@@ -255,3 +255,30 @@ def test_groupby_code_out_of_range_is_error(filt):
     with pytest.raises(vx.VxError) as e:
         vx.vx_groupby(ctx, [(fid["quantity"], 10)], vx.VX_AGG_COUNT, -1, -1, [])
     assert e.value.status == vx.VX_E_RANGE
+
+
+@pytest.mark.parametrize("late", [vx.VX_LATE_FORCE_EARLY, vx.VX_LATE_FORCE_LATE])
+def test_star_direct_maps_of_every_value_width(late):
+    """Grouping by part brand (250) x supplier city (250) x year (7) gives the
+    part map contributions up to 249 * 1750 (4-byte values), the supplier map up
+    to 249 * 7 (2 bytes) and the date map up to 6 (1 byte); 437,500 groups
+    accumulate in global memory.  Every group against the oracle."""
+    n = 3_000_007
+    fact, dims = G.star_fact(n, seed=23), G.star_dims(0)
+    T = {"dims": [{"dim": "part", "fk": "fk_part", "preds": [("mfgr", 0, 3)]},
+                  {"dim": "supp", "fk": "fk_supp", "preds": []},
+                  {"dim": "date", "fk": "date_fk", "preds": [("year", 1, 6)]}],
+         "fact_preds": [("discount", 1, 9)],
+         "group": [("part", "brand"), ("supp", "city"), ("date", "year")],
+         "agg": ("sub", "price", "cost")}
+    ctx = _open(256 << 20, 8 << 20)
+    try:
+        fid = {c: vx.vx_register_host_column(ctx, c, fact[c]) for c in fact}
+        did = {d: {a: vx.vx_register_host_column(ctx, f"{d}.{a}", arr) for a, arr in dims[d].items()} for d in dims}
+        st, gid, s, c, stats = vx.vx_run_plan(ctx, vx.make_plan(T, fid, did, G.STAR_ATTR_CARD, late), 1 << 19)
+    finally:
+        vx.vx_close(ctx)
+    es, ec = O.star(T, fact, dims, nthreads=8)
+    nz = np.nonzero(ec)[0]
+    assert st == vx.VX_OK and len(nz) > 65536
+    assert np.array_equal(gid, nz) and np.array_equal(s, es[nz]) and np.array_equal(c, ec[nz])
