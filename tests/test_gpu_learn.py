@@ -75,20 +75,30 @@ def test_training_reduces_loss_and_beats_equal_width(ctx):
     assert np.all(np.diff(ys) >= -1e-9)
 
 
-def test_trained_partitioner_gain_over_equal_width():
-    """Keys = Zipf ranks (small keys hot): equal-width cuts over [min, max]
-    put almost every key in the first partition; the trained network's cuts
-    balance them."""
+@pytest.mark.parametrize("sample", [4_000, 200_000])
+def test_trained_partitioner_against_sample_splitters(sample):
+    """What the trained network gives against the method without it: the
+    sample splitters (quantiles of the same key sample) at equal P, and
+    equal-width cuts.  Keys = Zipf ranks (small keys hot).  The network's cuts
+    balance the partitions as well as the sample quantiles do (within 10 %)
+    and far better than equal-width cuts;
+    the sample-size sweep shows it holds with a sample 50x smaller."""
     n, P = 1_000_000, 16
     k = G.u64_zipf(n, 1 << 20, 0.8, 0, 77, hashed=False)
     c = vx.vx_open(256 << 20)
     try:
         cid = vx.vx_register_host_column(c, "k", k)
-        spl = vx.vx_sort_splitters(c, cid, vx.VX_PART_LEARNED_MLP, P, 200_000, 1)
+        mlp = vx.vx_sort_splitters(c, cid, vx.VX_PART_LEARNED_MLP, P, sample, 1)
+        smp = vx.vx_sort_splitters(c, cid, vx.VX_PART_SAMPLE, P, sample, 1)
     finally:
         vx.vx_close(c)
     lo, hi = int(k.min()), int(k.max())
     eq = np.array([lo + (hi - lo) * p // P for p in range(1, P)], np.uint64)
-    imb = lambda s: np.bincount(np.searchsorted(s, k, side="right"), minlength=P).max() / (n / P)
-    learned, equal = imb(spl), imb(eq)
-    assert learned < 2.0 and equal > 4 * learned, (learned, equal)
+
+    def imb(s):
+        counts = np.bincount(np.searchsorted(s, k, side="right"), minlength=len(s) + 1)
+        return counts.max() / (n / (len(s) + 1))
+
+    learned, sampled, equal = imb(mlp), imb(smp), imb(eq)
+    assert learned <= 1.1 * sampled + 0.05, (learned, sampled)
+    assert equal > 4 * learned, (learned, equal)
