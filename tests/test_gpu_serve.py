@@ -149,9 +149,10 @@ def test_sort_and_join_queries_in_the_mix(tables):
         for kind, rb, re, merge in ops:
             if kind == "sort":
                 c2 = vx.vx_open(256 << 20)
+                kcopy, rcopy = sk[rb:re].copy(), sr[rb:re].copy()  # registered: kept alive until closed
                 try:
-                    k2 = vx.vx_register_host_column(c2, "k", sk[rb:re].copy())
-                    r2 = vx.vx_register_host_column(c2, "r", sr[rb:re].copy())
+                    k2 = vx.vx_register_host_column(c2, "k", kcopy)
+                    r2 = vx.vx_register_host_column(c2, "r", rcopy)
                     ok, orr = np.empty(re - rb, np.uint64), np.empty(re - rb, np.uint32)
                     o = vx.vx_sort_opts()
                     o.plan = vx.VX_SORT_MERGE if merge else vx.VX_SORT_PARTITION
@@ -200,9 +201,10 @@ def test_sort_and_join_queries_in_the_mix(tables):
                 exp = O.join(bk, bp, pk[rb:re], probe_row0=rb, nthreads=8)
                 assert (j["count"], j["payload_sum"], j["pair_fp"]) == exp
                 cj = vx.vx_open(256 << 20)
+                pcopy = pk[rb:re].copy()  # registered: kept alive until closed
                 try:
                     d = vx.vx_join(cj, vx.vx_register_host_column(cj, "a", bk), vx.vx_register_host_column(cj, "b", bp),
-                                   vx.vx_register_host_column(cj, "p", pk[rb:re].copy()), vx.vx_join_opts())
+                                   vx.vx_register_host_column(cj, "p", pcopy), vx.vx_join_opts())
                 finally:
                     vx.vx_close(cj)
                 assert (d["count"], d["payload_sum"]) == (j["count"], j["payload_sum"])
