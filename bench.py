@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--sort-pairs", type=int, default=1_000_000_000)
     ap.add_argument("--join-build", type=int, default=250_000_000)
     ap.add_argument("--join-probe", type=int, default=2_000_000_000)
-    ap.add_argument("--workload", default="star", choices=["star", "sort", "join", "serve"],
+    ap.add_argument("--workload", default="star", choices=["star", "sort", "join", "serve", "ops"],
                     help="star: the full benchmark line; sort / join / serve: that part alone")
     ap.add_argument("--serve-plain-queries", type=int, default=100)
     ap.add_argument("--sweep-queries", type=int, default=60, help="mixed serving queries per arrival rate (0: no sweep)")
@@ -437,6 +437,41 @@ def run_clustered(vx, G, ctx, did, args):
                   "link_bytes": int(x["bytes_h2d"] + x["bytes_zero_copy"]), "late_chunks": int(x["late_chunks"]),
                   "chunks": int(x["chunks"]), "late_mask": int(x["late_mask"])}
     out["equal"] = all(np.array_equal(a, b) for a, b in zip(res["plain"], res["learned"]))
+    return out
+
+
+def run_ops_extra(vx, G, args, ctx=None, fid=None, did=None):
+    """Operator-at-a-time execution with host intermediates against the fused
+    plan on the same context: a sparse template (T2_1, about 1 % of rows
+    survive the filter and probes) and a dense one (T3_10); each timed as its
+    second call, results compared equal."""
+    own = ctx is None
+    if own:
+        fact, dims = make_data(args.rows, pinned=True)
+        ctx = vx.vx_open(int(args.budget_gb * (1 << 30)))
+        fid = {c: vx.vx_register_host_column(ctx, c, fact[c]) for c in fact}
+        did = {d: {a: vx.vx_register_host_column(ctx, f"{d}.{a}", arr) for a, arr in dims[d].items()} for d in dims}
+    import datagen as G_
+    import numpy as np
+    tmpls = G_.star_templates()
+    out = {"rows": args.rows}
+    try:
+        for name in ("T2_1", "T3_10"):
+            plan = vx.make_plan(tmpls[name], fid, did, G_.STAR_ATTR_CARD)
+            res = {}
+            for form, fn in (("fused", vx.vx_run_plan), ("operators", vx.vx_run_plan_operators)):
+                fn(ctx, plan)
+                st, gid, sm, cnt, stats = fn(ctx, plan)
+                assert st == vx.VX_OK
+                res[form] = (gid, sm, cnt, stats)
+            f, o = res["fused"][3], res["operators"][3]
+            out[name] = {"fused_ms": round(f["ms_total"], 2), "operators_ms": round(o["ms_total"], 2),
+                         "operators_h2d_bytes": int(o["bytes_h2d"]), "operators_d2h_bytes": int(o["bytes_d2h"]),
+                         "operators_zero_copy_bytes": int(o["bytes_zero_copy"]), "fused_h2d_bytes": int(f["bytes_h2d"]),
+                         "equal": all(np.array_equal(a, b) for a, b in zip(res["fused"][:3], res["operators"][:3]))}
+    finally:
+        if own:
+            vx.vx_close(ctx)
     return out
 
 
@@ -842,6 +877,7 @@ def run_ours(args):
                                                                          "algorithmic_bytes_per_launch",
                                                                          "launch_ceiling")}
 
+    operators = run_ops_extra(vx, G, args, ctx, fid, did) if not args.no_extras else None
     serving = run_serving(vx, G, ctx, fid, did, args) if not args.no_extras and args.serve_queries > 0 else None
     if serving is not None and args.sweep_queries > 0:
         serving["mixed"] = run_serving_sweep(vx, G, ctx, fid, did, args)
@@ -872,6 +908,8 @@ def run_ours(args):
         "clocks": clocks,
         "setup_s": {"generate": round(t_gen, 1)},
     }
+    if operators:
+        line["operators"] = operators
     if serving:
         line["serving"] = serving
     if clustered:
@@ -948,6 +986,10 @@ def summarize(line):
         pr = so.get("presorted_runs")
         if pr:
             out["sort_runs_ms"] = {k: v["ms"] for k, v in pr.items() if isinstance(v, dict)}
+    op = line.get("operators")
+    if op:
+        out["operators_ms"] = {k: {"fused": v["fused_ms"], "operators": v["operators_ms"]} for k, v in op.items()
+                               if isinstance(v, dict)}
     jo = line.get("join")
     if jo:
         out["join_ms"] = {k: jo[k]["ms"] for k in jo if isinstance(jo[k], dict) and "ms" in jo[k]}
@@ -984,6 +1026,11 @@ def main():
         run_ours(args)
     elif args.workload == "serve":
         run_serve_only(args)
+    elif args.workload == "ops":
+        import datagen as G
+        import paper_2502_09541_gb300 as vx
+        vx.load()
+        print(json.dumps({"workload": "ops", "operators": run_ops_extra(vx, G, args)}), flush=True)
     else:  # one out-of-core operator alone (profiling, or a user's own sizes)
         import datagen as G
         import paper_2502_09541_gb300 as vx

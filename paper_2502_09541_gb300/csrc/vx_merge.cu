@@ -150,28 +150,54 @@ __device__ __forceinline__ I merge_path(const uint64_t *a, I na, const uint64_t 
   return lo;
 }
 
-__global__ void __launch_bounds__(kMergeThreads) merge_round_kernel(const MergeRound p) {
+// pair of segments holding output position t, and its bounds
+struct PairAt {
+  uint64_t base, amid, pend;
+};
+__device__ __forceinline__ PairAt pair_at(const MergeRound &p, uint64_t t) {
+  const uint32_t npairs = (p.nseg + 1) / 2;
+  uint32_t qlo = 0, qhi = npairs - 1;
+  while (qlo < qhi) {
+    const uint32_t mid = (qlo + qhi + 1) / 2;
+    if (p.seg[2 * mid] <= t) qlo = mid; else qhi = mid - 1;
+  }
+  return PairAt{p.seg[2 * qlo], p.seg[2 * qlo + 1], p.seg[2 * qlo + 2 < p.nseg ? 2 * qlo + 2 : p.nseg]};
+}
+
+// Merge-path cuts of a round, one thread per tile boundary: cut[b] = the
+// elements of the first segment of its pair among the pair's outputs before
+// output b * kMergeTile (searched in parallel for every tile, so a merge block
+// starts at once instead of waiting on a serial search of global memory).
+// A boundary that starts a pair has cut 0.
+__global__ void merge_cuts_kernel(const MergeRound p, uint64_t *cut, uint64_t n_bounds) {
+  for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < n_bounds; b += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = b * kMergeTile < p.n ? b * kMergeTile : p.n;
+    if (t >= p.n) {
+      cut[b] = 0;
+      continue;
+    }
+    const PairAt q = pair_at(p, t);
+    cut[b] = merge_path<uint64_t>(p.kin + q.base, q.amid - q.base, p.kin + q.amid, q.pend - q.amid, t - q.base);
+  }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) merge_round_kernel(const MergeRound p, const uint64_t *cut) {
   __shared__ uint64_t sk[kMergeTile];
   __shared__ uint32_t sv[kMergeTile];
-  __shared__ uint64_t s_cut[2];
   uint64_t t0 = (uint64_t)blockIdx.x * kMergeTile;
   const uint64_t t_end = t0 + kMergeTile < p.n ? t0 + kMergeTile : p.n;
-  const uint32_t npairs = (p.nseg + 1) / 2;
   while (t0 < t_end) {  // the outputs of one pair at a time (a tile may span pairs)
-    uint32_t qlo = 0, qhi = npairs - 1;
-    while (qlo < qhi) {
-      const uint32_t mid = (qlo + qhi + 1) / 2;
-      if (p.seg[2 * mid] <= t0) qlo = mid; else qhi = mid - 1;
-    }
-    const uint64_t base = p.seg[2 * qlo], amid = p.seg[2 * qlo + 1];
-    const uint64_t pend = p.seg[2 * qlo + 2 < p.nseg ? 2 * qlo + 2 : p.nseg];
+    const PairAt q = pair_at(p, t0);
+    const uint64_t base = q.base, amid = q.amid, pend = q.pend;
     const uint64_t t1 = t_end < pend ? t_end : pend;
     const uint64_t *A = p.kin + base, *B = p.kin + amid;
     const uint64_t na = amid - base, nb = pend - amid;
     const uint64_t d0 = t0 - base, d1 = t1 - base;
-    if (threadIdx.x < 2) s_cut[threadIdx.x] = merge_path<uint64_t>(A, na, B, nb, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const uint64_t i0 = s_cut[0], i1 = s_cut[1], j0 = d0 - i0;
+    // cuts at the tile's own boundaries come precomputed; a pair boundary
+    // inside the tile is where a pair starts (cut 0) or ends (cut na)
+    const uint64_t i0 = t0 == (uint64_t)blockIdx.x * kMergeTile ? cut[blockIdx.x] : 0;
+    const uint64_t i1 = t1 == pend ? na : cut[blockIdx.x + 1];
+    const uint64_t j0 = d0 - i0;
     const uint32_t la = (uint32_t)(i1 - i0), L = (uint32_t)(d1 - d0), lb = L - la;
     for (uint32_t x = threadIdx.x; x < L; x += kMergeThreads) {
       if (x < la) {
@@ -218,7 +244,9 @@ __global__ void __launch_bounds__(kMergeThreads) merge_round_kernel(const MergeR
 // Enqueues the merge of the nseg segments seg[0..nseg] of b.keys[0]/b.vals[0]
 // (n pairs) on s; returns the buffer that holds the result and adds the
 // executed rounds to *rounds.
-int merge_enqueue(RadixBufs b, uint64_t n, const std::vector<uint64_t> &seg, cudaStream_t s, uint64_t *rounds) {
+// cuts: device scratch of n / kMergeTile + 2 words
+int merge_enqueue(RadixBufs b, uint64_t n, const std::vector<uint64_t> &seg, uint64_t *cuts, cudaStream_t s,
+                  uint64_t *rounds) {
   int c = 0;
   std::vector<uint64_t> cur = seg;
   while (cur.size() > 2) {  // more than one segment
@@ -231,7 +259,8 @@ int merge_enqueue(RadixBufs b, uint64_t n, const std::vector<uint64_t> &seg, cud
     r.nseg = (uint32_t)(cur.size() - 1);
     for (size_t i = 0; i < cur.size(); ++i) r.seg[i] = cur[i];
     const unsigned grid = (unsigned)((n + kMergeTile - 1) / kMergeTile);
-    merge_round_kernel<<<grid, kMergeThreads, 0, s>>>(r);
+    merge_cuts_kernel<<<(grid + 1 + 255) / 256, 256, 0, s>>>(r, cuts, (uint64_t)grid + 1);
+    merge_round_kernel<<<grid, kMergeThreads, 0, s>>>(r, cuts);
     std::vector<uint64_t> nx;
     for (uint32_t q = 0; 2 * q < r.nseg; ++q) nx.push_back(cur[2 * q]);
     nx.push_back(n);
@@ -336,7 +365,8 @@ struct MergePass : ExKernel {
   int max_in_flight() override { return S; }
   uint64_t kb() const { return (8 * cap + 255) & ~255ull; }
   uint64_t vb() const { return (4 * cap + 255) & ~255ull; }
-  uint64_t slot_bytes() override { return 2 * kb() + 2 * vb(); }
+  uint64_t cb() const { return (8 * (cap / kMergeTile + 2) + 255) & ~255ull; }
+  uint64_t slot_bytes() override { return 2 * kb() + 2 * vb() + cb(); }
   RadixBufs bufs(char *slot) const {
     RadixBufs b;
     b.keys[0] = (uint64_t *)slot;
@@ -345,6 +375,7 @@ struct MergePass : ExKernel {
     b.vals[1] = (uint32_t *)(slot + 2 * kb() + vb());
     return b;
   }
+  uint64_t *cuts(char *slot) const { return (uint64_t *)(slot + 2 * kb() + 2 * vb()); }
   uint64_t seg_len(uint64_t p, uint32_t r) const { return cut[(p + 1) * N + r] - cut[p * N + r]; }
   uint64_t part_off(uint64_t p) const {
     uint64_t o = 0;
@@ -374,7 +405,7 @@ struct MergePass : ExKernel {
     const size_t e = p % S;
     if (!ev0.empty()) VX_CUDA_TRY(cudaEventRecord(ev0[e], s));
     uint64_t rounds = 0;
-    result_buf[e] = merge_enqueue(bufs(slot), n, segments_of(lens), s, &rounds);
+    result_buf[e] = merge_enqueue(bufs(slot), n, segments_of(lens), cuts(slot), s, &rounds);
     VX_CUDA_TRY(cudaGetLastError());
     if (!ev1.empty()) VX_CUDA_TRY(cudaEventRecord(ev1[e], s));
     rounds_pairs += rounds * n;
@@ -670,9 +701,10 @@ VX_API vx_status vx_merge_runs(vx_ctx *ctx, const uint64_t *keys, const uint32_t
   }
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
   const uint64_t kb = (8 * n + 255) & ~255ull, vb = (4 * n + 255) & ~255ull;
+  const uint64_t cb = (8 * (n / kMergeTile + 2) + 255) & ~255ull;
   DevBuf buf;
   buf.arena = &ctx->arena;
-  buf.p = ctx->arena.alloc(2 * kb + 2 * vb);
+  buf.p = ctx->arena.alloc(2 * kb + 2 * vb + cb);
   if (!buf.p) {
     set_error("vx_merge_runs: %llu pairs do not fit the arena twice", (unsigned long long)n);
     return VX_E_NOMEM;
@@ -686,7 +718,7 @@ VX_API vx_status vx_merge_runs(vx_ctx *ctx, const uint64_t *keys, const uint32_t
   VX_CUDA_TRY(cudaMemcpyAsync(b.keys[0], keys, 8 * n, cudaMemcpyHostToDevice, s));
   VX_CUDA_TRY(cudaMemcpyAsync(b.vals[0], vals, 4 * n, cudaMemcpyHostToDevice, s));
   uint64_t rounds = 0;
-  const int c = merge_enqueue(b, n, segments_of(lens), s, &rounds);
+  const int c = merge_enqueue(b, n, segments_of(lens), (uint64_t *)(buf.as<char>() + 2 * kb + 2 * vb), s, &rounds);
   VX_CUDA_TRY(cudaGetLastError());
   VX_CUDA_TRY(cudaMemcpyAsync(out_keys, b.keys[c], 8 * n, cudaMemcpyDeviceToHost, s));
   VX_CUDA_TRY(cudaMemcpyAsync(out_vals, b.vals[c], 4 * n, cudaMemcpyDeviceToHost, s));
