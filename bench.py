@@ -781,6 +781,8 @@ def run_ours(args):
                   "frac": round(zc_bytes / (g_ms * 1e6) / h2d_peak, 4), "peak_kind": "H2D copy, measured in this run",
                   "granule_bytes": 64, "values_read": int(zc_vals),
                   "algorithmic_gbs": round(4 * zc_vals / (g_ms * 1e6), 2),
+                  "survivors_per_launch": round(sum(s["survivors"] for s in stats_all if s["late_mask"]) /
+                                                max(1, sum(s["chunks"] for s in stats_all if s["late_mask"]))),
                   "avg_launch_us": round(1000 * g_ms / max(1, sum(s["chunks"] for s in stats_all if s["late_mask"])), 2)}
 
     # ---- learned / batched form: regressor trained on the plain form's log,
@@ -973,7 +975,12 @@ def summarize(line):
            "star_link_frac": {k: f[k]["step_roofline"]["link_frac"] for k in ("plain", "learned")},
            "star_step_roofline_frac": {k: f[k]["step_roofline"]["frac"] for k in ("plain", "learned")},
            "fused_kernel_hbm_frac": line["roofline"].get("frac"),
+           "fused_kernel_of_launch_ceiling": (line["roofline"].get("launch_ceiling") or {}).get("fused_of_ceiling"),
            "copy_engine_busy": line.get("copy_engine_busy")}
+    g = line.get("roofline_zero_copy_gather")
+    if g:
+        out["gather_link_frac"] = g.get("frac")
+        out["gather_survivors_per_launch"] = g.get("survivors_per_launch")
     sv = line.get("serving")
     if sv:
         out["serving_ms"] = {"p50": sv.get("p50_ms"), "p99": sv.get("p99_ms")}
