@@ -4,15 +4,8 @@
 // copy engine loads chunk n into a free slot and saves the output of chunk n-2
 // on the device-to-host stream.  Two schedules:
 //   VX_SCHED_IMMEDIATE — a host loop issues a copy only when it can start at
-//     once (its slot is free and the previous user of the slot has finished),
-//     following the first design principle of Section 4.3.  A chunk's store is
-//     issued only once its kernel has completed, which in turn waited for its
-//     load, so the device-to-host queue can never drain ahead of the
-//     host-to-device queue (the flow-control policy of Section 4.3) and at
-//     most max_in_flight() chunks occupy the link at once.  The loop polls
-//     with a 10 us back-off (Section 4.3's retry period); the wall-clock limit
-//     wait_timeout_ms applies to the time since the last completed step, so a
-//     long operator that keeps making progress never times out.
+//     once (vx_sched.h holds the decisions; this file gives them the
+//     context's streams and events).
 //   VX_SCHED_DAG — every copy and kernel is enqueued up front with stream and
 //     event dependencies (the baseline of Section 4.2).  Only operators whose
 //     outputs stay on the device use it.
@@ -20,6 +13,7 @@
 #include <thread>
 
 #include "vx_internal.h"
+#include "vx_sched.h"
 
 namespace vx {
 
@@ -74,6 +68,93 @@ vx_status issue_copies(const std::vector<CopyOp> &ops, cudaMemcpyKind kind, cuda
   }
   return VX_OK;
 }
+
+// The immediate schedule's device: the context's copy and compute streams,
+// one event set per staging slot (vx_sched.h makes the decisions)
+struct CudaDev {
+  vx_ctx *ctx;
+  ExKernel &k;
+  ExecStats *st;
+  EventSet &es;
+  char *base;
+  uint64_t slot_bytes;
+  bool tl;
+  double t_origin;
+  DevBuf *ring;
+  std::vector<CopyOp> ops;
+
+  char *slot(int s) const { return base + (uint64_t)s * slot_bytes; }
+  static int state(cudaEvent_t e) {
+    const cudaError_t q = cudaEventQuery(e);
+    if (q == cudaErrorNotReady) return 0;
+    if (q == cudaSuccess) return 1;
+    set_error("executor: %s", cudaGetErrorString(q));
+    return VX_E_CUDA;
+  }
+  bool has_outputs() { return k.has_outputs(); }
+  vx_status load(uint64_t it, int s) {
+    SlotState &sl = es.s[s];
+    ops.clear();
+    k.inputs(it, slot(s), ops);
+    if (tl) {
+      sl.issue_ms = (float)(now_ms() - t_origin);
+      VX_CUDA_TRY(cudaEventRecord(sl.ev_h0, ctx->s_h2d));
+    }
+    VX_TRY(issue_copies(ops, cudaMemcpyHostToDevice, ctx->s_h2d, &st->bytes_h2d));
+    if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_h1, ctx->s_h2d));
+    VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
+    VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
+    VX_CUDA_TRY(cudaEventRecord(sl.ev_k0, ctx->s_compute));
+    VX_TRY(k.kernel(slot(s), it, ctx->s_compute));
+    st->kernel_launches += 1;
+    VX_CUDA_TRY(cudaEventRecord(sl.ev_k, ctx->s_compute));
+    sl.chunk = (int64_t)it;
+    return VX_OK;
+  }
+  int kernel_state(int s) { return state(es.s[s].ev_k); }
+  vx_status retire(uint64_t it, int s) {
+    SlotState &sl = es.s[s];
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k) == cudaSuccess) st->ms_kernel += ms;
+    cudaGetLastError();
+    k.on_retire(it);
+    if (tl) {
+      const float row[VX_TIMELINE_COLS] = {(float)it, sl.issue_ms, since(es.ref, sl.ev_h0), since(es.ref, sl.ev_h1),
+                                           since(es.ref, sl.ev_k0), since(es.ref, sl.ev_k), -1.f, -1.f};
+      ctx->timeline.insert(ctx->timeline.end(), row, row + VX_TIMELINE_COLS);
+    }
+    return VX_OK;
+  }
+  vx_status store(uint64_t it, int s) {
+    SlotState &sl = es.s[s];
+    ops.clear();
+    VX_TRY(k.outputs(it, slot(s), ops));
+    if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_d0, ctx->s_d2h));
+    VX_TRY(issue_copies(ops, cudaMemcpyDeviceToHost, ctx->s_d2h, &st->bytes_d2h));
+    if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_d1, ctx->s_d2h));
+    VX_CUDA_TRY(cudaEventRecord(sl.ev_out, ctx->s_d2h));
+    return VX_OK;
+  }
+  int store_state(int s) { return state(es.s[s].ev_out); }
+  vx_status stored(uint64_t, int s) {
+    if (tl) {  // this chunk's row is the last one recorded so far (chunks retire in order)
+      float *row = &ctx->timeline[ctx->timeline.size() - VX_TIMELINE_COLS];
+      row[6] = since(es.ref, es.s[s].ev_d0);
+      row[7] = since(es.ref, es.s[s].ev_d1);
+    }
+    return VX_OK;
+  }
+  vx_status timed_out(uint64_t it) {
+    set_error("executor: no chunk completed a step within the wait limit of %u ms (at chunk %llu of %llu)",
+              ctx->cfg.wait_timeout_ms, (unsigned long long)it, (unsigned long long)k.size());
+    // the ring goes back to the arena only once the work already issued into
+    // it has finished; that drain is bounded too
+    if (!drain_streams(ctx)) ring->arena = nullptr;
+    return VX_E_TIMEOUT;
+  }
+  double now_ms() { return vx::now_ms(); }
+  void pause() { std::this_thread::sleep_for(std::chrono::microseconds(10)); }
+};
 
 }  // namespace
 
@@ -164,97 +245,8 @@ vx_status run_pipeline(vx_ctx *ctx, ExKernel &k, ExecStats *st) {
     return VX_OK;
   }
 
-  double last_progress = now_ms();
-  uint64_t next_load = 0, next_retire = 0;
-  const uint64_t max_in_flight = (uint64_t)std::max(1, k.max_in_flight());
-  while (next_retire < N) {
-    bool progress = false;
-    // retire in chunk order
-    while (next_retire < next_load) {
-      SlotState &sl = es.s[next_retire % S];
-      if (sl.phase == 1) {
-        cudaError_t q = cudaEventQuery(sl.ev_k);
-        if (q == cudaErrorNotReady) break;
-        VX_CUDA_TRY(q);
-        float ms = 0;
-        if (cudaEventElapsedTime(&ms, sl.ev_k0, sl.ev_k) == cudaSuccess) st->ms_kernel += ms;
-        cudaGetLastError();
-        k.on_retire(next_retire);
-        if (tl) {
-          const float row[VX_TIMELINE_COLS] = {(float)next_retire, sl.issue_ms, since(es.ref, sl.ev_h0),
-                                               since(es.ref, sl.ev_h1), since(es.ref, sl.ev_k0),
-                                               since(es.ref, sl.ev_k), -1.f, -1.f};
-          ctx->timeline.insert(ctx->timeline.end(), row, row + VX_TIMELINE_COLS);
-        }
-        if (k.has_outputs()) {
-          ops.clear();
-          VX_TRY(k.outputs(next_retire, base + (next_retire % S) * slot_bytes, ops));
-          if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_d0, ctx->s_d2h));
-          VX_TRY(issue_copies(ops, cudaMemcpyDeviceToHost, ctx->s_d2h, &st->bytes_d2h));
-          if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_d1, ctx->s_d2h));
-          VX_CUDA_TRY(cudaEventRecord(sl.ev_out, ctx->s_d2h));
-          sl.phase = 2;
-        } else {
-          sl.phase = 0;
-          ++next_retire;
-        }
-        progress = true;
-      } else if (sl.phase == 2) {
-        cudaError_t q = cudaEventQuery(sl.ev_out);
-        if (q == cudaErrorNotReady) break;
-        VX_CUDA_TRY(q);
-        if (tl) {  // this chunk's row is the last one recorded so far
-          float *row = &ctx->timeline[ctx->timeline.size() - VX_TIMELINE_COLS];
-          row[6] = since(es.ref, sl.ev_d0);
-          row[7] = since(es.ref, sl.ev_d1);
-        }
-        sl.phase = 0;
-        ++next_retire;
-        progress = true;
-      } else {
-        break;
-      }
-    }
-    // load the next chunk when its slot is free and fewer than max_in_flight
-    // chunks are loaded, computing or storing
-    if (next_load < N && next_load - next_retire < (uint64_t)S) {
-      SlotState &sl = es.s[next_load % S];
-      if (sl.phase == 0 && next_load - next_retire < max_in_flight) {
-        char *slot = base + (next_load % S) * slot_bytes;
-        ops.clear();
-        k.inputs(next_load, slot, ops);
-        if (tl) {
-          sl.issue_ms = (float)(now_ms() - t_origin);
-          VX_CUDA_TRY(cudaEventRecord(sl.ev_h0, ctx->s_h2d));
-        }
-        VX_TRY(issue_copies(ops, cudaMemcpyHostToDevice, ctx->s_h2d, &st->bytes_h2d));
-        if (tl) VX_CUDA_TRY(cudaEventRecord(sl.ev_h1, ctx->s_h2d));
-        VX_CUDA_TRY(cudaEventRecord(sl.ev_in, ctx->s_h2d));
-        VX_CUDA_TRY(cudaStreamWaitEvent(ctx->s_compute, sl.ev_in, 0));
-        VX_CUDA_TRY(cudaEventRecord(sl.ev_k0, ctx->s_compute));
-        VX_TRY(k.kernel(slot, next_load, ctx->s_compute));
-        st->kernel_launches += 1;
-        VX_CUDA_TRY(cudaEventRecord(sl.ev_k, ctx->s_compute));
-        sl.chunk = (int64_t)next_load;
-        sl.phase = 1;
-        ++next_load;
-        progress = true;
-      }
-    }
-    if (progress) {
-      last_progress = now_ms();
-    } else {
-      if (now_ms() - last_progress > ctx->cfg.wait_timeout_ms) {
-        set_error("executor: no chunk completed a step within the wait limit of %u ms (at chunk %llu of %llu)",
-                  ctx->cfg.wait_timeout_ms, (unsigned long long)next_retire, (unsigned long long)N);
-        // the ring goes back to the arena only once the work already issued
-        // into it has finished; that drain is bounded too
-        if (!drain_streams(ctx)) ring.arena = nullptr;
-        return VX_E_TIMEOUT;
-      }
-      std::this_thread::sleep_for(std::chrono::microseconds(10));
-    }
-  }
+  CudaDev dev{ctx, k, st, es, base, slot_bytes, tl, t_origin, &ring, {}};
+  VX_TRY(immediate_schedule(dev, N, S, (uint64_t)std::max(1, k.max_in_flight()), (double)ctx->cfg.wait_timeout_ms));
   st->chunks += N;
   VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_d2h));
   return VX_OK;
