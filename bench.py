@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--serve-chunk-rows", type=int, default=1 << 21, help="rows per shared-scan chunk")
     ap.add_argument("--serve-max-active", type=int, default=32, help="queries attached to the scan at once")
     ap.add_argument("--serve-slots", type=int, default=0, help="staging slots of the shared scan (0: library default)")
+    ap.add_argument("--kernel-rows", type=int, default=0, choices=[0, 2, 8, 16],
+                    help="plain form's fused-kernel shape (vx_config.kernel_rows; 2 = bulk-copy pipeline)")
+    ap.add_argument("--blocks-per-sm", type=int, default=4, help="plain form's vx_config.blocks_per_sm")
     ap.add_argument("--clustered-rows", type=int, default=300_000_000,
                     help="date-clustered fact table of the per-chunk materialization comparison (0: skip)")
     return ap.parse_args()
@@ -137,6 +140,9 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# fused chunk kernel shapes by vx_config.kernel_rows
+KERNEL_SHAPES = {0: "one tile per block (4 rows per thread)", 2: "bulk-copy pipeline (4 rows per thread)",
+                 8: "scalar, 8 rows per thread", 16: "scalar, 16 rows per thread"}
 STAR_KERNEL_END = {"vx_star.cu": b"// ---- end of the fused chunk kernel's device code",
                    "vx_star.cuh": b"// ---- end of what the fused chunk kernel's device code reads",
                    "vx_probe.cuh": None}  # the row-logic helpers: the whole file
@@ -719,6 +725,8 @@ def run_ours(args):
     # late/early decision per plan; its warm-up steps log per-chunk statistics
     cfg = vx.vx_get_config(ctx)
     cfg.log_chunk_stats = 1
+    cfg.kernel_rows = args.kernel_rows
+    cfg.blocks_per_sm = args.blocks_per_sm
     vx.vx_set_config(ctx, cfg)
     for _ in range(max(args.warmup, 3)):
         step([])
@@ -801,11 +809,12 @@ def run_ours(args):
     link_l = sum(s["bytes_h2d"] + s["bytes_zero_copy"] for s in stats_l) / args.steps / (ms_learned * 1e6)
     forms = {
         "plain": {"value": round(plain_gbs, 3), "ms_per_step": round(ms_step, 3), "link_gbs": round(link_gbs, 1),
-                  "chunk_bytes": 64 << 20, "sched": "immediate", "late": "per plan"},
+                  "chunk_bytes": 64 << 20, "sched": "immediate", "late": "per plan",
+                  "kernel_shape": {"kernel": KERNEL_SHAPES[args.kernel_rows], "blocks_per_sm": args.blocks_per_sm}},
         "learned": {"value": round(learned_gbs, 3), "ms_per_step": round(ms_learned, 3),
                     "link_gbs": round(link_l, 1), "chunk_bytes": int(tuned.chunk_bytes),
                     "n_slots": int(tuned.n_slots),
-                    "kernel_shape": {"rows_per_thread": int(tuned.kernel_rows) or "vector (4)",
+                    "kernel_shape": {"kernel": KERNEL_SHAPES.get(int(tuned.kernel_rows), "?"),
                                      "blocks_per_sm": int(tuned.blocks_per_sm)},
                     "graphs": True, "late": "per chunk (regressor)",
                     "regressor_chunks_logged": int(n_log), "clocks": clk2.summary()},
@@ -837,8 +846,8 @@ def run_ours(args):
     cfg.use_graphs = 0
     cfg.chunk_bytes = 64 << 20
     cfg.n_slots = 3
-    cfg.kernel_rows = 0
-    cfg.blocks_per_sm = 4
+    cfg.kernel_rows = args.kernel_rows
+    cfg.blocks_per_sm = args.blocks_per_sm
     vx.vx_set_config(ctx, cfg)
 
     # end to end through the public call: dimension tables rebuilt from host

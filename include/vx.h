@@ -83,10 +83,14 @@ typedef struct {
                                cardinality regressor's training data); not with use_graphs */
   int32_t log_timeline;     /* the immediate schedule records when every chunk's copies and kernel
                                ran (vx_last_timeline); not with use_graphs */
-  int32_t kernel_rows;      /* rows per thread of the fused chunk kernel: 0 = automatic (the vector
-                               path, 4 rows per thread read as 16-byte column vectors, where the
-                               columns allow; else 8 rows), 8 or 16 = the scalar kernel with that
-                               many rows per thread and at most blocks_per_sm blocks per SM */
+  int32_t kernel_rows;      /* shape of the fused chunk kernel: 0 = automatic (where the columns
+                               allow, one 1024-row tile per block, 4 rows per thread read as
+                               16-byte column vectors; else the scalar kernel at 8 rows per
+                               thread), 2 = the bulk-copy pipeline (persistent blocks, at most
+                               blocks_per_sm per SM, 1024-row tiles of the row-logic columns
+                               copied into a ring of shared-memory stages, 4 rows per thread),
+                               8 or 16 = the scalar kernel with that many rows per thread and at
+                               most blocks_per_sm blocks per SM */
   uint32_t lookback_spin_limit; /* polls a radix sort pass makes of one predecessor tile's published
                                count before it gives up, sets its error word and the call returns
                                VX_E_TIMEOUT (0 = 2^20) */

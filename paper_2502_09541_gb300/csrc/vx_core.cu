@@ -291,7 +291,7 @@ VX_API vx_status vx_set_config(vx_ctx *ctx, const vx_config *cfg) {
       cfg->block_threads > 1024 || (cfg->block_threads & 31) || cfg->blocks_per_sm < 1 ||
       cfg->blocks_per_sm > 32 || (cfg->sched != VX_SCHED_IMMEDIATE && cfg->sched != VX_SCHED_DAG) ||
       cfg->wait_timeout_ms == 0 || cfg->zc_threshold < 0 || cfg->zc_threshold > 1 ||
-      (cfg->kernel_rows != 0 && cfg->kernel_rows != 8 && cfg->kernel_rows != 16)) {
+      (cfg->kernel_rows != 0 && cfg->kernel_rows != 2 && cfg->kernel_rows != 8 && cfg->kernel_rows != 16)) {
     set_error("vx_set_config: value out of range");
     return VX_E_INVAL;
   }

@@ -50,6 +50,7 @@ enum : uint32_t {
   ERR_RANGE = 2u,
   ERR_HT_FULL = 4u,
   ERR_OVERFLOW = 8u,
+  ERR_WAIT = 16u,  // a bounded device-side wait gave up
 };
 
 // ------------------------------------------------------------------ arena

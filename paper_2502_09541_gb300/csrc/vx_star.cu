@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "vx_bulk.cuh"
 #include "vx_internal.h"
 #include "vx_probe.cuh"
 #include "vx_star.cuh"
@@ -242,13 +243,6 @@ struct RegVals {
   const int4 (&v)[kV][kR];
   __device__ __forceinline__ int32_t operator()(int slot, int j) const { return slot_val(v[j >> 2], slot, j & 3); }
 };
-template <int kV>
-struct SmemVals {  // slot k, group v of thread t at sv[(k * kV + v) * 256 + t]
-  const int4 *sv;
-  __device__ __forceinline__ int32_t operator()(int slot, int j) const {
-    return lane4(sv[(slot * kV + (j >> 2)) * 256 + threadIdx.x], j & 3);
-  }
-};
 
 // Vector path: kV groups of 4 consecutive rows, r0 + v * kVecTileRows + 0..3
 // (r0 a multiple of 4, staged columns 16-byte aligned).  Every row-logic
@@ -278,24 +272,23 @@ __device__ __forceinline__ void star_load4(const ChunkParams &p, uint64_t r0, in
   }
 }
 
-template <bool kSmem, bool kSplit, int kV, class Vals, class Tile>
-__device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, const Vals &vals,
-                                           unsigned long long *ssum, unsigned long long *scnt,
-                                           unsigned long long &surv, Tile *st) {
-  constexpr int kN = 4 * kV;  // rows of this thread
-  bool alive[kN];
-  uint32_t g[kN];
-#pragma unroll
-  for (int j = 0; j < kN; ++j) {
-    alive[j] = row_of(r0, j) >= p.row_lo && row_of(r0, j) < p.n;
-    g[j] = 0;
-  }
+// the fact predicates of kN rows (alive[j] &= row j passes them)
+template <int kN, class Vals>
+__device__ __forceinline__ void star_fact_preds(const ChunkParams &p, const Vals &vals, bool (&alive)[kN]) {
   for (int q = 0; q < p.n_fact_preds; ++q) {
     const int s = p.fp_slot[q];
     const PredRange r = pred_range(p.fp_op[q], p.fp_lo[q], p.fp_hi[q]);
 #pragma unroll
     for (int j = 0; j < kN; ++j) alive[j] = alive[j] && pred_in(r, vals(s, j));
   }
+}
+
+// the probes (dimension predicates and group-code contributions) and fact
+// group keys of kN rows: alive[j] &= row j finds a qualifying row in every
+// dimension, g[j] += its group code
+template <int kN, class Vals>
+__device__ __forceinline__ void star_probe_dims(const ChunkParams &p, const Vals &vals, bool (&alive)[kN],
+                                                uint32_t (&g)[kN]) {
   for (int d = 0; d < p.n_dims; ++d) {
     const int s = p.dim_slot[d];
     int32_t key[kN];
@@ -360,6 +353,31 @@ __device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, co
       g[j] += (uint32_t)code * p.fgk_stride[k];
     }
   }
+}
+
+// predicates, probes and fact group keys of a thread's 4 x kV rows: alive[j]
+// = row j qualifies, g[j] = its group id
+template <int kV, class Vals>
+__device__ __forceinline__ void star_eval4(const ChunkParams &p, uint64_t r0, const Vals &vals, bool (&alive)[4 * kV],
+                                           uint32_t (&g)[4 * kV]) {
+  constexpr int kN = 4 * kV;
+#pragma unroll
+  for (int j = 0; j < kN; ++j) {
+    alive[j] = row_of(r0, j) >= p.row_lo && row_of(r0, j) < p.n;
+    g[j] = 0;
+  }
+  star_fact_preds<kN>(p, vals, alive);
+  star_probe_dims<kN>(p, vals, alive, g);
+}
+
+template <bool kSmem, bool kSplit, int kV, class Vals, class Tile>
+__device__ __forceinline__ void star_rows4(const ChunkParams &p, uint64_t r0, const Vals &vals,
+                                           unsigned long long *ssum, unsigned long long *scnt,
+                                           unsigned long long &surv, Tile *st) {
+  constexpr int kN = 4 * kV;  // rows of this thread
+  bool alive[kN];
+  uint32_t g[kN];
+  star_eval4<kV>(p, r0, vals, alive, g);
   if (p.chunk_surv) {
 #pragma unroll
     for (int j = 0; j < kN; ++j) surv += alive[j];
@@ -411,6 +429,12 @@ constexpr size_t vec_col_bytes(bool split, int kr) {
   return vec_cols(split, kr) ? (size_t)kr * vec_groups(split, kr) * 256 * sizeof(int4) : 0;
 }
 
+struct StageVals {  // row-logic slot k of the thread's 4 rows at base[k * stride]
+  const int4 *base;
+  uint32_t stride;
+  __device__ __forceinline__ int32_t operator()(int slot, int j) const { return lane4(base[slot * stride], j & 3); }
+};
+
 // thread t's rows r0 + v * kVecTileRows + 0..3 of every row-logic column into
 // scol[(k * kV + v) * 256 + t]
 template <int kR, int kV>
@@ -443,6 +467,7 @@ template <bool kSmem, bool kSplit, int kR>
 __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   constexpr bool kCols = vec_cols(kSplit, kR);
   constexpr int kG = vec_groups(kSplit, kR);
+  static_assert(kG == 1, "thread slots hold one group of 4 rows");
   extern __shared__ __align__(16) unsigned long long sacc[];  // [2 * n_groups] when kSmem, then column slots
   __shared__ SurvTileT<kG * kVecTileRows> st;
   int4 *scol = reinterpret_cast<int4 *>(sacc + (kSmem ? 2 * p.n_groups : 0));  // 16-byte aligned: even count
@@ -458,7 +483,7 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
     const uint64_t r0 = t0 + 4ull * threadIdx.x;
     if (kCols) {
       star_stage4<kR, kG>(p, r0, scol);
-      star_rows4<kSmem, kSplit, kG>(p, r0, SmemVals<kG>{scol}, ssum, scnt, surv, &st);
+      star_rows4<kSmem, kSplit, kG>(p, r0, StageVals{scol + threadIdx.x, 256}, ssum, scnt, surv, &st);
     } else {
       int4 cur[kVecGroups][kR];
       star_load4<kR, kVecGroups>(p, r0, cur);
@@ -490,6 +515,153 @@ __global__ void __launch_bounds__(256) star_vec_kernel(const ChunkParams p) {
   if (p.chunk_surv) {
     for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
     if ((threadIdx.x & 31) == 0 && surv) atomicAdd(&p.chunk_surv[p.chunk_idx], surv);
+  }
+}
+
+// Bulk-copy pipeline of the fused chunk kernel (the automatic vector path).
+// Persistent blocks of 256 threads walk their 1024-row tiles of the chunk.
+// Thread 0 copies each tile's row-logic columns into one stage of a ring of
+// shared-memory stages with cp.async.bulk, counted on the stage's mbarrier by
+// bytes, n_stages tiles ahead of the block; every thread waits on the stage's
+// barrier, evaluates its four rows from shared memory, and after the block's
+// barrier (every read of the stage done) thread 0 refills the stage with the
+// tile n_stages further on.  The copies of the next tiles stream from HBM
+// while the current tile's dimension lookups run.  Survivors (split mode) are
+// placed by warp ballots and one global atomic per tile that has any.  Waits
+// are bounded: a wait that gives up sets ERR_WAIT, the block stops after the
+// tile's barrier (the same decision in every thread), and thread 0 waits,
+// bounded again, for the copies it issued to land before the block exits.
+constexpr uint32_t kBulkTile = kVecTileRows;  // 4 rows per thread of 256
+constexpr uint32_t kBulkColBytes = kBulkTile * 4;
+constexpr int kBulkMaxStages = 8;
+
+// tile k of the block (global tile blockIdx.x + k gridDim.x) into stage s
+__device__ __forceinline__ void bulk_issue(const ChunkParams &p, uint32_t nr, uint32_t tile, int4 *stage,
+                                           uint64_t *bar) {
+  const uint32_t row0 = tile * kBulkTile;
+  const uint32_t rows = (uint32_t)p.n - row0 < kBulkTile ? (uint32_t)p.n - row0 : kBulkTile;
+  const uint32_t bytes = (rows & ~3u) * 4u;  // the partial last group of rows is read by its thread
+  if (bytes) {
+    mbar_arrive_expect_tx(bar, nr * bytes);
+    for (uint32_t k = 0; k < nr; ++k)
+      bulk_g2s(reinterpret_cast<char *>(stage) + k * kBulkColBytes, p.staged[p.rowrole[k]] + row0, bytes, bar);
+  } else {
+    mbar_arrive(bar);
+  }
+}
+
+template <bool kSmem, bool kSplit>
+__global__ void __launch_bounds__(256, 6) star_bulk_kernel(const ChunkParams p, uint32_t n_stages) {
+  extern __shared__ __align__(128) unsigned long long sacc[];  // [2 * n_groups] when kSmem, then the stages
+  __shared__ __align__(8) uint64_t full[kBulkMaxStages];
+  __shared__ uint32_t s_wcnt[2][8], s_base[2], s_abort[2];
+  __shared__ int4 s_tail[8];  // the chunk's partial last group of rows (one thread in the grid)
+  const uint32_t nr = (uint32_t)p.n_rowroles;
+  const uint32_t stage_i4 = nr * (kBulkTile / 4);  // int4 per stage
+  int4 *stages = reinterpret_cast<int4 *>(sacc + (kSmem ? 2 * p.n_groups : 0));  // 16-byte aligned
+  unsigned long long *ssum = sacc, *scnt = sacc + p.n_groups;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t n = (uint32_t)p.n;  // chunk rows (< 2^31 on this path)
+  const uint32_t n_tiles = (n + kBulkTile - 1) / kBulkTile;
+  const uint32_t my_n = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  uint32_t issued = 0;  // thread 0: tiles of this block whose copies were issued
+  if (tid == 0) {
+    for (uint32_t s = 0; s < n_stages; ++s) mbar_init(&full[s], 1);
+    s_abort[0] = s_abort[1] = 0;
+    mbar_fence_init();
+    for (; issued < n_stages && issued < my_n; ++issued)
+      bulk_issue(p, nr, blockIdx.x + issued * gridDim.x, stages + issued * stage_i4, &full[issued]);
+  }
+  if (kSmem) {
+    for (uint32_t g = tid; g < 2 * p.n_groups; g += blockDim.x) sacc[g] = 0;
+  }
+  __syncthreads();
+  unsigned long long surv = 0;
+  uint32_t s = 0, phase = 0, par = 0, k = 0;
+  for (; k < my_n; ++k) {
+    const uint32_t t = blockIdx.x + k * gridDim.x;
+    const bool ok = mbar_wait(&full[s], phase);
+    if (!ok) {
+      atomicOr(p.err, ERR_WAIT);
+      s_abort[par] = 1u;
+    }
+    const uint32_t r0 = t * kBulkTile + 4u * tid;
+    StageVals vals{stages + s * stage_i4 + tid, kBulkTile / 4};
+    if (r0 < n && r0 + 3 >= n) {  // rows past the chunk's last whole group: from global memory
+      for (uint32_t c = 0; c < nr; ++c) {
+        const int32_t *col = p.staged[p.rowrole[c]];
+        s_tail[c] = make_int4(__ldg(col + r0), r0 + 1 < n ? __ldg(col + r0 + 1) : 0,
+                              r0 + 2 < n ? __ldg(col + r0 + 2) : 0, 0);
+      }
+      vals = StageVals{s_tail, 1};
+    }
+    bool alive[4] = {false, false, false, false};
+    uint32_t g[4] = {0, 0, 0, 0};
+    if constexpr (kSplit) {
+      if (ok) star_eval4<1>(p, r0, vals, alive, g);
+    } else {
+      if (ok) star_rows4<kSmem, false, 1>(p, r0, vals, ssum, scnt, surv, static_cast<SurvTile *>(nullptr));
+    }
+    uint32_t b[4] = {0, 0, 0, 0}, wtot = 0;
+    if constexpr (kSplit) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        b[j] = __ballot_sync(0xffffffffu, alive[j]);
+        wtot += __popc(b[j]);
+      }
+      if (lane == 0) s_wcnt[par][warp] = wtot;
+    }
+    __syncthreads();  // every read of stage s done; warp counts and abort flags visible
+    const bool abort = s_abort[par] != 0;
+    if (tid == 0 && !abort && issued < my_n) {
+      bulk_issue(p, nr, blockIdx.x + issued * gridDim.x, stages + s * stage_i4, &full[s]);
+      ++issued;
+    }
+    if constexpr (kSplit) {
+      uint32_t total = 0, woff = 0;
+#pragma unroll
+      for (uint32_t w = 0; w < 8; ++w) {
+        const uint32_t c = s_wcnt[par][w];
+        woff += w < warp ? c : 0u;
+        total += c;
+      }
+      if (p.chunk_surv && lane == 0) surv += wtot;
+      if (total) {
+        if (tid == 0) s_base[par] = atomicAdd(p.surv_cnt, total);
+        __syncthreads();
+        const uint32_t lt = (1u << lane) - 1u;
+        uint32_t o = s_base[par] + woff;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (alive[j] && o + __popc(b[j] & lt) < p.surv_cap)
+            p.surv_list[o + __popc(b[j] & lt)] = make_uint2(r0 + (uint32_t)j, g[j]);
+          o += __popc(b[j]);
+        }
+      }
+    }
+    par ^= 1u;
+    if (++s == n_stages) {
+      s = 0;
+      phase ^= 1u;
+    }
+    if (abort) break;
+  }
+  if (tid == 0) {  // copies issued for tiles the block did not consume (a wait gave up) land first
+    for (uint32_t j = k; j < issued; ++j)
+      if (!mbar_wait(&full[j % n_stages], (j / n_stages) & 1u)) atomicOr(p.err, ERR_WAIT);
+  }
+  if (kSmem) {
+    __syncthreads();
+    for (uint32_t q = tid; q < p.n_groups; q += blockDim.x) {
+      if (scnt[q]) {
+        atomicAdd(&p.g_sum[q], ssum[q]);
+        atomicAdd(&p.g_cnt[q], scnt[q]);
+      }
+    }
+  }
+  if (p.chunk_surv) {
+    for (int off = 16; off > 0; off >>= 1) surv += __shfl_down_sync(0xffffffffu, surv, off);
+    if (lane == 0 && surv) atomicAdd(&p.chunk_surv[p.chunk_idx], surv);
   }
 }
 // ---- end of the fused chunk kernel's device code
@@ -546,9 +718,70 @@ static vx_status launch_vec(const vx_ctx *ctx, const ChunkParams &p, int kr, siz
 }
 
 
+// The bulk-copy pipeline: a resident grid of at most blocks_per_sm blocks per
+// SM; the stages fill the shared memory that blocks_per_sm blocks leave after
+// the group accumulators (acc_smem bytes), 2 to kBulkMaxStages stages.
+template <bool kSmem, bool kSplit>
+static vx_status launch_bulk(const vx_ctx *ctx, const ChunkParams &p, size_t acc_smem, cudaStream_t s) {
+  static int smem_optin = 0, smem_sm = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaGetLastError();
+  });
+  static bool attr = false;
+  constexpr size_t kStatic = 1024;  // the kernel's static shared memory, rounded up
+  if (smem_optin <= (int)kStatic || smem_sm <= 0) {
+    set_error("launch_bulk: shared-memory limits unavailable");
+    return VX_E_CUDA;
+  }
+  if (!attr) {
+    VX_CUDA_TRY(cudaFuncSetAttribute(star_bulk_kernel<kSmem, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem_optin - (int)kStatic));
+    attr = true;
+  }
+  const uint32_t nr = (uint32_t)p.n_rowroles;
+  const size_t stage = (size_t)nr * kBulkColBytes;
+  const int bps = std::max(1, std::min(8, ctx->cfg.blocks_per_sm));
+  // per block: its share of the SM's shared memory less the static part and
+  // the 1 KB the hardware reserves per block
+  const size_t share = (size_t)smem_sm / bps > 2 * kStatic ? (size_t)smem_sm / bps - 2 * kStatic : 0;
+  size_t n_st = share > acc_smem ? (share - acc_smem) / stage : 0;
+  n_st = std::max<size_t>(2, std::min<size_t>(kBulkMaxStages, n_st));
+  while (n_st > 2 && acc_smem + n_st * stage > (size_t)smem_optin - kStatic) --n_st;
+  const size_t smem = acc_smem + n_st * stage;
+  if (smem > (size_t)smem_optin - kStatic) {
+    set_error("launch_bulk: accumulators and two stages exceed a block's shared memory");
+    return VX_E_UNSUPPORTED;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, star_bulk_kernel<kSmem, kSplit>, 256, smem) !=
+          cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  cudaGetLastError();
+  const uint64_t tiles = (p.n + kBulkTile - 1) / kBulkTile;
+  const uint64_t grid =
+      std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->num_sms * (uint64_t)std::min(occ, bps)));
+  star_bulk_kernel<kSmem, kSplit><<<(unsigned)grid, 256, smem, s>>>(p, (uint32_t)n_st);
+  return VX_OK;
+}
+
 // width (2, 4, 6 or 8 loaded columns) of the vector path for a chunk, or 0
 // for the scalar path (no row-logic column, more than 8, or a staged column
 // not 16-byte aligned)
+// kernel_rows 0 (automatic: one tile per block) and 2 (the bulk-copy
+// pipeline) take the vector path where a chunk allows it; 8 and 16 the scalar
+// kernel
+static bool vec_path(const vx_ctx *ctx) { return ctx->cfg.kernel_rows == 0 || ctx->cfg.kernel_rows == 2; }
+// the bulk-copy pipeline indexes a chunk's rows in 32 bits
+static bool bulk_ok(const vx_ctx *ctx, const ChunkParams &p) {
+  return ctx->cfg.kernel_rows == 2 && p.n < (1ull << 31);
+}
+
 static int vec_width(const ChunkParams &p) {
   if (p.n_rowroles < 1 || p.n_rowroles > 8) return 0;
   for (int k = 0; k < p.n_rowroles; ++k) {
@@ -1152,6 +1385,10 @@ vx_status check_err_word(vx_ctx *ctx, const uint32_t *d_err) {
     set_error("a survivor list overflowed with no rerun to catch it");
     return VX_E_CUDA;
   }
+  if (e & ERR_WAIT) {
+    set_error("a chunk kernel's wait for its staged tiles ran past its limit");
+    return VX_E_TIMEOUT;
+  }
   return VX_OK;
 }
 
@@ -1241,8 +1478,10 @@ struct StarExKernel : ExKernel {
       p.surv_cap = (unsigned int)surv_region();
       VX_CUDA_TRY(cudaMemsetAsync(p.surv_cnt, 0, 4, s));
       if (timed) VX_CUDA_TRY(rec(ev_a[ek]));
-      const int kr = ctx->cfg.kernel_rows ? 0 : vec_width(p);
-      if (kr) {
+      const int kr = vec_path(ctx) ? vec_width(p) : 0;
+      if (kr && bulk_ok(ctx, p)) {
+        VX_TRY((launch_bulk<false, true>(ctx, p, 0, s)));
+      } else if (kr) {
         VX_TRY((launch_vec<false, true>(ctx, p, kr, 0, s)));
       } else {
         const int gs = grid_for(ctx, (p.n + kStarTileRows - 1) / kStarTileRows, 1);
@@ -1271,8 +1510,14 @@ struct StarExKernel : ExKernel {
     }
     launches += 1;
     if (timed) VX_CUDA_TRY(rec(ev_a[ek]));
-    const int kr = ctx->cfg.kernel_rows ? 0 : vec_width(p);
-    if (kr) {  // vector path
+    const int kr = vec_path(ctx) ? vec_width(p) : 0;
+    if (kr && bulk_ok(ctx, p)) {  // bulk-copy pipeline
+      if (smem) {
+        VX_TRY((launch_bulk<true, false>(ctx, p, smem_bytes, s)));
+      } else {
+        VX_TRY((launch_bulk<false, false>(ctx, p, 0, s)));
+      }
+    } else if (kr) {  // one tile per block
       if (smem) {
         VX_TRY((launch_vec<true, false>(ctx, p, kr, smem_bytes, s)));
       } else {
@@ -2173,10 +2418,11 @@ VX_API vx_status vx_autotune(vx_ctx *ctx, const vx_plan *plan, uint64_t sample_r
       }
     }
   }
-  // launch shape of the fused kernel at the best chunking: the automatic
-  // vector path against the scalar kernel at 8 or 16 rows per thread and 4
-  // or 8 resident blocks per SM
-  const int shapes[5][2] = {{0, 0}, {8, 4}, {8, 8}, {16, 4}, {16, 8}};
+  // launch shape of the fused kernel at the best chunking: one tile per block,
+  // the bulk-copy pipeline at 4 or 6 blocks per SM (a ring of 3 or 2 stages),
+  // and the scalar kernel at 8 or 16 rows per thread and 4 or 8 resident
+  // blocks per SM
+  const int shapes[7][2] = {{0, 0}, {2, 4}, {2, 6}, {8, 4}, {8, 8}, {16, 4}, {16, 8}};
   const vx_config chunked = best_cfg;
   for (const auto &sh : shapes) {
     vx_config c = chunked;

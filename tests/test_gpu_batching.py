@@ -78,7 +78,7 @@ def test_autotuner_picks_a_candidate_and_keeps_results(star):
     best = vx.vx_autotune(ctx, plan, 2_000_000)
     assert best.chunk_bytes in [m << 20 for m in (8, 16, 32, 64, 128, 256)]
     assert best.n_slots in (2, 3, 4)
-    assert best.kernel_rows in (0, 8, 16) and best.blocks_per_sm in (4, 8)
+    assert best.kernel_rows in (0, 2, 8, 16) and best.blocks_per_sm in (4, 6, 8)
     cur = vx.vx_get_config(ctx)
     assert cur.chunk_bytes == best.chunk_bytes and cur.n_slots == best.n_slots
     assert cur.kernel_rows == best.kernel_rows and cur.blocks_per_sm == best.blocks_per_sm
@@ -87,12 +87,14 @@ def test_autotuner_picks_a_candidate_and_keeps_results(star):
     assert np.array_equal(gid, gid_e) and np.array_equal(s, s_e) and np.array_equal(c, c_e)
 
 
-@pytest.mark.parametrize("rows,bps", [(0, 4), (8, 4), (8, 8), (16, 4), (16, 8)])
+@pytest.mark.parametrize("rows,bps", [(0, 4), (2, 1), (2, 2), (2, 4), (2, 6), (2, 8), (8, 4), (8, 8), (16, 4), (16, 8)])
 @pytest.mark.parametrize("late", [vx.VX_LATE_FORCE_EARLY, vx.VX_LATE_FORCE_LATE])
 def test_kernel_shapes_bit_exact(star, rows, bps, late):
-    """Every launch shape the autotuner may pick (vector path, scalar kernel
-    at 8 or 16 rows per thread and 4 or 8 blocks per SM), in both the fused
-    and the split (late-column gather) forms."""
+    """Every launch shape the autotuner may pick (one tile per block, the
+    bulk-copy pipeline at 1 to 8 blocks per SM, i.e. 8 down to 2
+    shared-memory stages, the scalar kernel at 8 or 16 rows per thread and 4
+    or 8 blocks per SM), in both the fused and the split (late-column gather)
+    forms, over a row range whose chunks end in partial groups of rows."""
     ctx, fact, dims, fid, did = star
     cfg = vx.vx_get_config(ctx)
     saved = (cfg.kernel_rows, cfg.blocks_per_sm, cfg.chunk_bytes)
