@@ -172,7 +172,7 @@ vx_status vx_filter(vx_ctx *ctx, const vx_pred *preds, int32_t n_preds, uint64_t
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress with that device current) and keeps it for the
  *     life of the process, so the device must not be reset (cudaDeviceReset)
- *     between calls; make that first call before any stream capture;
+ *     between calls;
  *   - every call shares the one array, so calls whose work overlaps on the
  *     GPU (other streams, other host threads) race and give wrong results:
  *     serialise them. */
