@@ -792,6 +792,18 @@ def run_ours(args):
                   "survivors_per_launch": round(sum(s["survivors"] for s in stats_all if s["late_mask"]) /
                                                 max(1, sum(s["chunks"] for s in stats_all if s["late_mask"]))),
                   "avg_launch_us": round(1000 * g_ms / max(1, sum(s["chunks"] for s in stats_all if s["late_mask"])), 2)}
+        # its ceiling: the same number of sparse reads per launch over a window
+        # of one chunk's rows of one column, alone on an idle link
+        late = [s for s in stats_all if s["late_mask"]]
+        n_launch = max(1, sum(s["chunks"] for s in late))
+        reads = max(1, round(zc_vals / n_launch))
+        window = 4 * max(1, round(sum(s["rows"] for s in late) / n_launch))
+        us_first, us_warm, _ = vx.vx_probe_zero_copy_gather(ctx, window, reads)
+        gather["ceiling"] = {"probe": "vx_probe_zero_copy_gather", "reads_per_launch": reads, "window_bytes": window,
+                             "us_first": round(us_first, 2), "us_warm": round(us_warm, 2),
+                             "g_reads_per_s": round(reads / us_warm / 1e3, 3),
+                             "granule_gbs": round(64 * reads / us_warm / 1e3, 1)}
+        gather["of_ceiling"] = round(us_warm / gather["avg_launch_us"], 4) if gather["avg_launch_us"] else None
 
     # ---- learned / batched form: regressor trained on the plain form's log,
     # per-chunk late/early decisions, autotuned chunking, captured graphs
@@ -990,6 +1002,7 @@ def summarize(line):
     if g:
         out["gather_link_frac"] = g.get("frac")
         out["gather_survivors_per_launch"] = g.get("survivors_per_launch")
+        out["gather_of_sparse_read_ceiling"] = g.get("of_ceiling")
     sv = line.get("serving")
     if sv:
         out["serving_ms"] = {"p50": sv.get("p50_ms"), "p99": sv.get("p99_ms")}

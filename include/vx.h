@@ -640,6 +640,19 @@ vx_status vx_serve_stop(vx_ctx *ctx);
 vx_status vx_probe_zero_copy(vx_ctx *ctx, uint64_t n, const int32_t *sels, int32_t n_sel, double *ms_zero_copy,
                              double *ms_copy, uint64_t *checksums);
 
+/* Ceiling of the late-materialization gather (Section 6.3's zero-copy reads,
+ * sparse): one launch reads n_reads 4-byte values at sorted uniform positions
+ * (SplitMix64 of seed) of a window_bytes buffer of pinned, mapped host memory,
+ * grid of 4 blocks of 256 threads per SM, one read per thread, the link
+ * otherwise idle.  us_first: the first launch (the window's pages touched for
+ * the first time); us_warm: the best of three more.  The sum of the values
+ * read is checked on the host (checksum, optional).  The paper has no
+ * counterpart: it is this library's denominator for the gather kernel.
+ * VX_E_INVAL for window_bytes < 4 or above 2^34, or n_reads == 0; VX_E_NOMEM
+ * if the indices do not fit the arena. */
+vx_status vx_probe_zero_copy_gather(vx_ctx *ctx, uint64_t window_bytes, uint32_t n_reads, uint64_t seed,
+                                    double *us_first, double *us_warm, uint64_t *checksum);
+
 /* ---------------------------------------------------------------- link probe */
 
 /* Pinned-copy microbenchmark of the host link (Section 8.1 measures Exchange

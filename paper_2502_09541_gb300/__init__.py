@@ -193,6 +193,7 @@ SIGNATURES = {
     "vx_probe_hbm_random": ([_vp, _u64, _u64, _P(_dbl)], _i32),
     "vx_probe_stream": ([_vp, _u64, _i32, _P(_dbl)], _i32),
     "vx_probe_zero_copy": ([_vp, _u64, _vp, _i32, _vp, _vp, _vp], _i32),
+    "vx_probe_zero_copy_gather": ([_vp, _u64, _u32, _u64, _P(_dbl), _P(_dbl), _P(_u64)], _i32),
     "vx_sort": ([_vp, _i32, _i32, _vp, _vp, _P(vx_sort_opts), _P(vx_sort_stats)], _i32),
     "vx_radix_sort_pairs": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_range_partition": ([_vp, _vp, _vp, _u64, _vp, _u32, _vp, _vp, _vp], _i32),
@@ -489,6 +490,15 @@ def vx_probe_zero_copy(ctx, n: int, sels):
     ck = np.zeros(len(s), np.uint64)
     _check(load().vx_probe_zero_copy(ctx, n, s.ctypes.data, len(s), zc.ctypes.data, ce.ctypes.data, ck.ctypes.data))
     return zc, ce, ck
+
+
+def vx_probe_zero_copy_gather(ctx, window_bytes: int, n_reads: int, seed: int = 1):
+    """(us_first, us_warm, checksum) of one sparse gather launch over mapped
+    host memory: n_reads 4-byte reads at sorted uniform positions of a window."""
+    a, b, c = _dbl(), _dbl(), _u64()
+    _check(load().vx_probe_zero_copy_gather(ctx, window_bytes, n_reads, seed, ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def vx_probe_stream(ctx, nbytes: int, reps: int) -> float:

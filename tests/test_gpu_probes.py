@@ -60,3 +60,17 @@ def test_stream_probe(ctx):
         vx.vx_probe_stream(ctx, 8, 3)
     with pytest.raises(vx.VxError):
         vx.vx_probe_stream(ctx, 1 << 20, 0)
+
+
+def test_zero_copy_gather_probe(ctx):
+    """Sparse reads of mapped host memory: the probe checks its own sum (the
+    call fails otherwise), more reads per launch take longer but run at a
+    higher rate, and bad arguments are refused."""
+    f1, w1, c1 = vx.vx_probe_zero_copy_gather(ctx, 11 << 20, 2000)
+    f2, w2, c2 = vx.vx_probe_zero_copy_gather(ctx, 11 << 20, 100_000)
+    assert 0 < w1 < 10_000 and 0 < w2 < 100_000 and f1 > 0 and f2 > 0
+    assert w2 > w1 and 100_000 / w2 > 2000 / w1
+    assert c1 > 0 and c2 > c1
+    for bad in ((0, 10), (11 << 20, 0), (1 << 40, 10)):
+        with pytest.raises(vx.VxError):
+            vx.vx_probe_zero_copy_gather(ctx, *bad)
