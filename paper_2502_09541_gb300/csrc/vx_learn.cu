@@ -1,6 +1,7 @@
 // Learned range partitioner: a monotone CDF MLP (1 -> H -> 1, fp32) trained on
-// the device with hand-written forward/backward and Adam kernels, replayed
-// from a captured CUDA graph, then inverted by bisection to give integer
+// the device with a hand-written forward/backward kernel whose last block
+// applies the Adam step (one launch per step, captured in one CUDA
+// graph per 25 steps), then inverted by bisection to give integer
 // splitters.  The model only decides where partitions are cut; every cut gives
 // the same sorted output.
 //
@@ -22,71 +23,82 @@ __device__ __forceinline__ float sigmoidf(float v) { return 1.f / (1.f + expf(-v
 constexpr int kMlpMaxH = 64;
 constexpr int kMlpThreads = 256;
 
+struct AdamState {
+  float m1[3 * kMlpMaxH + 1], m2[3 * kMlpMaxH + 1];
+  int t;
+};
+
+// one Adam update (Kingma & Ba 2015) of parameter k at step `step`
+__device__ __forceinline__ void adam_update(float *theta, float g, AdamState *st, int k, int step, float lr, float b1,
+                                            float b2, float eps) {
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  const float m1 = b1 * st->m1[k] + (1.f - b1) * g;
+  const float m2 = b2 * st->m2[k] + (1.f - b2) * g * g;
+  st->m1[k] = m1;
+  st->m2[k] = m2;
+  theta[k] -= lr * (m1 / c1) / (sqrtf(m2 / c2) + eps);
+}
+
+// Adam settings of a fused training step (adam == nullptr: gradient only)
+struct StepArgs {
+  AdamState *adam;
+  unsigned int *done;  // blocks that have added their gradient; the last one steps
+  float lr, b1, b2, eps;
+};
+
 // dL/dtheta and L over m points; grad/loss are accumulated with atomics
-// (caller zeroes them).  theta = [omega(H), beta(H), alpha(H), gamma].
+// (caller zeroes them).  theta = [omega(H), beta(H), alpha(H), gamma].  Lane
+// j of a warp owns hidden unit j (H <= 32): a warp evaluates one point at a
+// time, every lane its unit, a butterfly sum gives y, and each lane keeps its
+// unit's three partial derivatives in registers.  With sa.adam set, the
+// last block to finish applies the Adam step to theta from the summed
+// gradient and zeroes grad, loss and the block counter for the next step, so
+// one launch is one training step.
 template <int H>
-__global__ void __launch_bounds__(kMlpThreads) mlp_fwd_bwd_kernel(const float *__restrict__ theta,
+__global__ void __launch_bounds__(kMlpThreads, 2) mlp_fwd_bwd_kernel(float *__restrict__ theta,
                                                                    const float *__restrict__ x,
                                                                    const float *__restrict__ t, uint64_t m,
-                                                                   float *grad, float *loss) {
-  __shared__ float w[H], b[H], a[H], dw[H], da[H];
+                                                                   float *grad, float *loss, StepArgs sa) {
+  static_assert(H >= 1 && H <= 32, "one hidden unit per lane");
   __shared__ float sg[3 * H + 2];
-  for (int j = threadIdx.x; j < H; j += blockDim.x) {
-    w[j] = softplusf(theta[j]);
-    dw[j] = sigmoidf(theta[j]);
-    b[j] = theta[H + j];
-    a[j] = softplusf(theta[2 * H + j]);
-    da[j] = sigmoidf(theta[2 * H + j]);
-  }
   for (int k = threadIdx.x; k < 3 * H + 2; k += blockDim.x) sg[k] = 0.f;
   __syncthreads();
+  const unsigned lane = threadIdx.x & 31;
+  const bool on = lane < (unsigned)H;
+  const float w = on ? softplusf(theta[lane]) : 0.f, dw = on ? sigmoidf(theta[lane]) : 0.f;
+  const float b = on ? theta[H + lane] : 0.f;
+  const float a = on ? softplusf(theta[2 * H + lane]) : 0.f, da = on ? sigmoidf(theta[2 * H + lane]) : 0.f;
   const float gamma = theta[3 * H];
   const float inv_m = 1.f / (float)m;
-  float g_om[H], g_be[H], g_al[H];
+  float g_om = 0.f, g_be = 0.f, g_al = 0.f, g_ga = 0.f, l = 0.f;
+  // a warp takes 32 consecutive points at a time: one coalesced load of x and
+  // t, then the points one by one, broadcast from the lane that loaded them
+  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
+       base += n_warps * 32) {
+    const uint64_t mine = base + lane;
+    const float xl = mine < m ? x[mine] : 0.f, tl = mine < m ? t[mine] : 0.f;
+    const int cnt = m - base < 32 ? (int)(m - base) : 32;
+    for (int k = 0; k < cnt; ++k) {
+      const float xi = __shfl_sync(0xffffffffu, xl, k), ti = __shfl_sync(0xffffffffu, tl, k);
+      const float si = on ? sigmoidf(w * xi + b) : 0.f;
+      float v = a * si;
 #pragma unroll
-  for (int j = 0; j < H; ++j) g_om[j] = g_be[j] = g_al[j] = 0.f;
-  float g_ga = 0.f, l = 0.f;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
-    const float xi = x[i];
-    float s[H];
-    float y = gamma;
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      s[j] = sigmoidf(w[j] * xi + b[j]);
-      y += a[j] * s[j];
-    }
-    const float r = y - t[i];
-    l += r * r;
-    const float dy = 2.f * r * inv_m;
-    g_ga += dy;
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const float ds = s[j] * (1.f - s[j]);
-      const float q = dy * a[j] * ds;
-      g_be[j] += q;
-      g_om[j] += q * xi * dw[j];
-      g_al[j] += dy * da[j] * s[j];
-    }
-  }
-  // warp reductions, then one shared atomic per warp and value
-  const unsigned lane = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < H; ++j) {
-    float v0 = g_om[j], v1 = g_be[j], v2 = g_al[j];
-    for (int off = 16; off > 0; off >>= 1) {
-      v0 += __shfl_down_sync(0xffffffffu, v0, off);
-      v1 += __shfl_down_sync(0xffffffffu, v1, off);
-      v2 += __shfl_down_sync(0xffffffffu, v2, off);
-    }
-    if (lane == 0) {
-      atomicAdd(&sg[j], v0);
-      atomicAdd(&sg[H + j], v1);
-      atomicAdd(&sg[2 * H + j], v2);
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      const float r = gamma + v - ti;
+      const float dy = 2.f * r * inv_m;
+      l += r * r;  // the same in every lane; lane 0's copy is kept
+      g_ga += dy;
+      const float q = dy * a * si * (1.f - si);
+      g_be += q;
+      g_om += q * xi * dw;
+      g_al += dy * da * si;
     }
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    g_ga += __shfl_down_sync(0xffffffffu, g_ga, off);
-    l += __shfl_down_sync(0xffffffffu, l, off);
+  if (on) {
+    atomicAdd(&sg[lane], g_om);
+    atomicAdd(&sg[H + lane], g_be);
+    atomicAdd(&sg[2 * H + lane], g_al);
   }
   if (lane == 0) {
     atomicAdd(&sg[3 * H], g_ga);
@@ -95,30 +107,26 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_fwd_bwd_kernel(const float *_
   __syncthreads();
   for (int k = threadIdx.x; k < 3 * H + 1; k += blockDim.x) atomicAdd(&grad[k], sg[k]);
   if (threadIdx.x == 0) atomicAdd(loss, sg[3 * H + 1] * inv_m);
-}
-
-struct AdamState {
-  float m1[3 * kMlpMaxH + 1], m2[3 * kMlpMaxH + 1];
-  int t;
-};
-
-// one Adam step (Kingma & Ba 2015) on n parameters
-__global__ void adam_kernel(float *theta, const float *grad, AdamState *st, int n, float lr, float b1, float b2,
-                            float eps) {
-  __shared__ int step;
-  if (threadIdx.x == 0) step = st->t + 1;
+  if (!sa.adam) return;
+  // the last block to finish: every other block's atomics are done
+  __shared__ bool last;
+  __threadfence();
   __syncthreads();
-  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const float g = grad[k];
-    const float m1 = b1 * st->m1[k] + (1.f - b1) * g;
-    const float m2 = b2 * st->m2[k] + (1.f - b2) * g * g;
-    st->m1[k] = m1;
-    st->m2[k] = m2;
-    theta[k] -= lr * (m1 / c1) / (sqrtf(m2 / c2) + eps);
+  if (threadIdx.x == 0) last = atomicAdd(sa.done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int step = sa.adam->t + 1;
+  for (int k = threadIdx.x; k < 3 * H + 1; k += blockDim.x) {
+    adam_update(theta, __ldcg(&grad[k]), sa.adam, k, step, sa.lr, sa.b1, sa.b2, sa.eps);
+    grad[k] = 0.f;
   }
   __syncthreads();
-  if (threadIdx.x == 0) st->t = step;
+  if (threadIdx.x == 0) {
+    sa.adam->t = step;
+    *loss = 0.f;
+    *sa.done = 0u;
+  }
 }
 
 // data-driven initial parameters from the (sorted) training points: unit j is
@@ -191,6 +199,7 @@ __global__ void mlp_splitters_kernel(const float *theta, const uint64_t *sorted,
 struct MlpWork {
   DevBuf buf;
   float *theta, *grad, *loss, *x, *t;
+  unsigned int *done;
   AdamState *adam;
 };
 
@@ -206,6 +215,7 @@ static vx_status mlp_alloc(vx_ctx *ctx, uint64_t M, MlpWork &w) {
   w.theta = (float *)p;
   w.grad = (float *)(p + 1024);
   w.loss = (float *)(p + 2048);
+  w.done = (unsigned int *)(p + 2048 + 64);
   w.adam = (AdamState *)(p + 4096);
   char *q = p + 4096 + ((sizeof(AdamState) + 255) & ~255ull);
   w.x = (float *)q;
@@ -213,16 +223,23 @@ static vx_status mlp_alloc(vx_ctx *ctx, uint64_t M, MlpWork &w) {
   return VX_OK;
 }
 
-static vx_status launch_fwd_bwd(int H, const float *theta, const float *x, const float *t, uint64_t m, float *grad,
-                                float *loss, int grid, cudaStream_t s) {
+// blocks of the forward/backward kernel: 32 points per warp, at most two
+// blocks per SM (each block adds 3H + 2 atomics to the global gradient)
+static int mlp_grid(const vx_ctx *ctx, uint64_t m) {
+  const uint64_t per_block = 32 * (kMlpThreads / 32);
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>((m + per_block - 1) / per_block, 2ull * ctx->num_sms));
+}
+
+static vx_status launch_fwd_bwd(int H, float *theta, const float *x, const float *t, uint64_t m, float *grad,
+                                float *loss, int grid, cudaStream_t s, StepArgs a = StepArgs{}) {
   if (H == 32)
-    mlp_fwd_bwd_kernel<32><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss);
+    mlp_fwd_bwd_kernel<32><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss, a);
   else if (H == 16)
-    mlp_fwd_bwd_kernel<16><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss);
+    mlp_fwd_bwd_kernel<16><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss, a);
   else if (H == 8)
-    mlp_fwd_bwd_kernel<8><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss);
+    mlp_fwd_bwd_kernel<8><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss, a);
   else if (H == 1)
-    mlp_fwd_bwd_kernel<1><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss);
+    mlp_fwd_bwd_kernel<1><<<grid, kMlpThreads, 0, s>>>(theta, x, t, m, grad, loss, a);
   else {
     set_error("MLP width %d not built (1, 8, 16, 32)", H);
     return VX_E_UNSUPPORTED;
@@ -231,27 +248,21 @@ static vx_status launch_fwd_bwd(int H, const float *theta, const float *x, const
   return VX_OK;
 }
 
-// one training step: zero grad/loss, forward+backward, Adam
-static vx_status enqueue_step(int H, MlpWork &w, uint64_t m, float lr, int grid, cudaStream_t s) {
-  VX_CUDA_TRY(cudaMemsetAsync(w.grad, 0, 2048, s));  // grad[0..3H] and loss
-  VX_TRY(launch_fwd_bwd(H, w.theta, w.x, w.t, m, w.grad, w.loss, grid, s));
-  adam_kernel<<<1, 256, 0, s>>>(w.theta, w.grad, w.adam, 3 * H + 1, lr, 0.9f, 0.999f, 1e-8f);
-  VX_CUDA_TRY(cudaGetLastError());
-  return VX_OK;
-}
+// trains with `steps` Adam steps: every step is one launch (forward,
+// backward, and the Adam update in the last block to finish); up to
+// kStepsPerGraph consecutive steps are captured in one CUDA graph, which is
+// launched as often as needed (one more graph for a remainder), so capture and
+// instantiation stay short
+constexpr uint32_t kStepsPerGraph = 25;
 
-// trains with `steps` Adam steps; the step is captured once in a CUDA graph
-// and replayed
-static vx_status train(vx_ctx *ctx, int H, MlpWork &w, uint64_t m, uint32_t steps, float lr) {
-  cudaStream_t s = ctx->s_compute;
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((m + kMlpThreads * 4 - 1) / (kMlpThreads * 4),
-                                                                  (uint64_t)ctx->num_sms));
-  VX_CUDA_TRY(cudaMemsetAsync(w.adam, 0, sizeof(AdamState), s));
-  if (steps == 0) return VX_OK;
+static vx_status launch_steps(int H, MlpWork &w, uint64_t m, uint32_t n, int grid, const StepArgs &a,
+                              cudaStream_t s, uint32_t times) {
+  if (n == 0 || times == 0) return VX_OK;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   VX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  vx_status st = enqueue_step(H, w, m, lr, grid, s);
+  vx_status st = VX_OK;
+  for (uint32_t i = 0; i < n && st == VX_OK; ++i) st = launch_fwd_bwd(H, w.theta, w.x, w.t, m, w.grad, w.loss, grid, s, a);
   cudaError_t ce = cudaStreamEndCapture(s, &g);
   if (st != VX_OK) {
     if (g) cudaGraphDestroy(g);
@@ -261,12 +272,22 @@ static vx_status train(vx_ctx *ctx, int H, MlpWork &w, uint64_t m, uint32_t step
   ce = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
   VX_CUDA_TRY(ce);
-  for (uint32_t i = 0; i < steps; ++i) {
-    ce = cudaGraphLaunch(ge, s);
-    if (ce != cudaSuccess) break;
-  }
+  for (uint32_t r = 0; r < times && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(ge, s);
   cudaGraphExecDestroy(ge);
   VX_CUDA_TRY(ce);
+  return VX_OK;
+}
+
+static vx_status train(vx_ctx *ctx, int H, MlpWork &w, uint64_t m, uint32_t steps, float lr) {
+  cudaStream_t s = ctx->s_compute;
+  const int grid = mlp_grid(ctx, m);
+  VX_CUDA_TRY(cudaMemsetAsync(w.adam, 0, sizeof(AdamState), s));
+  VX_CUDA_TRY(cudaMemsetAsync(w.grad, 0, 2048, s));  // grad[0..3H], loss, block counter
+  const StepArgs a{w.adam, w.done, lr, 0.9f, 0.999f, 1e-8f};
+  const uint32_t per = std::min(steps, kStepsPerGraph);
+  if (per == 0) return VX_OK;
+  VX_TRY(launch_steps(H, w, m, per, grid, a, s, steps / per));
+  VX_TRY(launch_steps(H, w, m, steps % per, grid, a, s, 1));
   return VX_OK;
 }
 
@@ -323,7 +344,7 @@ VX_API vx_status vx_mlp_loss_grad(vx_ctx *ctx, const float *theta, int32_t H, co
   cudaStream_t s = ctx->s_compute;
   VX_CUDA_TRY(cudaMemcpyAsync(w.theta, theta, 4 * (3 * H + 1), cudaMemcpyHostToDevice, s));
   VX_CUDA_TRY(cudaMemsetAsync(w.grad, 0, 2048, s));
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((m + 1023) / 1024, (uint64_t)ctx->num_sms));
+  const int grid = mlp_grid(ctx, m);
   VX_TRY(launch_fwd_bwd(H, w.theta, w.x, w.t, m, w.grad, w.loss, grid, s));
   VX_CUDA_TRY(cudaMemcpyAsync(grad_out, w.grad, 4 * (3 * H + 1), cudaMemcpyDeviceToHost, s));
   VX_CUDA_TRY(cudaMemcpyAsync(loss_out, w.loss, 4, cudaMemcpyDeviceToHost, s));
@@ -344,7 +365,7 @@ VX_API vx_status vx_mlp_train(vx_ctx *ctx, float *theta, int32_t H, const float 
   VX_TRY(train(ctx, H, w, m, steps, lr));
   // loss of the final parameters
   VX_CUDA_TRY(cudaMemsetAsync(w.grad, 0, 2048, s));
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((m + 1023) / 1024, (uint64_t)ctx->num_sms));
+  const int grid = mlp_grid(ctx, m);
   VX_TRY(launch_fwd_bwd(H, w.theta, w.x, w.t, m, w.grad, w.loss, grid, s));
   VX_CUDA_TRY(cudaMemcpyAsync(theta, w.theta, 4 * (3 * H + 1), cudaMemcpyDeviceToHost, s));
   VX_CUDA_TRY(cudaMemcpyAsync(loss_out, w.loss, 4, cudaMemcpyDeviceToHost, s));
