@@ -323,11 +323,14 @@ vx_status vx_chunk_log_clear(vx_ctx *ctx);
  * plan: times the plan over its first sample_rows fact rows (best of two
  * timed runs after one warm-up each) for every chunk size in {8, 16, 32, 64,
  * 128, 256} MiB and staging ring depth in {2, 3, 4} that fits the arena, then,
- * at the fastest of those, for every kernel shape in {automatic vector path,
- * scalar 8 or 16 rows per thread at 4 or 8 blocks per SM}; keeps the fastest
- * in the context's config and returns it.  Section 8.1 sweeps Exchange's
- * packet size the same way (fixed per-copy overhead against pipeline depth).
- * Results do not depend on the configuration, only the time does. */
+ * at the fastest of those, for every kernel shape in {one tile per block, the
+ * bulk-copy pipeline at 4 or 6 blocks per SM, scalar 8 or 16 rows per thread
+ * at 4 or 8 blocks per SM}; keeps the fastest in the context's config and
+ * returns it.  A candidate within 1 % of the fastest time (a tie on a
+ * link-bound plan) wins if its fused-kernel time is lower.  Section 8.1 sweeps
+ * Exchange's packet size the same way (fixed per-copy overhead against
+ * pipeline depth).  Results do not depend on the configuration, only the time
+ * does. */
 vx_status vx_autotune(vx_ctx *ctx, const vx_plan *plan, uint64_t sample_rows, vx_config *best);
 
 /* Frees the dimension hash tables that vx_run_plan keeps resident on the
