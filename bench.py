@@ -890,6 +890,16 @@ def run_ours(args):
             rf["launch_ceiling"] = {"kernel": "stream_read_kernel (vx_probe_stream)", "achieved": round(ceil_gbs, 1),
                                     "frac": round(ceil_gbs / hbm_peak, 4),
                                     "fused_of_ceiling": round(rf["achieved"] / ceil_gbs, 4)}
+            # the same read while a chunk-sized host-to-device copy streams in,
+            # as the fused kernel runs inside the pipeline
+            try:
+                cc = vx.vx_probe_stream_copying(ctx, rf["algorithmic_bytes_per_launch"], 15, 256 << 20)
+                rf["launch_ceiling"]["under_copy"] = {"kernel": "stream_read_kernel (vx_probe_stream_copying)",
+                                                      "copy_bytes": 256 << 20, "achieved": round(cc, 1),
+                                                      "frac": round(cc / hbm_peak, 4),
+                                                      "fused_of_ceiling": round(rf["achieved"] / cc, 4)}
+            except vx.VxError:
+                pass
     roofline = roofline_learned if use_learned and roofline_learned["achieved"] else roofline_plain
     roofline["form"] = "learned" if roofline is roofline_learned else "plain"
     # the step as a whole is bound by the host link: its roofline rides along
@@ -997,6 +1007,8 @@ def summarize(line):
            "star_step_roofline_frac": {k: f[k]["step_roofline"]["frac"] for k in ("plain", "learned")},
            "fused_kernel_hbm_frac": line["roofline"].get("frac"),
            "fused_kernel_of_launch_ceiling": (line["roofline"].get("launch_ceiling") or {}).get("fused_of_ceiling"),
+           "fused_kernel_of_ceiling_under_copy": ((line["roofline"].get("launch_ceiling") or {}).get("under_copy")
+                                                  or {}).get("fused_of_ceiling"),
            "copy_engine_busy": line.get("copy_engine_busy")}
     g = line.get("roofline_zero_copy_gather")
     if g:

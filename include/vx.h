@@ -691,6 +691,16 @@ vx_status vx_probe_hbm_random(vx_ctx *ctx, uint64_t table_bytes, uint64_t n_read
  * VX_E_INVAL for bytes < 16, reps < 1 or a null output. */
 vx_status vx_probe_stream(vx_ctx *ctx, uint64_t bytes, int32_t reps, double *gbs);
 
+/* The same read with a host-to-device copy in flight: in each round a copy of
+ * copy_bytes from pinned host memory into a second arena buffer is issued on
+ * the context's host-to-device stream (a 4 MiB lead copy, then the rest), and
+ * the read starts on the compute stream once the lead has landed, so it runs
+ * while the rest streams in, as a chunk's kernel runs while the executor
+ * copies the next chunk.  The paper has no counterpart: it is the in-pipeline
+ * ceiling of the fused chunk kernel.  VX_E_NOMEM if bytes + copy_bytes do not
+ * fit the arena; VX_E_INVAL for copy_bytes < 16 and as vx_probe_stream. */
+vx_status vx_probe_stream_copying(vx_ctx *ctx, uint64_t bytes, int32_t reps, uint64_t copy_bytes, double *gbs);
+
 #ifdef __cplusplus
 }
 #endif

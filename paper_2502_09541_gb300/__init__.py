@@ -194,6 +194,7 @@ SIGNATURES = {
     "vx_probe_stream": ([_vp, _u64, _i32, _P(_dbl)], _i32),
     "vx_probe_zero_copy": ([_vp, _u64, _vp, _i32, _vp, _vp, _vp], _i32),
     "vx_probe_zero_copy_gather": ([_vp, _u64, _u32, _u64, _P(_dbl), _P(_dbl), _P(_u64)], _i32),
+    "vx_probe_stream_copying": ([_vp, _u64, _i32, _u64, _P(_dbl)], _i32),
     "vx_sort": ([_vp, _i32, _i32, _vp, _vp, _P(vx_sort_opts), _P(vx_sort_stats)], _i32),
     "vx_radix_sort_pairs": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "vx_range_partition": ([_vp, _vp, _vp, _u64, _vp, _u32, _vp, _vp, _vp], _i32),
@@ -506,6 +507,13 @@ def vx_probe_stream(ctx, nbytes: int, reps: int) -> float:
     copy (median of reps launches)."""
     r = _dbl()
     _check(load().vx_probe_stream(ctx, nbytes, reps, ctypes.byref(r)))
+    return r.value
+
+
+def vx_probe_stream_copying(ctx, nbytes: int, reps: int, copy_bytes: int) -> float:
+    """GB/s of the same read with a host-to-device copy of copy_bytes in flight."""
+    r = _dbl()
+    _check(load().vx_probe_stream_copying(ctx, nbytes, reps, copy_bytes, ctypes.byref(r)))
     return r.value
 
 

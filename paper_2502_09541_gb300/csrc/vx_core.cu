@@ -689,37 +689,57 @@ __global__ void __launch_bounds__(256) stream_read_kernel(const int4 *__restrict
 }
 }  // namespace
 
-VX_API vx_status vx_probe_stream(vx_ctx *ctx, uint64_t bytes, int32_t reps, double *gbs) {
+// one coalesced read of `bytes` right after their host-to-device copy, timed
+// with events on the compute stream (median of reps launches after one
+// warm-up); with copy_bytes > 0 a copy of copy_bytes from pinned host memory
+// into another device buffer is in flight on the host-to-device stream while
+// the read runs, as the next chunk's copy is while a chunk's kernel runs
+static vx_status probe_stream(vx_ctx *ctx, uint64_t bytes, int32_t reps, uint64_t copy_bytes, double *gbs,
+                              const char *who) {
   clear_error();
   VX_TRY(check_ctx(ctx));
   if (bytes < 16 || reps < 1 || !gbs) {
-    set_error("vx_probe_stream: need bytes >= 16, reps >= 1 and an output");
+    set_error("%s: need bytes >= 16, reps >= 1 and an output", who);
     return VX_E_INVAL;
   }
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
   const uint64_t n16 = bytes / 16;
   bytes = n16 * 16;
-  DevBuf db;
-  db.arena = &ctx->arena;
+  const uint64_t lead = copy_bytes ? std::min<uint64_t>(copy_bytes, 4ull << 20) : 0;  // starts the copy engine
+  DevBuf db, cb;
+  db.arena = cb.arena = &ctx->arena;
   db.p = ctx->arena.alloc(bytes + 256);
-  if (!db.p) {
-    set_error("vx_probe_stream: %llu bytes do not fit the arena", (unsigned long long)bytes);
+  if (copy_bytes) cb.p = ctx->arena.alloc(copy_bytes);
+  if (!db.p || (copy_bytes && !cb.p)) {
+    set_error("%s: %llu + %llu bytes do not fit the arena", who, (unsigned long long)bytes,
+              (unsigned long long)copy_bytes);
     return VX_E_NOMEM;
   }
   unsigned long long *sink = (unsigned long long *)(db.as<char>() + bytes);
   char *hs = nullptr;
-  VX_CUDA_TRY(cudaHostAlloc((void **)&hs, bytes, cudaHostAllocDefault));
-  memset(hs, 3, bytes);
-  cudaStream_t s = ctx->s_compute;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  VX_CUDA_TRY(cudaHostAlloc((void **)&hs, std::max(bytes, copy_bytes), cudaHostAllocDefault));
+  memset(hs, 3, std::max(bytes, copy_bytes));
+  cudaStream_t s = ctx->s_compute, sc = ctx->s_h2d;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, ec = nullptr;
   std::vector<float> t;
   cudaError_t ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ec, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(sink, 0, 8, s);
   const uint64_t grid = (n16 + 1023) / 1024;
   for (int it = 0; ce == cudaSuccess && it <= reps; ++it) {  // the first launch warms up
     // the bytes arrive by copy engine first, as a staged chunk does
     ce = cudaMemcpyAsync(db.p, hs, bytes, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess && copy_bytes) {
+      // a short lead copy, then the long one: the read starts once the lead
+      // has landed, with the long copy streaming behind it
+      ce = cudaMemcpyAsync(cb.p, hs, lead, cudaMemcpyHostToDevice, sc);
+      if (ce == cudaSuccess) ce = cudaEventRecord(ec, sc);
+      if (ce == cudaSuccess && copy_bytes > lead)
+        ce = cudaMemcpyAsync(cb.as<char>() + lead, hs + lead, copy_bytes - lead, cudaMemcpyHostToDevice, sc);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ec, 0);
+    }
     if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
     if (ce == cudaSuccess) {
       stream_read_kernel<<<(unsigned)std::min<uint64_t>(grid, 1u << 30), 256, 0, s>>>(db.as<int4>(), n16, sink);
@@ -727,18 +747,34 @@ VX_API vx_status vx_probe_stream(vx_ctx *ctx, uint64_t bytes, int32_t reps, doub
     }
     if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
     if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess && copy_bytes) ce = cudaStreamSynchronize(sc);
     float ms = 0;
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
     if (ce == cudaSuccess && it) t.push_back(ms);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  if (ec) cudaEventDestroy(ec);
   cudaFreeHost(hs);
   VX_CUDA_TRY(ce);
   std::sort(t.begin(), t.end());
   const float med = t[t.size() / 2];
   *gbs = med > 0 ? (double)bytes / (med * 1e6) : 0.0;
   return VX_OK;
+}
+
+VX_API vx_status vx_probe_stream(vx_ctx *ctx, uint64_t bytes, int32_t reps, double *gbs) {
+  return probe_stream(ctx, bytes, reps, 0, gbs, "vx_probe_stream");
+}
+
+VX_API vx_status vx_probe_stream_copying(vx_ctx *ctx, uint64_t bytes, int32_t reps, uint64_t copy_bytes,
+                                         double *gbs) {
+  if (copy_bytes < 16) {
+    clear_error();
+    set_error("vx_probe_stream_copying: need copy_bytes >= 16");
+    return VX_E_INVAL;
+  }
+  return probe_stream(ctx, bytes, reps, copy_bytes, gbs, "vx_probe_stream_copying");
 }
 
 // ------------------------------------------------------------------ link probe

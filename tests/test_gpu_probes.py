@@ -74,3 +74,13 @@ def test_zero_copy_gather_probe(ctx):
     for bad in ((0, 10), (11 << 20, 0), (1 << 40, 10)):
         with pytest.raises(vx.VxError):
             vx.vx_probe_zero_copy_gather(ctx, *bad)
+
+
+def test_stream_probe_under_copy(ctx):
+    # the read of a 64 MiB chunk's staged bytes with a 256 MiB copy streaming in
+    a = vx.vx_probe_stream_copying(ctx, 45 << 20, 5, 256 << 20)
+    assert 100.0 < a < 20000.0
+    with pytest.raises(vx.VxError):
+        vx.vx_probe_stream_copying(ctx, 45 << 20, 3, 0)
+    with pytest.raises(vx.VxError):
+        vx.vx_probe_stream_copying(ctx, 45 << 20, 3, 2 << 30)
