@@ -160,6 +160,78 @@ struct RjJoinParams {
   unsigned int *heavy_n;
 };
 
+// Calls f(c, idx) for every tuple of group g in the chunks of one side, with
+// the warp's lanes spread over the group's tuples in all chunks at once rather
+// than chunk after chunk: lane c of each batch of 32 chunks loads chunk c's
+// boundaries (one round of loads for the batch), a warp scan turns the
+// segments' lengths into offsets, and tuple i of the batch goes to lane
+// i mod 32, which finds its chunk by a binary search over the scan (five
+// shuffles).  Every lane must call it (warp collectives); f runs only for real
+// tuples.
+template <class F>
+__device__ __forceinline__ void rj_for_group_tuples(const uint32_t *bnd, const uint64_t *base, uint32_t nchunks,
+                                                    uint64_t ng1, uint64_t g, uint32_t lane, F &&f) {
+  for (uint32_t c0 = 0; c0 < nchunks; c0 += 32) {
+    const uint32_t c = c0 + lane;
+    uint32_t m = 0;
+    uint64_t at = 0;
+    if (c < nchunks) {
+      const uint32_t *bd = bnd + (uint64_t)c * ng1;
+      const uint32_t lo = bd[g];
+      m = bd[g + 1] - lo;
+      at = base[c] + (lo - bd[0]);
+    }
+    uint32_t incl = m;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= (uint32_t)off) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      uint32_t k = 0;  // lanes whose inclusive count is <= i: the chunk of tuple i
+#pragma unroll
+      for (uint32_t step = 16; step > 0; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, incl, (int)(k + step - 1));
+        if (v <= i) k += step;
+      }
+      k = k < 31 ? k : 31;
+      const uint32_t mk = __shfl_sync(0xffffffffu, m, (int)k), ik = __shfl_sync(0xffffffffu, incl, (int)k);
+      const uint64_t ak = __shfl_sync(0xffffffffu, at, (int)k);
+      if (i < total) f(c0 + k, ak + (i - (ik - mk)));
+    }
+  }
+}
+
+// the build tuples of group g into the warp's shared-memory table of cap
+// slots, the lanes spread over the group's tuples of every chunk
+__device__ __forceinline__ void rj_build_group_warp(const RjJoinParams &p, uint64_t g, uint32_t cap, uint32_t lane,
+                                                    unsigned long long *tkey, unsigned long long *tpay,
+                                                    unsigned long long *sent) {
+  rj_for_group_tuples(p.abnd, p.abase, p.na, (uint64_t)p.ng + 1, g, lane, [&](uint32_t, uint64_t idx) {
+    const uint64_t k = p.akeys[idx], pay = p.apay[idx];
+    if (k == kRjEmpty) {
+      if (atomicExch(&sent[0], 1ull)) atomicOr(&p.acc->err, ERR_DUPKEY);
+      sent[1] = pay;
+      return;
+    }
+    uint32_t h = (uint32_t)(rj_mix(k >> p.key_shift) & (cap - 1));
+    for (uint32_t step = 0; step < cap; ++step) {
+      const unsigned long long old = atomicCAS(&tkey[h], kRjEmpty, k);
+      if (old == kRjEmpty) {
+        tpay[h] = pay;
+        break;
+      }
+      if (old == k) {
+        atomicOr(&p.acc->err, ERR_DUPKEY);
+        break;
+      }
+      h = (h + 1) & (cap - 1);
+    }
+  });
+}
+
 // the build tuples of group g into an open-addressing table of cap slots in
 // shared memory (threads t = 0, stride of them cooperate); a build key equal
 // to the empty marker goes to sent[0..1]
@@ -267,23 +339,19 @@ __global__ void __launch_bounds__(32 * kRjWarps) rj_join_kernel(const RjJoinPara
       for (uint32_t i = lane; i < cap; i += 32) tkey[w][i] = kRjEmpty;
       if (lane == 0) sent[w][0] = 0;
       __syncwarp();
-      rj_build_group(p, g, cap, lane, 32, tkey[w], tpay[w], sent[w]);
+      rj_build_group_warp(p, g, cap, lane, tkey[w], tpay[w], sent[w]);
       __syncwarp();
     }
-    for (uint32_t c = 0; c < p.nb; ++c) {  // lanes stripe each chunk's probe tuples of the group
-      const uint32_t *bd = p.bbnd + (uint64_t)c * (p.ng + 1);
-      const uint64_t at = p.bbase[c] + (bd[g] - bd[0]);
-      const uint32_t m = bd[g + 1] - bd[g];
-      for (uint32_t i = lane; i < m; i += 32) {
-        uint64_t pay = 0;
-        if (rj_probe_one(p, g, p.bkeys[at + i], in_smem, cap, tkey[w], tpay[w], sent[w], pay)) {
-          const uint64_t row = (uint64_t)c * p.probe_chunk_rows + p.brows[at + i];
-          cnt += 1;
-          psum += pay;
-          fp += rj_mix(row ^ ((pay << 17) | (pay >> 47)));
-        }
+    // the lanes spread over the group's probe tuples of every chunk
+    rj_for_group_tuples(p.bbnd, p.bbase, p.nb, (uint64_t)p.ng + 1, g, lane, [&](uint32_t c, uint64_t idx) {
+      uint64_t pay = 0;
+      if (rj_probe_one(p, g, p.bkeys[idx], in_smem, cap, tkey[w], tpay[w], sent[w], pay)) {
+        const uint64_t row = (uint64_t)c * p.probe_chunk_rows + p.brows[idx];
+        cnt += 1;
+        psum += pay;
+        fp += rj_mix(row ^ ((pay << 17) | (pay >> 47)));
       }
-    }
+    });
     __syncwarp();
   }
   for (int off = 16; off > 0; off >>= 1) {
