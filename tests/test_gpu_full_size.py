@@ -8,7 +8,8 @@ output and scratch fit the host's memory).
 The star join is compared with the oracle over the whole 600M-row table
 for two templates (the oracle's row-range threads use every host core), and
 on a ragged 20M-row range under every materialization policy; per-group
-additivity over disjoint row ranges covers three more.  The join and the sort
+additivity over disjoint row ranges covers three more, and every other kernel
+shape must give the plain form's groups over the whole table.  The join and the sort
 are too large for the oracle to rescan in a test, so they are checked by
 properties that hold at any size: the join count and payload sum the
 generator records while drawing the probe keys, and a sort output that is
@@ -122,6 +123,27 @@ def test_star_full_table_batched_form_equals_plain(star_full):
         cfg.chunk_bytes = 64 << 20
         cfg.n_slots = 3
         vx.vx_set_config(c, cfg)
+
+
+@pytest.mark.parametrize("rows,bps", [(2, 4), (2, 6), (8, 4), (16, 8)])
+def test_star_full_table_kernel_shapes_equal_plain(star_full, rows, bps):
+    """The other launch shapes the autotuner may pick (the bulk-copy pipeline,
+    the scalar kernel) over the whole table give the plain form's groups, which
+    the test above compares with the oracle."""
+    c, fact, dims, fid, did = star_full
+    for name in ("T2_1", "T3_1"):
+        T = G.star_templates()[name]
+        plain = _dense(*_run(c, T, fid, did)[:3])
+        cfg = vx.vx_get_config(c)
+        saved = (cfg.kernel_rows, cfg.blocks_per_sm)
+        cfg.kernel_rows, cfg.blocks_per_sm = rows, bps
+        vx.vx_set_config(c, cfg)
+        try:
+            got = _dense(*_run(c, T, fid, did)[:3])
+        finally:
+            cfg.kernel_rows, cfg.blocks_per_sm = saved
+            vx.vx_set_config(c, cfg)
+        assert np.array_equal(got[0], plain[0]) and np.array_equal(got[1], plain[1]), name
 
 
 def test_join_full_size_matches_generator_truth():
