@@ -517,10 +517,11 @@ def run_sort_extra(vx, G, args):
         o.host_scratch_bytes = scratch.nbytes
         vx.vx_sort(ctx, kc, rc, ok, orr, o)  # warm-up: first pass over freshly pinned host pages
 
-        def form(part, plan):
+        def form(part, plan, runs_mode=0):
             o = vx.vx_sort_opts()
             o.partitioner = part
             o.plan = plan
+            o.runs_mode = runs_mode
             o.host_scratch = scratch.ctypes.data
             o.host_scratch_bytes = scratch.nbytes
             o.sample_size = 1 << 20
@@ -538,8 +539,8 @@ def run_sort_extra(vx, G, args):
                  "out_of_region_pairs": st["out_of_region_pairs"],
                  "link_gbs": round((st["bytes_h2d"] + st["bytes_d2h"]) / st["ms_total"] / 1e6, 1)}
             if plan == vx.VX_SORT_MERGE:  # pass 1 sorts runs, pass 2 merges: no sample, exact cuts
-                d.update({"runs": st["n_runs"], "ms_cut": round(st["ms_sample"], 2),
-                          "ms_merge_kernel": round(st["ms_merge_kernel"], 1)})
+                d.update({"runs": st["n_runs"], "natural_runs": bool(st["natural_runs"]),
+                          "ms_cut": round(st["ms_sample"], 2), "ms_merge_kernel": round(st["ms_merge_kernel"], 1)})
                 if st["ms_merge_kernel"] > 0:
                     hbm_peak, _ = measured_peaks()
                     ach = 24 * st["merge_pass_pairs"] / (st["ms_merge_kernel"] * 1e6)
@@ -573,7 +574,9 @@ def run_sort_extra(vx, G, args):
         vx.vx_sort(ctx, kc, rc, ok, orr, vx.vx_sort_opts())  # first pass over the rewritten pages
         out["presorted_runs"] = {"plain_sample": form(vx.VX_PART_SAMPLE, vx.VX_SORT_PARTITION)[0],
                                  "learned_pl": form(vx.VX_PART_LEARNED_PL, vx.VX_SORT_PARTITION)[0],
-                                 "merge_exact": form(vx.VX_PART_SAMPLE, vx.VX_SORT_MERGE)[0]}
+                                 "merge_exact": form(vx.VX_PART_SAMPLE, vx.VX_SORT_MERGE)[0],
+                                 # the same plan made to sort its chunks into runs first
+                                 "merge_sorted_chunks": form(vx.VX_PART_SAMPLE, vx.VX_SORT_MERGE, 1)[0]}
         out["presorted_runs"]["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
     finally:
         vx.vx_close(ctx)

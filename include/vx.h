@@ -381,7 +381,10 @@ typedef struct {
   uint64_t max_slot_pairs;    /* optional cap on the pairs per staging slot (0 = from the arena) */
   uint64_t *splitters_out;    /* optional: receives the P-1 top-level splitters (PARTITION plan) */
   int32_t plan;               /* VX_SORT_PARTITION (default) or VX_SORT_MERGE */
-  int32_t reserved;
+  int32_t runs_mode;          /* MERGE: 0 = when a sample of adjacent pairs suggests the input is
+                                 made of at most 256 ascending runs, find them (one pass over the
+                                 keys) and merge them as they are, skipping pass 1; 1 = always
+                                 sort the chunks into runs */
 } vx_sort_opts;
 
 typedef struct {
@@ -403,6 +406,9 @@ typedef struct {
   uint32_t n_runs;                 /* MERGE: sorted runs written by pass 1 */
   double ms_merge_kernel;          /* MERGE: device time of the merge rounds (CUDA events) */
   uint64_t merge_pass_pairs;       /* MERGE: pairs x executed merge rounds */
+  uint32_t natural_runs;           /* MERGE: 1 = the input's own ascending runs were merged (n_runs
+                                      of them; pass 1 skipped, ms_partition is the detection) */
+  uint32_t reserved;
 } vx_sort_stats;
 
 /* Out-of-core sort of (uint64 key, uint32 row id) pairs held in two registered
@@ -418,7 +424,9 @@ typedef struct {
  * trained on the device (VX_PART_LEARNED_MLP).  MERGE plan (opts->plan): pass
  * 1 radix-sorts each contiguous chunk into a sorted run of the intermediate;
  * the runs are cut at exact ranks (vx_exact_splits) into equal partitions;
- * pass 2 loads each partition's run segments and merges them (vx_merge_runs).
+ * pass 2 loads each partition's run segments and merges them (vx_merge_runs);
+ * an input already made of at most 256 ascending runs is merged as it is
+ * (opts->runs_mode).
  * Both plans and any splitters give the same output; they decide only where
  * to cut.  The intermediate is opts->host_scratch when it holds 12 n bytes,
  * else allocated for the call. */

@@ -99,7 +99,7 @@ class vx_sort_opts(ctypes.Structure):
                 ("sample_size", ctypes.c_uint64), ("mlp_steps", ctypes.c_uint32), ("region_slack_pct", ctypes.c_uint32),
                 ("host_scratch", ctypes.c_void_p), ("host_scratch_bytes", ctypes.c_uint64),
                 ("max_slot_pairs", ctypes.c_uint64), ("splitters_out", ctypes.c_void_p), ("plan", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("runs_mode", ctypes.c_int32)]
 
 
 class vx_sort_stats(ctypes.Structure):
@@ -112,7 +112,8 @@ class vx_sort_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("ms_sort_kernel", ctypes.c_double),
                 ("radix_pass_pairs", ctypes.c_uint64), ("out_of_region_pairs", ctypes.c_uint64),
                 ("spill_buffers", ctypes.c_uint64), ("plan", ctypes.c_uint32), ("n_runs", ctypes.c_uint32),
-                ("ms_merge_kernel", ctypes.c_double), ("merge_pass_pairs", ctypes.c_uint64)]
+                ("ms_merge_kernel", ctypes.c_double), ("merge_pass_pairs", ctypes.c_uint64),
+                ("natural_runs", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

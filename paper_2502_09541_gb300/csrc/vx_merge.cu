@@ -51,6 +51,30 @@ __global__ void run_fences_kernel(const uint64_t *k0, const uint64_t *k1, const 
     fences[j] = k[j * kFenceStride];
 }
 
+// ------------------------------------------------------------------ natural runs
+// Descents of one staged chunk of keys (chunk rows row0 .. row0 + m): every i
+// in [1, m) with k[i] < k[i - 1] starts an ascending run of the input; up to
+// cap of their global rows go to pos (in no particular order), all of them are
+// counted in *cnt.  A chunk's first row is compared on the host.
+__global__ void descent_kernel(const uint64_t *__restrict__ k, uint64_t m, uint64_t row0, unsigned long long *cnt,
+                               uint64_t *pos, uint32_t cap) {
+  for (uint64_t i = 1 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    if (k[i] < k[i - 1]) {
+      const unsigned long long j = atomicAdd(cnt, 1ull);
+      if (j < cap) pos[j] = row0 + i;
+    }
+}
+
+// fences of ascending runs of the input read through mapped host memory:
+// run r = blockIdx.y, fence j of it = key run_off[r] + j * kFenceStride
+__global__ void natural_fences_kernel(const uint64_t *keys, const uint64_t *run_off, const uint64_t *fence_start,
+                                      uint64_t *fences) {
+  const uint32_t r = blockIdx.y;
+  const uint64_t len = run_off[r + 1] - run_off[r], nf = (len + kFenceStride - 1) / kFenceStride;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nf; j += (uint64_t)gridDim.x * blockDim.x)
+    fences[fence_start[r] + j] = keys[run_off[r] + j * kFenceStride];
+}
+
 // ------------------------------------------------------------------ exact cuts
 struct SplitParams {
   const uint64_t *keys;         // run r at keys + run_off[r] (mapped host memory or HBM)
@@ -339,6 +363,97 @@ struct RunPass : ExKernel {
   }
 };
 
+// ------------------------------------------------------------------ run detection
+// Streams the keys through the device chunk by chunk and records where the
+// input's ascending runs start (descent_kernel); nothing comes back but the
+// positions.
+struct RunDetectPass : ExKernel {
+  const uint64_t *keys;
+  uint64_t n, R;
+  unsigned long long *d_cnt;
+  uint64_t *d_pos;
+  uint32_t cap;
+  int num_sms;
+
+  uint64_t size() override { return (n + R - 1) / R; }
+  uint64_t rows(uint64_t it) const { return std::min(R, n - it * R); }
+  uint64_t slot_bytes() override { return (8 * R + 255) & ~255ull; }
+  void inputs(uint64_t it, char *slot, std::vector<CopyOp> &h2d) override {
+    h2d.push_back({keys + it * R, slot, 8 * rows(it)});
+  }
+  vx_status kernel(char *slot, uint64_t it, cudaStream_t s) override {
+    const uint64_t m = rows(it);
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((m + 255) / 256, (uint64_t)num_sms * 8));
+    descent_kernel<<<(unsigned)grid, 256, 0, s>>>((const uint64_t *)slot, m, it * R, d_cnt, d_pos, cap);
+    VX_CUDA_TRY(cudaGetLastError());
+    return VX_OK;
+  }
+};
+
+// Starts of the input's ascending runs when there are at most kMaxRuns of
+// them (*found = true; starts[0] = 0), after a host-side sample of adjacent
+// pairs has suggested so; else *found = false (and the detection pass did not
+// run, or counted too many descents).
+vx_status natural_runs(vx_ctx *ctx, const uint64_t *keys, uint64_t n, uint64_t max_rows,
+                       std::vector<uint64_t> *starts, bool *found, uint64_t *bytes_h2d) {
+  *found = false;
+  starts->assign(1, 0);
+  if (n < 2) {
+    *found = true;
+    return VX_OK;
+  }
+  // sample: descents among up to 65,536 adjacent pairs at pseudo-random rows
+  const uint64_t ns = std::min<uint64_t>(65536, n - 1);
+  uint64_t desc = 0;
+  for (uint64_t j = 0; j < ns; ++j) {
+    uint64_t z = 0x9E3779B97F4A7C15ull * (j + 1);
+    z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 29;
+    const uint64_t i = 1 + (uint64_t)(((unsigned __int128)z * (n - 1)) >> 64);
+    desc += keys[i] < keys[i - 1];
+  }
+  if ((double)desc * (double)(n - 1) / (double)ns >= (double)kMaxRuns) return VX_OK;
+  const int S = std::max(2, ctx->cfg.n_slots);
+  uint64_t R = (uint64_t)((double)ctx->arena.largest_free() / S * 0.9) / 8;
+  R = std::min<uint64_t>(R, kPipelineRows);
+  if (max_rows) R = std::min<uint64_t>(R, max_rows);
+  if (R < 2) return VX_OK;
+  DevBuf b;
+  b.arena = &ctx->arena;
+  b.p = ctx->arena.alloc(8 * (kMaxRuns + 1));
+  if (!b.p) return VX_OK;
+  unsigned long long *d_cnt = b.as<unsigned long long>();
+  uint64_t *d_pos = b.as<uint64_t>() + 1;
+  VX_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 8, ctx->s_compute));
+  RunDetectPass dp;
+  dp.keys = keys;
+  dp.n = n;
+  dp.R = R;
+  dp.d_cnt = d_cnt;
+  dp.d_pos = d_pos;
+  dp.cap = kMaxRuns;
+  dp.num_sms = ctx->num_sms;
+  ExecStats es;
+  VX_TRY(run_pipeline(ctx, dp, &es));
+  *bytes_h2d += es.bytes_h2d;
+  uint64_t cnt = 0;
+  VX_CUDA_TRY(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, ctx->s_compute));
+  VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  std::vector<uint64_t> pos(std::min<uint64_t>(cnt, kMaxRuns));
+  if (!pos.empty()) {
+    VX_CUDA_TRY(cudaMemcpyAsync(pos.data(), d_pos, 8 * pos.size(), cudaMemcpyDeviceToHost, ctx->s_compute));
+    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+  }
+  // the chunks' first rows against the rows before them
+  for (uint64_t c = R; c < n; c += R)
+    if (keys[c] < keys[c - 1]) ++cnt, pos.push_back(c);
+  if (cnt + 1 > kMaxRuns) return VX_OK;
+  std::sort(pos.begin(), pos.end());
+  starts->insert(starts->end(), pos.begin(), pos.end());
+  *found = true;
+  return VX_OK;
+}
+
 // ------------------------------------------------------------------ pass 2: merge partitions
 struct MergePass : ExKernel {
   vx_ctx *ctx;
@@ -470,84 +585,141 @@ vx_status exact_cuts(vx_ctx *ctx, const uint64_t *keys, const std::vector<uint64
 
 }  // namespace
 
-// The merge plan of vx_sort.
-vx_status merge_sort_plan(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, uint64_t n, uint64_t *out_keys,
-                          uint32_t *out_vals, const vx_sort_opts &o, vx_sort_stats &ss) {
+// The merge plan of vx_sort.  When a sample of adjacent pairs suggests the
+// input is already made of few ascending runs, a detection pass finds them
+// (at most kMaxRuns) and they serve as the sorted runs directly: pass 1 and its
+// intermediate are skipped, and the merge pass loads the runs' segments from
+// the input itself.
+vx_status merge_sort_plan(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, const uint64_t *dev_keys,
+                          uint64_t n, uint64_t *out_keys, uint32_t *out_vals, const vx_sort_opts &o,
+                          vx_sort_stats &ss) {
   const int S = std::max(2, ctx->cfg.n_slots);
   ss.plan = VX_SORT_MERGE;
   if (n == 0) return VX_OK;
-  const uint64_t avail = ctx->arena.largest_free();
-  // pass 1 runs: kPipelineRows pairs, fewer if S slots of them do not fit
-  uint64_t cap1 = (uint64_t)((double)avail / (S * (24.0 + 256.0 * 8 / kRxTile)) * 0.9);
-  cap1 = cap1 / kRxTile * kRxTile;
-  if (o.max_slot_pairs) cap1 = std::min<uint64_t>(cap1, o.max_slot_pairs / kRxTile * kRxTile);
-  const uint64_t R = std::min<uint64_t>(cap1, kPipelineRows);
-  if (R < kRxTile) {
-    set_error("vx_sort: arena of %llu bytes too small", (unsigned long long)ctx->arena.capacity());
-    return VX_E_NOMEM;
-  }
-  const uint64_t N64 = (n + R - 1) / R;
-  if (N64 > kMaxRuns) {
-    set_error("vx_sort (merge plan): %llu runs; at most %u", (unsigned long long)N64, kMaxRuns);
-    return VX_E_UNSUPPORTED;
-  }
-  const uint32_t N = (uint32_t)N64;
-
-  // ---- host intermediate for the sorted runs: keys (8 n bytes), then values
-  uint64_t *mid_keys = nullptr;
-  uint32_t *mid_vals = nullptr;
-  std::unique_ptr<char[]> own;
-  HostReg reg_mid;
-  if (o.host_scratch && o.host_scratch_bytes >= 12 * n) {
-    mid_keys = (uint64_t *)o.host_scratch;
-    mid_vals = (uint32_t *)((char *)o.host_scratch + 8 * n);
-    VX_TRY(reg_mid.add(o.host_scratch, 12 * n));
-  } else {
-    own.reset(new (std::nothrow) char[12 * n + 4096]);
-    if (!own) {
-      set_error("vx_sort: no host memory for the %llu-pair intermediate", (unsigned long long)n);
-      return VX_E_NOMEM;
-    }
-    char *base = (char *)(((uintptr_t)own.get() + 4095) & ~(uintptr_t)4095);
-    mid_keys = (uint64_t *)base;
-    mid_vals = (uint32_t *)(base + 8 * n);
-    VX_TRY(reg_mid.add(base, 12 * n));
-  }
-  void *dev_mid = nullptr;
-  VX_CUDA_TRY(cudaHostGetDevicePointer(&dev_mid, mid_keys, 0));
-
-  // ---- pass 1: sorted runs and their fences
-  const uint64_t fpr = (R + kFenceStride - 1) / kFenceStride;
+  std::vector<uint64_t> run_off, fence_start;
   DevBuf fb;
   fb.arena = &ctx->arena;
-  fb.p = ctx->arena.alloc(8 * fpr * N);
-  if (!fb.p) {
-    set_error("vx_sort: fences do not fit the arena");
-    return VX_E_NOMEM;
+  const uint64_t *run_keys = nullptr, *run_keys_dev = nullptr;
+  const uint32_t *run_vals = nullptr;
+  uint32_t N = 0;
+  std::unique_ptr<char[]> own;
+  HostReg reg_mid;
+
+  // ---- natural runs of the input
+  bool nat = false;
+  if (o.runs_mode == 0 && dev_keys) {
+    const double td = now_ms();
+    std::vector<uint64_t> starts;
+    VX_TRY(natural_runs(ctx, keys, n, o.max_slot_pairs, &starts, &nat, &ss.bytes_h2d));
+    if (nat) {
+      N = (uint32_t)starts.size();
+      run_off = starts;
+      run_off.push_back(n);
+      fence_start.assign(N, 0);
+      uint64_t nf = 0, mx_nf = 0;
+      for (uint32_t r = 0; r < N; ++r) {
+        fence_start[r] = nf;
+        const uint64_t f = (run_off[r + 1] - run_off[r] + kFenceStride - 1) / kFenceStride;
+        nf += f;
+        mx_nf = std::max(mx_nf, f);
+      }
+      fb.p = ctx->arena.alloc(8 * (nf + 2 * (uint64_t)N + 1));
+      if (!fb.p) {
+        set_error("vx_sort: fences do not fit the arena");
+        return VX_E_NOMEM;
+      }
+      uint64_t *d_fences = fb.as<uint64_t>(), *d_off = d_fences + nf, *d_fs = d_off + N + 1;
+      VX_CUDA_TRY(cudaMemcpyAsync(d_off, run_off.data(), 8 * (N + 1), cudaMemcpyHostToDevice, ctx->s_compute));
+      VX_CUDA_TRY(cudaMemcpyAsync(d_fs, fence_start.data(), 8 * N, cudaMemcpyHostToDevice, ctx->s_compute));
+      const dim3 grid((unsigned)std::max<uint64_t>(1, std::min<uint64_t>((mx_nf + 255) / 256, 256)), N);
+      natural_fences_kernel<<<grid, 256, 0, ctx->s_compute>>>(dev_keys, d_off, d_fs, d_fences);
+      VX_CUDA_TRY(cudaGetLastError());
+      VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+      run_keys = keys;
+      run_vals = vals;
+      run_keys_dev = dev_keys;
+      ss.natural_runs = 1;
+    }
+    ss.ms_partition += now_ms() - td;
   }
-  double t0 = now_ms();
-  {
-    RunPass rp;
-    rp.ctx = ctx;
-    rp.keys = keys;
-    rp.vals = vals;
-    rp.n = n;
-    rp.R = R;
-    rp.mid_keys = mid_keys;
-    rp.mid_vals = mid_vals;
-    rp.d_fences = fb.as<uint64_t>();
-    rp.fences_per_run = fpr;
-    rp.S = S;
-    ExecStats es;
-    VX_TRY(run_pipeline(ctx, rp, &es));
-    VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
-    ss.bytes_h2d += es.bytes_h2d;
-    ss.bytes_d2h += es.bytes_d2h;
-    ss.kernel_launches += es.kernel_launches * 37;  // radix sort (35), fences, publish
-    ss.ms_sort_kernel += es.ms_kernel;
-    ss.radix_pass_pairs += rp.pass_pairs;
+
+  if (!nat) {
+    const uint64_t avail = ctx->arena.largest_free();
+    // pass 1 runs: kPipelineRows pairs, fewer if S slots of them do not fit
+    uint64_t cap1 = (uint64_t)((double)avail / (S * (24.0 + 256.0 * 8 / kRxTile)) * 0.9);
+    cap1 = cap1 / kRxTile * kRxTile;
+    if (o.max_slot_pairs) cap1 = std::min<uint64_t>(cap1, o.max_slot_pairs / kRxTile * kRxTile);
+    const uint64_t R = std::min<uint64_t>(cap1, kPipelineRows);
+    if (R < kRxTile) {
+      set_error("vx_sort: arena of %llu bytes too small", (unsigned long long)ctx->arena.capacity());
+      return VX_E_NOMEM;
+    }
+    const uint64_t N64 = (n + R - 1) / R;
+    if (N64 > kMaxRuns) {
+      set_error("vx_sort (merge plan): %llu runs; at most %u", (unsigned long long)N64, kMaxRuns);
+      return VX_E_UNSUPPORTED;
+    }
+    N = (uint32_t)N64;
+
+    // ---- host intermediate for the sorted runs: keys (8 n bytes), then values
+    uint64_t *mid_keys = nullptr;
+    uint32_t *mid_vals = nullptr;
+    if (o.host_scratch && o.host_scratch_bytes >= 12 * n) {
+      mid_keys = (uint64_t *)o.host_scratch;
+      mid_vals = (uint32_t *)((char *)o.host_scratch + 8 * n);
+      VX_TRY(reg_mid.add(o.host_scratch, 12 * n));
+    } else {
+      own.reset(new (std::nothrow) char[12 * n + 4096]);
+      if (!own) {
+        set_error("vx_sort: no host memory for the %llu-pair intermediate", (unsigned long long)n);
+        return VX_E_NOMEM;
+      }
+      char *base = (char *)(((uintptr_t)own.get() + 4095) & ~(uintptr_t)4095);
+      mid_keys = (uint64_t *)base;
+      mid_vals = (uint32_t *)(base + 8 * n);
+      VX_TRY(reg_mid.add(base, 12 * n));
+    }
+    void *dev_mid = nullptr;
+    VX_CUDA_TRY(cudaHostGetDevicePointer(&dev_mid, mid_keys, 0));
+
+    // ---- pass 1: sorted runs and their fences
+    const uint64_t fpr = (R + kFenceStride - 1) / kFenceStride;
+    fb.p = ctx->arena.alloc(8 * fpr * N);
+    if (!fb.p) {
+      set_error("vx_sort: fences do not fit the arena");
+      return VX_E_NOMEM;
+    }
+    double t0 = now_ms();
+    {
+      RunPass rp;
+      rp.ctx = ctx;
+      rp.keys = keys;
+      rp.vals = vals;
+      rp.n = n;
+      rp.R = R;
+      rp.mid_keys = mid_keys;
+      rp.mid_vals = mid_vals;
+      rp.d_fences = fb.as<uint64_t>();
+      rp.fences_per_run = fpr;
+      rp.S = S;
+      ExecStats es;
+      VX_TRY(run_pipeline(ctx, rp, &es));
+      VX_CUDA_TRY(cudaStreamSynchronize(ctx->s_compute));
+      ss.bytes_h2d += es.bytes_h2d;
+      ss.bytes_d2h += es.bytes_d2h;
+      ss.kernel_launches += es.kernel_launches * 37;  // radix sort (35), fences, publish
+      ss.ms_sort_kernel += es.ms_kernel;
+      ss.radix_pass_pairs += rp.pass_pairs;
+    }
+    ss.ms_partition += now_ms() - t0;
+    run_off.assign(N + 1, 0);
+    fence_start.assign(N, 0);
+    for (uint32_t r = 0; r <= N; ++r) run_off[r] = std::min<uint64_t>((uint64_t)r * R, n);
+    for (uint32_t r = 0; r < N; ++r) fence_start[r] = (uint64_t)r * fpr;
+    run_keys = mid_keys;
+    run_vals = mid_vals;
+    run_keys_dev = (const uint64_t *)dev_mid;
   }
-  ss.ms_partition += now_ms() - t0;
   ss.n_runs = N;
 
   // ---- partitions: equal shares of the pairs, each within a merge slot;
@@ -563,18 +735,15 @@ vx_status merge_sort_plan(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
               (unsigned long long)((n + P - 1) / P), (unsigned long long)cap2);
     return VX_E_NOMEM;
   }
-  std::vector<uint64_t> run_off(N + 1), fence_start(N);
-  for (uint32_t r = 0; r <= N; ++r) run_off[r] = std::min<uint64_t>((uint64_t)r * R, n);
-  for (uint32_t r = 0; r < N; ++r) fence_start[r] = (uint64_t)r * fpr;
   std::vector<uint64_t> ranks;
   for (uint64_t p = 1; p < P; ++p) ranks.push_back(p * n / P);
   std::vector<uint64_t> inner;
-  VX_TRY(exact_cuts(ctx, (const uint64_t *)dev_mid, run_off, fence_start, fb.as<uint64_t>(), ranks, &inner));
+  VX_TRY(exact_cuts(ctx, run_keys_dev, run_off, fence_start, fb.as<uint64_t>(), ranks, &inner));
   fb.release();
   MergePass mp;
   mp.ctx = ctx;
-  mp.run_keys = mid_keys;
-  mp.run_vals = mid_vals;
+  mp.run_keys = run_keys;
+  mp.run_vals = run_vals;
   mp.run_off = run_off;
   mp.N = N;
   mp.P = (uint32_t)P;

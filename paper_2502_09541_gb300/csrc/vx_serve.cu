@@ -411,7 +411,8 @@ static vx_status run_op(vx_ctx *child, ServeQuery *q) {
     const uint64_t *k = (const uint64_t *)kc->host + rb;
     const uint32_t *v = (const uint32_t *)vc->host + rb;
     vx_status st = r.sort.plan == VX_SORT_MERGE
-                       ? merge_sort_plan(child, k, v, n, r.out_keys, r.out_rowids, r.sort, ss)
+                       ? merge_sort_plan(child, k, v, (const uint64_t *)kc->dev + rb, n, r.out_keys, r.out_rowids,
+                                         r.sort, ss)
                        : sort_contiguous(child, k, v, (const uint64_t *)kc->dev + rb, n, r.out_keys, r.out_rowids,
                                          r.sort, ss, 0);
     ss.ms_total = now_ms() - t0;

@@ -1153,7 +1153,8 @@ VX_API vx_status vx_sort(vx_ctx *ctx, int32_t key_col, int32_t rowid_col, uint64
   vx_sort_opts o{};
   if (opts) o = *opts;
   if (o.partitioner < VX_PART_SAMPLE || o.partitioner > VX_PART_LEARNED_MLP || o.n_partitions < 0 ||
-      o.n_partitions > 256 || (o.plan != VX_SORT_PARTITION && o.plan != VX_SORT_MERGE)) {
+      o.n_partitions > 256 || (o.plan != VX_SORT_PARTITION && o.plan != VX_SORT_MERGE) || o.runs_mode < 0 ||
+      o.runs_mode > 1) {
     set_error("vx_sort: bad options");
     return VX_E_INVAL;
   }
@@ -1164,8 +1165,8 @@ VX_API vx_status vx_sort(vx_ctx *ctx, int32_t key_col, int32_t rowid_col, uint64
   vx_sort_stats ss{};
   double t0 = now_ms();
   vx_status st = o.plan == VX_SORT_MERGE
-                     ? merge_sort_plan(ctx, (const uint64_t *)kc->host, (const uint32_t *)vc->host, n, out_keys,
-                                       out_rowids, o, ss)
+                     ? merge_sort_plan(ctx, (const uint64_t *)kc->host, (const uint32_t *)vc->host,
+                                       (const uint64_t *)kc->dev, n, out_keys, out_rowids, o, ss)
                      : sort_contiguous(ctx, (const uint64_t *)kc->host, (const uint32_t *)vc->host,
                                        (const uint64_t *)kc->dev, n, out_keys, out_rowids, o, ss, 0);
   ss.ms_total = now_ms() - t0;

@@ -47,8 +47,9 @@ vx_status radix_join(vx_ctx *ctx, const Column *bk, const Column *bp, const Colu
                      vx_join_result *out);
 
 // the merge plan of vx_sort (sorted runs, exact cuts, merged partitions)
-vx_status merge_sort_plan(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, uint64_t n, uint64_t *out_keys,
-                          uint32_t *out_vals, const vx_sort_opts &o, vx_sort_stats &ss);
+vx_status merge_sort_plan(vx_ctx *ctx, const uint64_t *keys, const uint32_t *vals, const uint64_t *dev_keys,
+                          uint64_t n, uint64_t *out_keys, uint32_t *out_vals, const vx_sort_opts &o,
+                          vx_sort_stats &ss);
 
 vx_status sample_and_sort(vx_ctx *ctx, const uint64_t *dev_keys, uint64_t n, uint64_t &m, uint64_t seed,
                           DevBuf &sorted_out, uint64_t **sorted_ptr);

@@ -129,3 +129,71 @@ def test_sort_merge_plan_empty_and_tiny():
             vx.vx_close(c)
         ek, er = O.sort_pairs(k, r)
         assert np.array_equal(ok, ek) and np.array_equal(orr, er)
+
+
+def _merge_sort(k, r, budget=40 << 20, **opts):
+    c = vx.vx_open(budget)
+    try:
+        kc = vx.vx_register_host_column(c, "k", k)
+        rc = vx.vx_register_host_column(c, "r", r)
+        ok = np.empty(len(k), np.uint64)
+        orr = np.empty(len(k), np.uint32)
+        o = vx.vx_sort_opts()
+        o.plan = vx.VX_SORT_MERGE
+        for name, v in opts.items():
+            setattr(o, name, v)
+        st = vx.vx_sort(c, kc, rc, ok, orr, o)
+    finally:
+        vx.vx_close(c)
+    return ok, orr, st
+
+
+def test_sort_merge_plan_natural_runs():
+    """An input of 64 presorted runs is merged as it is (pass 1 skipped): the
+    same output as the oracle and as the plan that sorts its chunks first."""
+    n = 3_000_017
+    k, r = G.sort_input(n, "runs", seed=5)
+    ek, er = O.sort_pairs(k, r)
+    ok, orr, st = _merge_sort(k, r)
+    assert np.array_equal(ok, ek) and np.array_equal(orr, er)
+    assert st["natural_runs"] == 1 and 1 < st["n_runs"] <= 64 and st["radix_pass_pairs"] == 0
+    assert st["max_partition"] - st["min_partition"] <= 1
+    ok2, orr2, st2 = _merge_sort(k, r, runs_mode=1)
+    assert np.array_equal(ok2, ek) and np.array_equal(orr2, er) and st2["natural_runs"] == 0
+    # a shuffled input: the sample finds descents, the chunks are sorted
+    ku, ru = G.sort_input(n, "uniform", seed=5)
+    oku, oru, stu = _merge_sort(ku, ru)
+    eku, eru = O.sort_pairs(ku, ru)
+    assert np.array_equal(oku, eku) and np.array_equal(oru, eru) and stu["natural_runs"] == 0
+
+
+def test_sort_merge_plan_natural_runs_ties_and_chunk_edges():
+    """Ascending runs over four key values (equal keys in every run: the merge
+    must keep input order), with run starts on the detection pass's chunk
+    starts (chunks of max_slot_pairs rows) and between them."""
+    n = 1_000_000
+    v = G.i32_uniform(n, 0, 4, 3, 7).astype(np.uint64)
+    starts = sorted({0, 100_000, 200_000, 250_001, 300_000, 777_777, 900_000, 999_999})
+    k = np.empty(n, np.uint64)
+    for a, b in zip(starts, starts[1:] + [n]):
+        k[a:b] = np.sort(v[a:b])
+    r = np.arange(n, dtype=np.uint32)
+    ok, orr, st = _merge_sort(k, r, max_slot_pairs=100_000)
+    ek, er = O.sort_pairs(k, r)
+    assert np.array_equal(ok, ek) and np.array_equal(orr, er)
+    # a run start is a descent unless the run's first key reaches the previous run's last
+    assert st["natural_runs"] == 1 and st["n_runs"] == 1 + int(np.count_nonzero(k[1:] < k[:-1]))
+    assert st["n_runs"] >= len(starts) - 1
+
+
+def test_sort_merge_plan_too_many_runs_sorts_chunks():
+    n = 1_200_000
+    k = np.empty(n, np.uint64)
+    bounds = np.linspace(0, n, 301).astype(np.int64)  # 300 runs: more than the merge takes
+    src = G.u64_uniform(n, 2, 13)
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        k[a:b] = np.sort(src[a:b])
+    r = np.arange(n, dtype=np.uint32)
+    ok, orr, st = _merge_sort(k, r)
+    ek, er = O.sort_pairs(k, r)
+    assert np.array_equal(ok, ek) and np.array_equal(orr, er) and st["natural_runs"] == 0
