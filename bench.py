@@ -568,6 +568,12 @@ def run_sort_extra(vx, G, args):
                                      "achieved": round(ach, 1), "peak": hbm_peak, "frac": round(ach / hbm_peak, 4),
                                      "peak_kind": peak_kind, "pass_pairs": int(st["radix_pass_pairs"]),
                                      "ms_sort_kernel": round(st["ms_sort_kernel"], 1)}
+        # uniform 64-bit keys (every digit pass runs): both plans
+        G.sort_input(n, "uniform", keys=k, rowids=r)
+        vx.vx_sort(ctx, kc, rc, ok, orr, vx.vx_sort_opts())  # first pass over the rewritten pages
+        out["uniform"] = {"plain_sample": form(vx.VX_PART_SAMPLE, vx.VX_SORT_PARTITION)[0],
+                          "merge_exact": form(vx.VX_PART_SAMPLE, vx.VX_SORT_MERGE)[0]}
+        out["uniform"]["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
         # 64 presorted runs (the third key distribution): partition-then-sort
         # against the merge plan on the same input
         G.sort_input(n, "runs", keys=k, rowids=r)
@@ -1030,6 +1036,9 @@ def summarize(line):
         pr = so.get("presorted_runs")
         if pr:
             out["sort_runs_ms"] = {k: v["ms"] for k, v in pr.items() if isinstance(v, dict)}
+        un = line["sort"].get("uniform")
+        if un:
+            out["sort_uniform_ms"] = {k: v["ms"] for k, v in un.items() if isinstance(v, dict)}
     op = line.get("operators")
     if op:
         out["operators_ms"] = {k: {"fused": v["fused_ms"], "operators": v["operators_ms"]} for k, v in op.items()
