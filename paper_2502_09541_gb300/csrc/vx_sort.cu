@@ -435,13 +435,69 @@ __global__ void pl_splitters_kernel(const uint64_t *knots, uint32_t S, uint32_t 
   }
 }
 
+// Keys of the sorted sample that occur at least m / (2P) times (up to cap of
+// them, in no particular order; *n counts them all).  Thread i looks at run
+// starts only and finds the run's end by binary search.
+__global__ void heavy_keys_kernel(const uint64_t *sorted, uint64_t m, uint32_t P, uint64_t *keys, uint32_t *n,
+                                  uint32_t cap) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = sorted[i];
+    if (i > 0 && sorted[i - 1] == v) continue;
+    uint64_t a = i, b = m;  // first index with sorted[] > v
+    while (a < b) {
+      const uint64_t mid = (a + b) >> 1;
+      if (sorted[mid] <= v) a = mid + 1;
+      else b = mid;
+    }
+    if ((a - i) * 2 * (uint64_t)P >= m) {
+      const uint32_t j = atomicAdd(n, 1u);
+      if (j < cap) keys[j] = v;
+    }
+  }
+}
+
+// raw (n_raw non-decreasing splitters of a smooth model) merged with the heavy
+// keys (sorted here, at most cap_heavy of them), duplicates dropped, at most
+// cap_out entries: every heavy key becomes a splitter, so the isolation below
+// gives it a partition of its own as the sample's quantiles do.  One thread.
+__global__ void merge_heavy_kernel(const uint64_t *raw, uint32_t n_raw, uint64_t *heavy, const uint32_t *n_heavy,
+                                   uint32_t cap_heavy, uint64_t *out, uint32_t *n_out, uint32_t cap_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const uint32_t nh = *n_heavy < cap_heavy ? *n_heavy : cap_heavy;
+  for (uint32_t i = 1; i < nh; ++i) {  // insertion sort of a few dozen keys
+    const uint64_t x = heavy[i];
+    uint32_t j = i;
+    while (j > 0 && heavy[j - 1] > x) {
+      heavy[j] = heavy[j - 1];
+      --j;
+    }
+    heavy[j] = x;
+  }
+  uint32_t a = 0, b = 0, k = 0;
+  // the model's splitters all stay; heavy keys fill what room is left
+  uint32_t room = cap_out > n_raw ? cap_out - n_raw : 0;
+  while ((a < n_raw || b < nh) && k < cap_out) {
+    uint64_t v;
+    if (b >= nh || (a < n_raw && raw[a] <= heavy[b])) {
+      v = raw[a++];
+    } else {
+      v = heavy[b++];
+      if (room == 0) continue;
+      --room;
+    }
+    if (k > 0 && out[k - 1] == v) continue;
+    out[k++] = v;
+  }
+  *n_out = k;
+}
+
 // Heavy keys.  A value repeated among consecutive splitters would leave empty
 // partitions, and one partition [v, next) would hold all copies of v plus
 // other keys.  Walking left to right, a splitter not above the last kept one
 // becomes that one + 1 (dropped at UINT64_MAX); a kept value v that occurs at
 // least m / (2P) times in the sorted sample (half a partition's share) is
 // followed by the boundary v + 1, so [v, v + 1) holds v alone.  At most
-// 2(P-1) splitters result; their count goes to *n_out.
+// 2 n_raw splitters result; their count goes to *n_out.
 __global__ void isolate_splitters_kernel(const uint64_t *raw, uint32_t n_raw, const uint64_t *sorted, uint64_t m,
                                          uint32_t P, uint64_t *out, uint32_t *n_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -566,7 +622,7 @@ vx_status range_partition_enqueue(RadixBufs b, uint64_t n, const uint64_t *spl, 
 
 // Splitters for P requested partitions from the sorted sample (device), then
 // heavy-key isolation.  spl_buf has kSplitterBufBytes: [out 256 | raw 256 |
-// knots 1025 | count]; returns the number of splitters in *n_spl (<= 2(P-1)).
+// knots 1025 | count]; returns the number of splitters in *n_spl (at most 254).
 vx_status splitters_from_sample(vx_ctx *ctx, int32_t kind, const uint64_t *sorted, uint64_t m, uint32_t P,
                                 uint64_t *spl_buf, uint32_t mlp_steps, double *ms_train, uint32_t *n_spl) {
   cudaStream_t s = ctx->s_compute;
@@ -589,7 +645,24 @@ vx_status splitters_from_sample(vx_ctx *ctx, int32_t kind, const uint64_t *sorte
     set_error("unknown partitioner %d", kind);
     return VX_E_INVAL;
   }
-  isolate_splitters_kernel<<<1, 32, 0, s>>>(d_raw, P - 1, sorted, m, P, d_out, d_n);
+  uint32_t n_raw = P - 1;
+  if (kind == VX_PART_LEARNED_MLP) {
+    // a smooth CDF model steps over a heavy key's jump instead of landing a
+    // splitter on it: add the sample's heavy keys to its splitters (the
+    // knots area is free here: heavy keys, then the merged list, then counts)
+    constexpr uint32_t kHeavyCap = 64, kMergedCap = 127;  // isolation doubles at most: <= 254 cuts
+    uint64_t *d_heavy = d_knots, *d_merged = d_knots + kHeavyCap;
+    uint32_t *d_cnt = (uint32_t *)(d_knots + kHeavyCap + kMergedCap);
+    VX_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 8, s));
+    heavy_keys_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 1024), 256, 0, s>>>(sorted, m, P, d_heavy, d_cnt,
+                                                                                      kHeavyCap);
+    merge_heavy_kernel<<<1, 1, 0, s>>>(d_raw, P - 1, d_heavy, d_cnt, kHeavyCap, d_merged, d_cnt + 1, kMergedCap);
+    VX_CUDA_TRY(cudaGetLastError());
+    VX_CUDA_TRY(cudaMemcpyAsync(&n_raw, d_cnt + 1, 4, cudaMemcpyDeviceToHost, s));
+    VX_CUDA_TRY(cudaStreamSynchronize(s));
+    VX_CUDA_TRY(cudaMemcpyAsync(d_raw, d_merged, 8ull * n_raw, cudaMemcpyDeviceToDevice, s));
+  }
+  isolate_splitters_kernel<<<1, 32, 0, s>>>(d_raw, n_raw, sorted, m, P, d_out, d_n);
   VX_CUDA_TRY(cudaGetLastError());
   VX_CUDA_TRY(cudaMemcpyAsync(n_spl, d_n, 4, cudaMemcpyDeviceToHost, s));
   VX_CUDA_TRY(cudaStreamSynchronize(s));
