@@ -94,6 +94,12 @@ typedef struct {
   uint32_t lookback_spin_limit; /* polls a radix sort pass makes of one predecessor tile's published
                                count before it gives up, sets its error word and the call returns
                                VX_E_TIMEOUT (0 = 2^20) */
+  int32_t h2d_copy_blocks;  /* host-to-device staging of every executor: 0 = the copy engine
+                               (cudaMemcpyAsync); n > 0 = a copy kernel of n blocks of 256 threads
+                               on the host-to-device stream, loading the pinned host memory through
+                               its device-visible address (where the device allows it, else the
+                               copy engine); at most 1024 */
+  int32_t reserved;         /* 0 */
 } vx_config;
 
 /* ---------------------------------------------------------------- lifetime */

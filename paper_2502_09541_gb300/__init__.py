@@ -45,7 +45,8 @@ class vx_config(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("wait_timeout_ms", ctypes.c_uint32), ("log_chunk_stats", ctypes.c_int32),
                 ("log_timeline", ctypes.c_int32), ("kernel_rows", ctypes.c_int32),
-                ("lookback_spin_limit", ctypes.c_uint32)]
+                ("lookback_spin_limit", ctypes.c_uint32), ("h2d_copy_blocks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class vx_pred(ctypes.Structure):

@@ -123,6 +123,9 @@ static void default_config(vx_config *c) {
 static vx_status init_common(vx_ctx *ctx) {
   VX_CUDA_TRY(cudaGetDevice(&ctx->device));
   VX_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  int hp = 0;
+  VX_CUDA_TRY(cudaDeviceGetAttribute(&hp, cudaDevAttrCanUseHostPointerForRegisteredMem, ctx->device));
+  ctx->host_ptr_ok = hp != 0;
   if (!ctx->s_compute) {
     VX_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->s_compute, cudaStreamNonBlocking));
     ctx->own_compute = true;
@@ -291,7 +294,8 @@ VX_API vx_status vx_set_config(vx_ctx *ctx, const vx_config *cfg) {
       cfg->block_threads > 1024 || (cfg->block_threads & 31) || cfg->blocks_per_sm < 1 ||
       cfg->blocks_per_sm > 32 || (cfg->sched != VX_SCHED_IMMEDIATE && cfg->sched != VX_SCHED_DAG) ||
       cfg->wait_timeout_ms == 0 || cfg->zc_threshold < 0 || cfg->zc_threshold > 1 ||
-      (cfg->kernel_rows != 0 && cfg->kernel_rows != 2 && cfg->kernel_rows != 8 && cfg->kernel_rows != 16)) {
+      (cfg->kernel_rows != 0 && cfg->kernel_rows != 2 && cfg->kernel_rows != 8 && cfg->kernel_rows != 16) ||
+      cfg->h2d_copy_blocks < 0 || cfg->h2d_copy_blocks > 1024 || cfg->reserved != 0) {
     set_error("vx_set_config: value out of range");
     return VX_E_INVAL;
   }

@@ -148,6 +148,7 @@ struct vx_ctx {
   // within the drain limit either: the arena blocks that work may still write
   // are never handed out again, and every later call fails
   bool poisoned = false;
+  bool host_ptr_ok = false;  // kernels may use host pointers of registered memory as they are
   // per-chunk timeline of the last pipeline run with log_timeline (rows of
   // VX_TIMELINE_COLS floats)
   std::vector<float> timeline;
@@ -200,6 +201,16 @@ struct ExecStats {
   uint64_t chunks = 0, bytes_h2d = 0, bytes_d2h = 0, kernel_launches = 0;
   double ms_kernel = 0;
 };
+
+// Issues host <-> device copies on stream s (bytes += their sizes): the copy
+// engine, or for host-to-device copies with sm_blocks > 0 a copy kernel of
+// that many blocks reading the pinned host memory (4-byte aligned ops only;
+// others go to the copy engine).  Host addresses off a 512-byte boundary are
+// split for the copy engine into a short head and an aligned body.
+vx_status issue_copies(const std::vector<CopyOp> &ops, cudaMemcpyKind kind, cudaStream_t s, uint64_t *bytes,
+                       int sm_blocks);
+// the context's choice for host-to-device staging: copy-kernel blocks, or 0
+int h2d_sm_blocks(const vx_ctx *ctx);
 
 // Runs all chunks of `k` through a ring of cfg.n_slots staging slots allocated
 // from the arena (Section 5.3 pipelined executor).

@@ -306,13 +306,12 @@ static vx_status cycle(ServeEngine &e, bool *did) {
   }
   if (qs.empty()) return VX_OK;
   std::lock_guard<std::recursive_mutex> g(ctx->mu);
+  std::vector<CopyOp> ops;
   for (size_t i = 0; i < cols.size(); ++i) {
     const uint64_t len = cols[i]->n_rows > c0 ? std::min(cr, cols[i]->n_rows - c0) : 0;
-    if (len)
-      VX_CUDA_TRY(cudaMemcpyAsync(dcols + i * col_bytes(e), (const char *)cols[i]->host + c0 * 4, 4 * len,
-                                  cudaMemcpyHostToDevice, ctx->s_h2d));
-    e.bytes_h2d += 4 * len;
+    if (len) ops.push_back({(const char *)cols[i]->host + c0 * 4, dcols + i * col_bytes(e), 4 * len});
   }
+  VX_TRY(issue_copies(ops, cudaMemcpyHostToDevice, ctx->s_h2d, &e.bytes_h2d, h2d_sm_blocks(ctx)));
   VX_CUDA_TRY(cudaMemcpyAsync(dparams, hparams, sizeof(ChunkParams) * qs.size(), cudaMemcpyHostToDevice, ctx->s_h2d));
   if (n_items)
     VX_CUDA_TRY(cudaMemcpyAsync(ditems, hitems, sizeof(MultiItem) * n_items, cudaMemcpyHostToDevice, ctx->s_h2d));

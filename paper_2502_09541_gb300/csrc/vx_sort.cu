@@ -984,11 +984,17 @@ vx_status sort_contiguous(vx_ctx *ctx, const uint64_t *keys, const uint32_t *val
   DevBuf sbuf, splbuf;
   uint64_t *sorted = nullptr;
   double ts = now_ms();
-  VX_TRY(sample_and_sort(ctx, dev_keys, n, m, o.seed + (uint64_t)depth * 7919, sbuf, &sorted));
+  // the splitters outlive the sample: allocated first, they do not split the
+  // arena's free space in two once the sample is released (the passes below
+  // size their slots from the largest free block)
   splbuf.arena = &ctx->arena;
   splbuf.p = ctx->arena.alloc(kSplitterBufBytes);
-  if (!splbuf.p) return VX_E_NOMEM;
+  if (!splbuf.p) {
+    set_error("vx_sort: no room for the splitters");
+    return VX_E_NOMEM;
+  }
   uint64_t *d_spl = splbuf.as<uint64_t>();
+  VX_TRY(sample_and_sort(ctx, dev_keys, n, m, o.seed + (uint64_t)depth * 7919, sbuf, &sorted));
   double ms_train = 0;
   uint32_t n_spl = 0;
   VX_TRY(splitters_from_sample(ctx, o.partitioner, sorted, m, P, d_spl, o.mlp_steps, &ms_train, &n_spl));

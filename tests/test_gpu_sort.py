@@ -197,3 +197,22 @@ def test_out_of_core_sort_region_overflow_and_spills(dist):
     assert st["contiguous_layout"] == 1
     assert st["out_of_region_pairs"] > 3_000_017 // 64
     assert st["spill_buffers"] >= 1
+
+
+@pytest.mark.parametrize("budget_mib", [40, 64, 128])
+def test_partition_plan_small_budgets(budget_mib):
+    """Budgets of a few staging slots: the long-lived splitter buffer must not
+    split the arena's free space once the key sample is released (the passes
+    size their slots from the largest free block)."""
+    n = 2_000_003
+    k, r = G.sort_input(n, "zipf", seed=2)
+    c = vx.vx_open(budget_mib << 20)
+    try:
+        kc = vx.vx_register_host_column(c, "k", k)
+        rc = vx.vx_register_host_column(c, "r", r)
+        ok, orr = np.empty(n, np.uint64), np.empty(n, np.uint32)
+        st = vx.vx_sort(c, kc, rc, ok, orr, vx.vx_sort_opts())
+    finally:
+        vx.vx_close(c)
+    ek, er = O.sort_pairs(k, r)
+    assert np.array_equal(ok, ek) and np.array_equal(orr, er) and st["n_partitions"] > 1
