@@ -145,11 +145,13 @@ struct CudaDev {
 
 }  // namespace
 
-// Host -> HBM copies made by the SMs instead of the copy engine: loads of
-// pinned host memory through its device-visible address (the same address on
-// this platform), stores into HBM.  Measured on the host link, a copy engine's
-// 2 GB transfers now and then ran at 80-190 GB/s where SM-driven transfers in
-// between kept 207-211 GB/s; 32 blocks of 256 threads reach the link's rate.
+// Host -> HBM copies made by the SMs instead of the copy engine
+// (vx_config.h2d_copy_blocks > 0): loads of pinned host memory through its
+// device-visible address (the same address on this platform), stores into
+// HBM.  Alone on the link, a copy engine's 2 GB transfers now and then ran at
+// 80-190 GB/s where SM-driven transfers in between kept 207-211 GB/s (32
+// blocks of 256 threads reach the link's rate); inside a pipeline the copy
+// kernel takes SMs from the chunk kernels, so the copy engine is the default.
 constexpr int kCopyBatch = 16;
 struct HostCopyBatch {
   const void *src[kCopyBatch];
