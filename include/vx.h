@@ -331,8 +331,9 @@ vx_status vx_chunk_log_clear(vx_ctx *ctx);
  * 128, 256} MiB and staging ring depth in {2, 3, 4} that fits the arena, then,
  * at the fastest of those, for every kernel shape in {one tile per block, the
  * bulk-copy pipeline at 4 or 6 blocks per SM, scalar 8 or 16 rows per thread
- * at 4 or 8 blocks per SM}; keeps the fastest in the context's config and
- * returns it.  A candidate within 1 % of the fastest time (a tie on a
+ * at 4 or 8 blocks per SM}, then host-to-device staging by the copy engine or
+ * by a copy kernel of 32 blocks (h2d_copy_blocks, where the device allows
+ * it); keeps the fastest in the context's config and returns it.  A candidate within 1 % of the fastest time (a tie on a
  * link-bound plan) wins if its fused-kernel time is lower.  Section 8.1 sweeps
  * Exchange's packet size the same way (fixed per-copy overhead against
  * pipeline depth).  Results do not depend on the configuration, only the time

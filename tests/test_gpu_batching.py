@@ -79,6 +79,7 @@ def test_autotuner_picks_a_candidate_and_keeps_results(star):
     assert best.chunk_bytes in [m << 20 for m in (8, 16, 32, 64, 128, 256)]
     assert best.n_slots in (2, 3, 4)
     assert best.kernel_rows in (0, 2, 8, 16) and best.blocks_per_sm in (4, 6, 8)
+    assert best.h2d_copy_blocks in (0, 32)
     cur = vx.vx_get_config(ctx)
     assert cur.chunk_bytes == best.chunk_bytes and cur.n_slots == best.n_slots
     assert cur.kernel_rows == best.kernel_rows and cur.blocks_per_sm == best.blocks_per_sm
