@@ -950,9 +950,11 @@ def run_ours(args):
                    "rows": args.rows, "l2": "inputs larger than L2 (fact columns stream from host)",
                    "form": "learned" if use_learned else "plain"},
         "forms": forms,
+        # link use of the form the value comes from
         "link": {"h2d_peak_gbs": round(h2d_peak, 1), "d2h_peak_gbs": round(d2h_peak, 1),
-                 "bidir_peak_gbs": round(bid_peak, 1), "link_gbs": round(link_gbs, 1),
-                 "link_frac": round(link_gbs / h2d_peak, 4), "host_frac": round(host_gbs / world / h2d_peak, 4)},
+                 "bidir_peak_gbs": round(bid_peak, 1), "link_gbs": round(link_l if use_learned else link_gbs, 1),
+                 "link_frac": round((link_l if use_learned else link_gbs) / h2d_peak, 4),
+                 "host_frac": round(host_gbs / world / h2d_peak, 4)},
         "rows_per_s": round(rows_step * world / (ms_step / 1000)),
         "query_ms": per_q_ms,
         "overlap": overlap,
