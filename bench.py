@@ -556,6 +556,14 @@ def run_sort_extra(vx, G, args):
             out[name], last = form(part, plan)
             if plan == vx.VX_SORT_PARTITION:
                 st = last
+        # the plain form again, staged by a 32-block copy kernel instead of
+        # the copy engine (stores stay on the copy engine)
+        cfg = vx.vx_get_config(ctx)
+        cfg.h2d_copy_blocks = 32
+        vx.vx_set_config(ctx, cfg)
+        out["plain_sample_copy_kernel"] = form(vx.VX_PART_SAMPLE, vx.VX_SORT_PARTITION)[0]
+        cfg.h2d_copy_blocks = 0
+        vx.vx_set_config(ctx, cfg)
         out["sorted"] = bool(np.all(ok[1:] >= ok[:-1]))
         # per-partition radix sorts against HBM: 24 algorithmic bytes per pair
         # and executed pass (the one-sweep scatter reads and writes the 12-byte
