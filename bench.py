@@ -843,6 +843,34 @@ def run_ours(args):
     learned_gbs = sum(s["bytes_logical"] for s in stats_l) / args.steps * world / (ms_learned * 1e6)
     roofline_learned = fused_roofline(stats_l)
     link_l = sum(s["bytes_h2d"] + s["bytes_zero_copy"] for s in stats_l) / args.steps / (ms_learned * 1e6)
+    # the copy kernel that stages the batched form: by device time it is the
+    # largest kernel of that form (it runs as long as the link is busy), bound
+    # by the host link.  Its launches timed with CUDA events on the
+    # host-to-device stream (the per-chunk timeline of one run of every
+    # template, the same configuration without graph capture)
+    copy_roofline = None
+    if tuned.h2d_copy_blocks:
+        cfg.use_graphs = 0
+        cfg.log_timeline = 1
+        vx.vx_set_config(ctx, cfg)
+        cb, cms, cn = 0, 0.0, 0
+        for p in lplans:
+            _, _, _, _, qs = vx.vx_run_plan(ctx, p)
+            tl = vx.vx_last_timeline(ctx)
+            if len(tl):
+                cb += qs["bytes_h2d"]
+                cms += float((tl[:, 3] - tl[:, 2]).sum())
+                cn += len(tl)
+        cfg.log_timeline = 0
+        cfg.use_graphs = 1
+        vx.vx_set_config(ctx, cfg)
+        if cms > 0:
+            ach = cb / (cms * 1e6)
+            copy_roofline = {"kernel": "host_copy_kernel (%d blocks)" % tuned.h2d_copy_blocks, "bound": "link",
+                             "unit": "GB/s", "achieved": round(ach, 1), "peak": round(h2d_peak, 1),
+                             "frac": round(ach / h2d_peak, 4), "peak_kind": "H2D copy, measured in this run",
+                             "bytes_per_launch": round(cb / max(1, cn)),
+                             "avg_launch_us": round(1000 * cms / max(1, cn), 1), "launches": cn}
     forms = {
         "plain": {"value": round(plain_gbs, 3), "ms_per_step": round(ms_step, 3), "link_gbs": round(link_gbs, 1),
                   "chunk_bytes": 64 << 20, "sched": "immediate", "late": "per plan",
@@ -967,7 +995,7 @@ def run_ours(args):
         "query_ms": per_q_ms,
         "overlap": overlap,
         "call_overhead_ms": round(statistics.median(s["host_ms"] - s["ms_total"] for s in stats_all), 3),
-        "roofline": roofline, "roofline_zero_copy_gather": gather,
+        "roofline": roofline, "roofline_zero_copy_gather": gather, "roofline_h2d_copy": copy_roofline,
         "e2e": {"value": round(e2e_gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": int(e2e_h2d),
                 "d2h_bytes_per_step": int(e2e_d2h), "h2d_staging": e2e_staging},
         "gpu_launches": (int(sum(s["kernel_launches"] for s in stats_l)) +
@@ -1050,6 +1078,9 @@ def summarize(line):
         out["gather_link_frac"] = g.get("frac")
         out["gather_survivors_per_launch"] = g.get("survivors_per_launch")
         out["gather_of_sparse_read_ceiling"] = g.get("of_ceiling")
+    cr = line.get("roofline_h2d_copy")
+    if cr:
+        out["h2d_copy_kernel_link_frac"] = cr.get("frac")
     sv = line.get("serving")
     if sv:
         out["serving_ms"] = {"p50": sv.get("p50_ms"), "p99": sv.get("p99_ms")}
