@@ -95,3 +95,30 @@ def test_config_rejects_bad_block_counts(star):
         cfg.h2d_copy_blocks = bad
         with pytest.raises(vx.VxError):
             vx.vx_set_config(c, cfg)
+
+
+def test_serving_scan_sm_copy(star):
+    """The serving engine's shared scan staged by the copy kernel: every query
+    as alone and as the oracle."""
+    c, fact, dims, fid, did = star
+    names = ["T2_1", "T3_1", "T2_10", "T3_0.1"]
+    ranges = [(0, N), (123_457, 2_500_001), (7, 3_999_999), (1_000_000, 1_000_000 + 777_777)]
+    try:
+        _set(c, 0)
+        alone = [vx.vx_run_plan(c, vx.make_plan(G.star_templates()[n], fid, did, G.STAR_ATTR_CARD,
+                                                vx.VX_LATE_AUTO, rb, re)) for n, (rb, re) in zip(names, ranges)]
+        _set(c, 32)
+        vx.vx_serve_start(c, chunk_rows=1 << 19, max_active=8)
+        tickets = [vx.vx_submit(c, vx.make_plan(G.star_templates()[n], fid, did, G.STAR_ATTR_CARD,
+                                                 vx.VX_LATE_AUTO, rb, re)) for n, (rb, re) in zip(names, ranges)]
+        results = [vx.vx_wait(c, t) for t in tickets]
+        vx.vx_serve_stop(c)
+    finally:
+        _set(c, 0, 64 << 20)
+    for (n, (rb, re)), a, r in zip(zip(names, ranges), alone, results):
+        assert r[0] == vx.VX_OK
+        for x, y in zip(a[1:4], r[1:4]):
+            assert np.array_equal(x, y), (n, rb, re)
+    es, ec = O.star(G.star_templates()[names[1]], fact, dims, *ranges[1], nthreads=8)
+    nz = np.nonzero(ec)[0]
+    assert np.array_equal(results[1][1], nz) and np.array_equal(results[1][2], es[nz])
