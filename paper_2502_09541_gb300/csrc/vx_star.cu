@@ -1649,7 +1649,9 @@ vx_status star_graph(vx_ctx *ctx, StarExKernel &ek, const std::vector<std::share
     return st;
   }
   VX_CUDA_TRY(ce);
-  ce = cudaGraphInstantiate(&e->exec, g, 0);
+  // per-node priorities, so that the copy kernels' high priority holds in
+  // the replayed graph too (without the flag it runs at the stream's)
+  ce = cudaGraphInstantiate(&e->exec, g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
   VX_CUDA_TRY(ce);
   e->chunks = est.chunks;
