@@ -98,7 +98,9 @@ typedef struct {
                                (cudaMemcpyAsync); n > 0 = a copy kernel of n blocks of 256 threads
                                on the host-to-device stream, loading the pinned host memory through
                                its device-visible address (where the device allows it, else the
-                               copy engine); at most 1024 */
+                               copy engine), launched at the device's greatest stream priority (and
+                               captured graphs honour it) so that its blocks are not queued behind
+                               a chunk kernel's; at most 1024 */
   int32_t reserved;         /* 0 */
 } vx_config;
 
