@@ -828,11 +828,11 @@ def run_ours(args):
     tuned = vx.vx_autotune(ctx, plans[TEMPLATES.index("T3_1")], min(args.rows, 100_000_000))
     cfg = vx.vx_get_config(ctx)
     cfg.use_graphs = 1
-    # the batched form stages with a 32-block copy kernel: on hosts where the
-    # copy engine's rate drops (it does after a long run of other GPU work on
-    # the same box) a copy kernel holds 183-191 GB/s; where the copy engine
-    # holds, the plain form keeps its rate, and the line reports the better
-    # form
+    # the batched form stages with a 32-block copy kernel (launched at the
+    # highest priority): on hosts where the copy engine's rate drops (it does
+    # after a long run of other GPU work on the same box) the copy kernel
+    # holds the link's rate; the plain form stages by copy engine, and the
+    # line reports the better form
     cfg.h2d_copy_blocks = 32
     tuned.h2d_copy_blocks = 32
     vx.vx_set_config(ctx, cfg)
