@@ -196,12 +196,12 @@ def make_data(rows, pinned=False, row0=0):
     return fact, dims
 
 
-def cpu_baseline(fact, dims, sample_rows):
-    """The oracle as it stands, on the host cores, over the first sample_rows
-    fact rows of every template of one step."""
+def cpu_baseline(fact, dims, sample_rows, nthreads=None):
+    """The oracle as it stands, on the host cores (nthreads, default all),
+    over the first sample_rows fact rows of every template of one step."""
     import datagen as G
     import oracle as O
-    nthreads = os.cpu_count() or 1
+    nthreads = nthreads or os.cpu_count() or 1
     logical = 0
     t0 = time.perf_counter()
     for name in TEMPLATES:
@@ -212,6 +212,15 @@ def cpu_baseline(fact, dims, sample_rows):
         logical += 4 * len(cols) * sample_rows
     dt = time.perf_counter() - t0
     return logical / dt / 1e9, nthreads, dt
+
+
+def single_thread_baseline(fact, dims, sample_rows):
+    """The same oracle on one host thread, over a tenth of the sample (at
+    most 2M rows) so that it stays within a few seconds."""
+    n1 = max(1, min(sample_rows // 10, 2_000_000))
+    v1, _, dt1 = cpu_baseline(fact, dims, n1, nthreads=1)
+    return {"value": round(v1, 3), "unit": "GB/s", "cores": 1,
+            "sample": f"first {n1} fact rows x 6 templates ({dt1:.1f} s)"}
 
 
 def run_reference(args):
@@ -236,7 +245,8 @@ def run_reference(args):
         "config": {"workload": f"star join, {TEMPLATES} over the first {sample} rows of the 600M-row fact table",
                    "rows": sample},
         "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
-                         "sample": f"first {sample} fact rows, 6 templates"},
+                         "sample": f"first {sample} fact rows, 6 templates",
+                         "single_thread": single_thread_baseline(fact, dims, sample)},
         "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -1014,7 +1024,8 @@ def run_ours(args):
         sample = args.cpu_sample_rows or min(args.rows, 20_000_000)
         v, cores, dt = cpu_baseline(fact, dims, sample)
         line["cpu_baseline"] = {"value": round(v, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
-                                "sample": f"first {sample} fact rows x 6 templates ({dt:.1f} s)"}
+                                "sample": f"first {sample} fact rows x 6 templates ({dt:.1f} s)",
+                                "single_thread": single_thread_baseline(fact, dims, sample)}
     vx.vx_close(ctx)
     del arena
     if rank == 0 and world == 1 and not args.no_extras:
