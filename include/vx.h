@@ -49,7 +49,7 @@ enum {
   VX_E_CAPACITY = -4,    /* caller output buffer too small; required size reported */
   VX_E_TIMEOUT = -5,     /* a bounded wait expired */
   VX_E_BUSY = -6,        /* serving queue full */
-  VX_E_UNSUPPORTED = -7, /* valid request outside what this build implements */
+  VX_E_UNSUPPORTED = -7, /* valid request outside what the library implements */
   VX_E_DUPKEY = -8,      /* duplicate key on the build side of a join */
   VX_E_RANGE = -9        /* a group-key code outside [0, card) */
 };
