@@ -536,7 +536,7 @@ def run_sort_extra(vx, G, args):
             o.host_scratch_bytes = scratch.nbytes
             o.sample_size = 1 << 20
             # two runs per form, the faster reported (single runs of a form
-            # have come out up to 35 % slow on some boxes, whichever form ran)
+            # have come out up to 35 % slow on some machines, whichever form ran)
             runs = [vx.vx_sort(ctx, kc, rc, ok, orr, o) for _ in range(2)]
             st = min(runs, key=lambda r: r["ms_total"])
             d = {"gpairs_s": round(n / st["ms_total"] / 1e6, 3), "ms": round(st["ms_total"], 1),
@@ -840,7 +840,7 @@ def run_ours(args):
     cfg.use_graphs = 1
     # the batched form stages with a 32-block copy kernel (launched at the
     # highest priority): on hosts where the copy engine's rate drops (it does
-    # after a long run of other GPU work on the same box) the copy kernel
+    # after a long run of other GPU work on the same machine) the copy kernel
     # holds the link's rate; the plain form stages by copy engine, and the
     # line reports the better form
     cfg.h2d_copy_blocks = 32

@@ -2464,9 +2464,9 @@ VX_API vx_status vx_autotune(vx_ctx *ctx, const vx_plan *plan, uint64_t sample_r
   }
   // host-to-device staging at that chunking and shape: the copy engine
   // against a copy kernel of 32 blocks.  On some hosts the copy engine's rate
-  // drops (measured: 116-156 GB/s on the same box where a copy kernel staged at
-  // 183-191); where it holds, it wins (the copy kernel takes SMs from the fused
-  // kernel) and a tie keeps it, its fused-kernel time being lower.
+  // drops (measured: 116-156 GB/s on a host where a copy kernel staged at
+  // 183-191); where it holds, it ties or wins (the copy kernel takes SMs from
+  // the fused kernel) and a tie keeps it, its fused-kernel time being lower.
   if (ctx->host_ptr_ok) {
     vx_config c = best_cfg;
     c.h2d_copy_blocks = best_cfg.h2d_copy_blocks ? 0 : 32;
