@@ -52,6 +52,33 @@ def test_star_sm_copy_equals_copy_engine_and_oracle(star, blocks, name):
     assert np.array_equal(got[1], nz) and np.array_equal(got[2], es[nz]) and np.array_equal(got[3], ec[nz])
 
 
+@pytest.mark.parametrize("late", [vx.VX_LATE_AUTO, vx.VX_LATE_PER_CHUNK])
+@pytest.mark.parametrize("name", ["T2_10", "T3_1"])
+def test_star_graphs_sm_copy_equal_oracle(star, name, late):
+    """The batched form as the benchmark times it: the pipeline captured in a
+    graph (copy kernels at the highest priority, per-node priorities kept),
+    two staging slots, per-chunk late decisions; the capture and its replay
+    both equal the oracle on a ragged range."""
+    c, fact, dims, fid, did = star
+    T = G.star_templates()[name]
+    rb, re = 1_001, 3_999_999
+    cfg = vx.vx_get_config(c)
+    saved = (cfg.use_graphs, cfg.chunk_bytes, cfg.n_slots, cfg.h2d_copy_blocks)
+    cfg.use_graphs, cfg.chunk_bytes, cfg.n_slots, cfg.h2d_copy_blocks = 1, 8 << 20, 2, 32
+    vx.vx_set_config(c, cfg)
+    try:
+        runs = [vx.vx_run_plan(c, vx.make_plan(T, fid, did, G.STAR_ATTR_CARD, late, rb, re)) for _ in range(2)]
+    finally:
+        cfg.use_graphs, cfg.chunk_bytes, cfg.n_slots, cfg.h2d_copy_blocks = saved
+        vx.vx_set_config(c, cfg)
+    es, ec = O.star(T, fact, dims, rb, re, nthreads=8)
+    nz = np.nonzero(ec)[0]
+    for r in runs:
+        assert r[0] == vx.VX_OK
+        assert np.array_equal(r[1], nz) and np.array_equal(r[2], es[nz]) and np.array_equal(r[3], ec[nz])
+    assert runs[0][4]["chunks"] > 2  # several chunks, so the copies overlap kernels
+
+
 @pytest.mark.parametrize("plan", [0, 1])
 def test_sort_sm_copy(plan):
     n = 2_000_003
